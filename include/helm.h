@@ -1,0 +1,217 @@
+/*
+ * helm.h -- C ABI of libhelm, complex Krylov solvers for Helmholtz
+ * finite-element systems on one GB300 GPU (sm_103a).
+ *
+ * The operations follow "Iterative Krylov Methods for Acoustic Problems on
+ * GPU" (Cheik Ahamed & Magoules, arXiv 2112.11880):
+ *   - the problem: -lap(u) - k^2 u = g, k = 2 pi F / c, discretised by finite
+ *     elements into a sparse complex system A x = b (Section 1);
+ *   - matrices in CSR (Section 2);
+ *   - complex double-precision vector kernels and CSR SpMV (Section 3,
+ *     Tables 2-8);
+ *   - preconditioned BiCGStab, BiCGStab(l) and TFQMR with residual
+ *     tolerance, zero initial guess and an iteration cap (Section 4).
+ *
+ * Conventions shared by every call:
+ *   - Complex numbers are stored interleaved (re, im): complex128 = two
+ *     doubles (16 bytes), complex64 = two floats (8 bytes).  Device arrays
+ *     must be aligned to their element size; CSR values and vectors used by
+ *     the solvers must be 16-byte aligned (any cudaMalloc'd or PyTorch buffer
+ *     is).
+ *   - Pointers prefixed d_ are device pointers; all others are host pointers.
+ *   - The caller owns every buffer passed in.  A CSR handle borrows rowptr,
+ *     colind and values: they must stay allocated and unchanged while the
+ *     handle lives.  The handle owns only its own workspace, released by
+ *     helm_csr_destroy.
+ *   - `stream` is a cudaStream_t (0 = legacy default stream).  Kernels are
+ *     enqueued on it; calls documented as asynchronous return after enqueueing
+ *     and report launch errors only.
+ *   - Every call returns a helm_status; nothing aborts, traps or prints.
+ *     Invalid arguments are detected on the host before any work is enqueued.
+ */
+#ifndef HELM_H
+#define HELM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* helm_stream_t; /* same type as cudaStream_t */
+
+typedef enum {
+  HELM_OK = 0,
+  HELM_ERR_INVALID = 1,       /* bad argument or malformed CSR */
+  HELM_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+  HELM_ERR_NOMEM = 3,         /* device allocation failed */
+  HELM_ERR_NOT_CONVERGED = 4, /* iteration cap reached before the tolerance */
+  HELM_ERR_BREAKDOWN = 5,     /* Krylov breakdown (a zero denominator) */
+  HELM_ERR_TIMEOUT = 6,       /* the device-side deadline expired */
+  HELM_ERR_NONFINITE = 7      /* NaN or Inf met in a scalar of the recurrence */
+} helm_status;
+
+typedef enum { HELM_C128 = 0, HELM_C64 = 1 } helm_dtype;
+
+/* Flags for helm_csr_create. */
+#define HELM_CSR_VALIDATE 1u  /* check rowptr monotone, colind in range and
+                                 sorted within rows (one device pass + sync) */
+
+typedef struct helm_csr_s* helm_csr; /* opaque CSR handle */
+
+/*
+ * helm_csr_create -- wrap an n x n complex CSR matrix (Section 2: matrices
+ * are stored in CSR) and prepare it for SpMV and the solvers.
+ *   out      : receives the handle (host).
+ *   n        : number of rows = columns, 0 <= n < 2^31.
+ *   nnz      : number of stored entries, 0 <= nnz < 2^31, equal to rowptr[n].
+ *   d_rowptr : int32[n+1], rowptr[0] = 0, non-decreasing.
+ *   d_colind : int32[nnz], column of each entry, 0 <= colind < n.
+ *   d_vals   : complex[nnz] of type dt (complex128 or complex64).
+ *   flags    : HELM_CSR_VALIDATE or 0.
+ * Work done: row statistics and the choice of SpMV variant (one device pass),
+ * workspace allocation.  Synchronises `stream` once.  Returns
+ * HELM_ERR_INVALID on bad sizes, a misaligned pointer, or (with
+ * HELM_CSR_VALIDATE) a malformed pattern; HELM_ERR_NOMEM if the workspace
+ * cannot be allocated.
+ */
+helm_status helm_csr_create(helm_csr* out, int32_t n, int64_t nnz, const int32_t* d_rowptr,
+                            const int32_t* d_colind, const void* d_vals, helm_dtype dt,
+                            uint32_t flags, helm_stream_t stream);
+
+/* helm_csr_destroy -- free the handle's workspace (synchronises the device
+ * work of the handle first).  NULL is accepted. */
+helm_status helm_csr_destroy(helm_csr A);
+
+/*
+ * helm_spmv -- y = alpha * A x + beta * y (Section 3, Table 8: CSR SpMV,
+ * complex arithmetic).
+ *   alpha, beta : host complex128 scalars (double[2]); for a complex64 handle
+ *                 they are rounded to complex64.
+ *   d_x         : complex[n] of the handle's type; must not alias d_y.
+ *   d_y         : complex[n]; not read when beta == 0.
+ * Asynchronous.
+ */
+helm_status helm_spmv(helm_csr A, const double* alpha, const void* d_x, const double* beta,
+                      void* d_y, helm_stream_t stream);
+
+/*
+ * helm_dot -- d_out = (x, y) = sum_i conj(x_i) y_i when conj_x != 0 (zdotc),
+ * sum_i x_i y_i when conj_x == 0 (zdotu).  Section 3 computes the dot product
+ * as an element-wise product followed by a block-wise sum of the products;
+ * here each block sums its share in a fixed order and one block adds the block
+ * partials in block order, so the result is bit-for-bit reproducible.
+ *   n     : vector length, 0 <= n < 2^31 (n = 0 gives 0).
+ *   dt    : element type of x and y; complex64 inputs are accumulated in
+ *           double precision.
+ *   d_out : device complex128 (double[2]).
+ * Asynchronous.  Uses stream-ordered scratch memory (cudaMallocAsync).
+ */
+helm_status helm_dot(int64_t n, helm_dtype dt, const void* d_x, const void* d_y, int conj_x,
+                     void* d_out, helm_stream_t stream);
+
+/*
+ * helm_nrm2 -- d_out = ||x||_2 = sqrt(sum_i |x_i|^2) (Section 3, Table 7).
+ *   d_out : device double.
+ * Asynchronous, deterministic, stream-ordered scratch as helm_dot.
+ */
+helm_status helm_nrm2(int64_t n, helm_dtype dt, const void* d_x, double* d_out,
+                      helm_stream_t stream);
+
+/*
+ * helm_axpby -- y = alpha * x + beta * y (Section 3: ZAXPY, Table 4, is
+ * beta = 1; ZSCAL, Table 3, is alpha = 0 with y scaled by beta; ZASSIGN,
+ * Table 2, is alpha = 1, beta = 0).
+ *   alpha, beta : host complex128 (double[2]).
+ *   d_x         : complex[n]; may equal d_y.  Not read when alpha == 0.
+ *   d_y         : complex[n]; not read when beta == 0.
+ * Asynchronous.
+ */
+helm_status helm_axpby(int64_t n, helm_dtype dt, const double* alpha, const void* d_x,
+                       const double* beta, void* d_y, helm_stream_t stream);
+
+/* Krylov method selector (Section 4). */
+typedef enum { HELM_BICGSTAB = 0, HELM_TFQMR = 1, HELM_BICGSTABL = 2 } helm_method;
+/* Arithmetic of the solve. */
+typedef enum {
+  HELM_PREC_FP64 = 0, /* complex128 throughout */
+  HELM_PREC_MIXED = 1 /* complex64 inner BiCGStab inside complex128 iterative
+                         refinement: residual, update and norms in FP64 */
+} helm_precision;
+/* How the iteration loop is driven on the device. */
+typedef enum {
+  HELM_LAUNCH_AUTO = 0,
+  HELM_LAUNCH_GRAPH = 1,      /* CUDA graph with a device-driven while node */
+  HELM_LAUNCH_PERSISTENT = 2  /* one cooperative kernel with grid barriers */
+} helm_launch;
+
+typedef struct {
+  double tol;          /* target ||b - A x|| / ||b|| (Section 4 uses 1e-9) */
+  int32_t maxit;       /* iteration cap (Section 4 uses 1000); each BiCGStab
+                          or TFQMR iteration applies A twice */
+  int32_t use_x0;      /* 0: start from x = 0 (Section 4); 1: start from d_x */
+  int32_t method;      /* helm_method */
+  int32_t precision;   /* helm_precision */
+  double inner_tol;    /* HELM_PREC_MIXED: relative tolerance of each inner
+                          complex64 solve */
+  double deadline_s;   /* device wall-clock limit of one solve; <= 0: none */
+  int32_t ell;         /* l of BiCGStab(l), 1..8 */
+  int32_t launch;      /* helm_launch */
+} helm_opts;
+
+typedef struct {
+  int32_t iters;        /* iterations performed (all restarts / refinement
+                           steps included; for mixed precision, inner
+                           iterations) */
+  int32_t restarts;     /* restarts (BiCGStab) or refinement steps (mixed) */
+  double relres_recur;  /* last recurrence residual / ||b|| */
+  double relres_true;   /* ||b - A x|| / ||b|| recomputed in FP64 at the end */
+  helm_status status;
+  int32_t spmv_count;   /* applications of A (all precisions) */
+} helm_info;
+
+/* Defaults: tol 1e-8, maxit 20000, use_x0 0, BiCGStab, FP64, inner_tol 1e-5,
+ * no deadline, ell 2, launch auto. */
+void helm_opts_default(helm_opts* o);
+
+/*
+ * helm_bicgstab_solve -- solve A x = b with the Krylov method of o->method
+ * (Section 4: P-BiCGSTAB, P-BiCGSTAB(l), P-TFQMR; identity preconditioner).
+ *   d_b  : complex128[n] right-hand side.
+ *   d_x  : complex128[n] solution, overwritten; read first when o->use_x0.
+ *   o    : options (NULL = defaults).
+ *   info : host, filled after one synchronisation of `stream` at the end;
+ *          may be NULL.
+ * Scalars of the recurrence stay on the device: no host round trip per dot
+ * product (the paper copies each dot product back; here the whole loop runs
+ * on the device and only the final status is read).  The handle must be
+ * complex128.  Returns info->status.  d_x always holds the last iterate.
+ * Solves on one handle must not overlap (they share the handle's workspace).
+ */
+helm_status helm_bicgstab_solve(helm_csr A, const void* d_b, void* d_x, const helm_opts* o,
+                                helm_info* info, helm_stream_t stream);
+
+/*
+ * helm_adjoint -- the backward pass of u = A^{-1} b for a real loss L(u):
+ * solves A^T mu = d_dLdu (A^T = A is required: complex symmetric FEM
+ * matrices) and, when d_dLdvals != NULL, writes dL/dA_ij = -mu_i u_j on every
+ * stored entry (CSR order).  With that, dL/db = conj(mu) * 2 in PyTorch's
+ * convention and dL/dtheta = 2 Re sum_ij dL/dA_ij dA_ij/dtheta.
+ *   d_u       : complex128[n] forward solution.
+ *   d_dLdu    : complex128[n] dL/du in the holomorphic sense
+ *               (for L = sum |u_r - d_r|^2: conj(u_r - d_r) on receivers).
+ *   d_mu      : complex128[n] output.
+ *   d_dLdvals : complex128[nnz] output or NULL.
+ * Synchronises once at the end (info as helm_bicgstab_solve).
+ */
+helm_status helm_adjoint(helm_csr A, const void* d_u, const void* d_dLdu, const helm_opts* o,
+                         void* d_mu, void* d_dLdvals, helm_info* info, helm_stream_t stream);
+
+/* helm_status_string -- static description of a status code. */
+const char* helm_status_string(helm_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HELM_H */

@@ -1,0 +1,176 @@
+"""CPU oracle for the Helmholtz Krylov hot path -- TEST INFRASTRUCTURE ONLY.
+
+Only the tests, the smoke check and the benchmark's CPU-baseline leg may
+import this package.  The product library (paper_2112_11880_gb300) never
+imports it, and this package never imports the product library: the two share
+no code.  Inputs come from `helmgen`, the seeded generator both sides use.
+
+The compiled part (helm_oracle.cpp) holds the sequential C++ SpMV, zdotc,
+norm and BiCGStab.  This module adds the numpy-level pieces that are plain
+definitions: forming A(w) = K - w^2 M_c + i w B_c for a frequency, dense
+solves on tiny meshes, and the adjoint sound-speed gradient chain.
+
+Parity pins for every function here are in tests/test_oracle_*.py.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "helm_oracle.cpp")
+_LIB_PATH = os.path.join(_HERE, "_build", "libhelm_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+STATUS = {0: "ok", 1: "invalid", 4: "not_converged", 5: "breakdown", 7: "nonfinite"}
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with g++ -O2 (no fast-math) if it is missing or stale."""
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    subprocess.check_call(["g++", "-std=c++17", "-O2", "-fPIC", "-shared", "-o", tmp, _SRC])
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.c_void_p
+            lib.oracle_spmv.argtypes = [ctypes.c_int32, P, P, P, P, P]
+            lib.oracle_spmv.restype = None
+            lib.oracle_zdotc.argtypes = [ctypes.c_int64, P, P, P]
+            lib.oracle_zdotc.restype = None
+            lib.oracle_dznrm2.argtypes = [ctypes.c_int64, P]
+            lib.oracle_dznrm2.restype = ctypes.c_double
+            lib.oracle_bicgstab.argtypes = [ctypes.c_int32, P, P, P, P, P, ctypes.c_double,
+                                            ctypes.c_int32, ctypes.c_int, P, P, P]
+            lib.oracle_bicgstab.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _c(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+def spmv(rowptr, colind, vals, x) -> np.ndarray:
+    """y = A x for complex128 CSR (sequential, CSR order)."""
+    lib = _load()
+    n = len(rowptr) - 1
+    rp, prp = _c(rowptr, np.int32)
+    ci, pci = _c(colind, np.int32)
+    v, pv = _c(vals, np.complex128)
+    xx, px = _c(x, np.complex128)
+    y = np.empty(n, dtype=np.complex128)
+    lib.oracle_spmv(n, prp, pci, pv, px, y.ctypes.data_as(ctypes.c_void_p))
+    return y
+
+
+def zdotc(x, y) -> complex:
+    """(x, y) = sum conj(x_i) y_i with Neumaier-compensated sums."""
+    lib = _load()
+    xx, px = _c(x, np.complex128)
+    yy, py = _c(y, np.complex128)
+    if xx.size != yy.size:
+        raise ValueError("length mismatch")
+    out = np.zeros(2)
+    lib.oracle_zdotc(xx.size, px, py, out.ctypes.data_as(ctypes.c_void_p))
+    return complex(out[0], out[1])
+
+
+def dznrm2(x) -> float:
+    lib = _load()
+    xx, px = _c(x, np.complex128)
+    return float(lib.oracle_dznrm2(xx.size, px))
+
+
+def bicgstab(rowptr, colind, vals, b, tol=1e-8, maxit=20000, x0=None):
+    """Textbook BiCGStab; returns (x, info dict)."""
+    lib = _load()
+    n = len(rowptr) - 1
+    rp, prp = _c(rowptr, np.int32)
+    ci, pci = _c(colind, np.int32)
+    v, pv = _c(vals, np.complex128)
+    bb, pb = _c(b, np.complex128)
+    x = np.zeros(n, dtype=np.complex128) if x0 is None else np.array(x0, dtype=np.complex128)
+    it = ctypes.c_int32(0)
+    rr = ctypes.c_double(0.0)
+    rt = ctypes.c_double(0.0)
+    st = lib.oracle_bicgstab(n, prp, pci, pv, pb, x.ctypes.data_as(ctypes.c_void_p), float(tol),
+                             int(maxit), 0 if x0 is None else 1, ctypes.byref(it),
+                             ctypes.byref(rr), ctypes.byref(rt))
+    return x, {"status": STATUS.get(st, st), "iters": it.value, "relres_recur": rr.value,
+               "relres_true": rt.value}
+
+
+# ---------------------------------------------------------------------------
+# numpy-level definitions
+# ---------------------------------------------------------------------------
+
+def helmholtz_values(K, Mc, Bc, w: float) -> np.ndarray:
+    """A(w) = K - w^2 M_c + i w B_c entry by entry (the frequency-dependent
+    system of the Helmholtz problem of Section 1 with the impedance term)."""
+    K = np.asarray(K, dtype=np.float64)
+    return (K - (w * w) * np.asarray(Mc)) + 1j * (w * np.asarray(Bc))
+
+
+def densify(rowptr, colind, vals, ncols=None) -> np.ndarray:
+    n = len(rowptr) - 1
+    D = np.zeros((n, n if ncols is None else ncols), dtype=np.complex128)
+    for i in range(n):
+        for k in range(rowptr[i], rowptr[i + 1]):
+            D[i, colind[k]] += vals[k]
+    return D
+
+
+def dense_solve(rowptr, colind, vals, b) -> np.ndarray:
+    """LAPACK zgesv on the densified matrix (tiny meshes only)."""
+    return np.linalg.solve(densify(rowptr, colind, vals), np.asarray(b, dtype=np.complex128))
+
+
+def loss(u, receivers, d) -> float:
+    """L = sum over receivers of |u_r - d_r|^2."""
+    e = np.asarray(u)[receivers] - np.asarray(d)
+    return float(np.sum(e.real ** 2 + e.imag ** 2))
+
+
+def adjoint_rhs(n, u, receivers, d) -> np.ndarray:
+    """w = dL/du in the holomorphic sense: w_r = conj(u_r - d_r) on receivers."""
+    w = np.zeros(n, dtype=np.complex128)
+    w[receivers] = np.conj(np.asarray(u)[receivers] - np.asarray(d))
+    return w
+
+
+def nnz_gradient(rowptr, colind, mu, u) -> np.ndarray:
+    """G_k = -mu_i u_j for CSR slot k = (i, j): dL/dA_ij for L real, u = A^-1 b
+    and A^T mu = dL/du (A = A^T here)."""
+    rows = np.repeat(np.arange(len(rowptr) - 1), np.diff(rowptr))
+    return -np.asarray(mu)[rows] * np.asarray(u)[np.asarray(colind)]
+
+
+def sound_speed_gradient(G, elem_map, Me, Bf, c, w, top) -> np.ndarray:
+    """dL/dc_e = 2 Re sum_{a,b} G[map[e,a,b]] dA_ab/dc_e with
+    dA/dc_e = (2 w^2 / c_e^3) M_e - i (w / c_e^2) B_f (B_f only on top elements).
+    Slots eliminated by the Dirichlet condition (map = -1) do not depend on c."""
+    E = elem_map.shape[0]
+    grad = np.zeros(E)
+    Gm = np.where(elem_map >= 0, np.asarray(G)[np.maximum(elem_map, 0)], 0.0)   # [E, 64]
+    c = np.asarray(c, dtype=np.float64)
+    dM = (2.0 * w * w / c ** 3)[:, None] * Me.reshape(1, 64)
+    dB = np.where(np.asarray(top)[:, None], (w / c ** 2)[:, None] * Bf.reshape(1, 64), 0.0)
+    dA = dM - 1j * dB
+    grad = 2.0 * np.real(np.sum(Gm * dA, axis=1))
+    return grad
