@@ -1,0 +1,371 @@
+"""Benchmark: complex128 BiCGStab solves per second on the 120x60x50 Q1
+Helmholtz cavity (376,431 unknowns, 9,677,849 stored entries, F = 1360 Hz,
+10 points per wavelength) to a relative residual of 1e-8, plus the roofline
+of the dominant kernel (the complex128 CSR SpMV, two per iteration).
+
+One step = one full solve (device-resident b -> x, status read back).
+Prints one JSON line.  `--impl reference` times the CPU oracle instead (on a
+bounded sample of the same workload).
+
+Multi-GPU: the solves are independent, so N processes run N replicas (one
+per GPU, no collective on the data path); the value is all solves of all
+ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import helmgen  # noqa: E402
+
+METRIC = "BiCGStab solves/sec and SpMV HBM GB/s (fraction of peak) at 1e-8 rel. error"
+WORKLOAD = "cavity120"
+FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (vector and tensor) nominal rate
+PROFILE = os.path.join(ROOT, "profiles", "spmv_c128_cavity120.md")
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    for f in ("spmv.cuh", "common.cuh", "api.cu"):
+        with open(os.path.join(ROOT, "paper_2112_11880_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """dram bytes per SpMV launch from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    try:
+        txt = open(PROFILE).read()
+    except OSError:
+        return None
+    sha = re.search(r"source_sha:\s*([0-9a-f]+)", txt)
+    tb = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not sha or not tb or sha.group(1) != kernel_source_sha():
+        return None
+    return float(tb.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def barrier_max(value: float, ws: int) -> float:
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t[0])
+
+
+def build_problem(cfg):
+    p = helmgen.assemble(cfg)
+    vals = helmgen.helmholtz_values(p, cfg.F)
+    b = helmgen.source(p)
+    return p, vals, b
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def run_gpu(args):
+    import torch
+
+    import paper_2112_11880_gb300 as helm
+    from paper_2112_11880_gb300 import build as hbuild
+
+    ws, rank, local = dist_info()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    hbuild.build()
+    cfg = helmgen.CONFIGS[WORKLOAD]
+    p, vals, b = build_problem(cfg)
+    A = helm.CsrMatrix.from_host(p.rowptr, p.colind, vals, device=dev)
+    bd = torch.as_tensor(b, device=dev)
+    xd = torch.empty_like(bd)
+    opts = helm.default_opts(tol=cfg.tol, maxit=100000)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        return helm.helm_bicgstab_solve(A.handle, bd, xd, opts, stream)
+
+    for _ in range(args.warmup):
+        info = step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    infos = []
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            infos.append(step())
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ms = barrier_max(ms, ws)
+    ok = all(i["status"] == "ok" and i["relres_true"] <= 1.5 * cfg.tol for i in infos)
+    iters = [i["iters"] for i in infos]
+    launches = sum(3 * (i["restarts"] + 1) + 5 * i["iters"] for i in infos)
+    solves = args.steps * ws
+    value = solves / (ms / 1e3)
+    # independent check of the last solution with the CPU SpMV of the generator data
+    xg = xd.cpu().numpy()
+    import scipy.sparse as sp
+    Ah = sp.csr_matrix((vals, p.colind, p.rowptr), shape=(p.n, p.n))
+    relres_host = float(np.linalg.norm(b - Ah @ xg) / np.linalg.norm(b))
+
+    # dominant kernel: the complex128 SpMV, timed alone in a loop of launches
+    # (same engine as the two SpMVs of every iteration); matrix 207 MB > L2.
+    peaks, peak_src = load_peaks()
+    x1 = torch.as_tensor(helmgen.complex_vector(p.n, 1), device=dev)
+    y1 = torch.empty_like(x1)
+    for _ in range(5):
+        A.matvec(x1, y1)
+    reps = 50
+    torch.cuda.synchronize()
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for _ in range(reps):
+        A.matvec(x1, y1)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    spmv_ms = s0.elapsed_time(s1) / reps
+    spmv_bytes = 20 * p.nnz + 4 * (p.n + 1) + 16 * p.n + 16 * p.n
+    spmv_flops = 8 * p.nnz
+    spmv_gbs = spmv_bytes / (spmv_ms * 1e-3) / 1e9
+    spmv_tflops = spmv_flops / (spmv_ms * 1e-3) / 1e12
+    traffic = profiled_traffic()
+    roofline = {"bound": "alu", "achieved": round(spmv_tflops, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": round(spmv_tflops / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
+                "kernel": "k_spmv<double2> complex128 CSR SpMV (8 flop/nnz = 4 DFMA)",
+                "launch_ms": round(spmv_ms, 5),
+                "hbm": {"achieved_gbs": round(spmv_gbs, 1), "peak_gbs": peaks.get("hbm_gbs"),
+                        "frac": round(spmv_gbs / peaks.get("hbm_gbs", 6800.0), 4), "peak_src": peak_src,
+                        "alg_bytes": spmv_bytes},
+                "peak_src": "GB300 FP64 nominal 1.25 TFLOP/s (1.19 measured by DFMA probe)"}
+
+    # end to end through the C ABI with host buffers: upload the matrix and b
+    # from pinned memory, create the handle, solve, read x back.
+    h_rowptr = torch.as_tensor(p.rowptr).pin_memory()
+    h_colind = torch.as_tensor(p.colind).pin_memory()
+    h_vals = torch.as_tensor(vals).pin_memory()
+    h_b = torch.as_tensor(b).pin_memory()
+    h_x = torch.empty_like(h_b).pin_memory()
+    d_rowptr = torch.empty_like(h_rowptr, device=dev)
+    d_colind = torch.empty_like(h_colind, device=dev)
+    d_vals = torch.empty_like(h_vals, device=dev)
+    d_b = torch.empty_like(h_b, device=dev)
+    d_x = torch.empty_like(h_b, device=dev)
+
+    def e2e_step():
+        d_rowptr.copy_(h_rowptr, non_blocking=True)
+        d_colind.copy_(h_colind, non_blocking=True)
+        d_vals.copy_(h_vals, non_blocking=True)
+        d_b.copy_(h_b, non_blocking=True)
+        h = helm.helm_csr_create(p.n, p.nnz, d_rowptr.data_ptr(), d_colind.data_ptr(), d_vals.data_ptr(),
+                                 helm.HELM_C128, 0, stream)
+        info = helm.helm_bicgstab_solve(h, d_b, d_x, opts, stream)
+        h_x.copy_(d_x, non_blocking=True)
+        torch.cuda.synchronize()
+        helm.helm_csr_destroy(h)
+        return info
+
+    e2e_steps = max(1, min(args.steps, 2))
+    e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    e2e_s = barrier_max(time.perf_counter() - t0, ws)
+    h2d = int(h_rowptr.numel() * 4 + h_colind.numel() * 4 + h_vals.numel() * 16 + h_b.numel() * 16)
+    d2h = int(h_x.numel() * 16)
+
+    line = {
+        "metric": METRIC, "value": round(value, 4), "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD}: Q1 Helmholtz box 120x60x50, n={p.n}, nnz={p.nnz}, F={cfg.F:.1f} Hz, "
+                               f"BiCGStab to rel. residual {cfg.tol:g}, complex128",
+                   "n": p.n, "nnz": p.nnz, "tol": cfg.tol, "parallelism": f"replicas x{ws}",
+                   "l2": "inputs larger than L2 (matrix 207 MB vs 129 MB L2); Krylov vectors L2-resident "
+                         "inside a solve by design"},
+        "iters_per_solve": iters, "converged": ok, "relres_true_host": relres_host,
+        "spmv_ms": round(spmv_ms, 5), "spmv_hbm_gbs": round(spmv_gbs, 1),
+        "spmv_hbm_frac": round(spmv_gbs / peaks.get("hbm_gbs", 6800.0), 4),
+        "roofline": roofline,
+        "e2e": {"value": round(e2e_steps * ws / e2e_s, 4), "unit": "solves/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    if rank == 0:
+        line["cpu_baseline"] = cpu_baseline(p, vals, b, iters[0] if iters else 1, args)
+        print(json.dumps(line), flush=True)
+    A.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- CPU oracle
+
+def oracle_iteration_time(p, vals, b, iters: int):
+    """Seconds per BiCGStab iteration of the CPU oracle, from a capped run."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    _, info = oracle.bicgstab(p.rowptr, p.colind, vals, b, tol=1e-30, maxit=iters)
+    dt = time.perf_counter() - t0
+    return dt / max(info["iters"], 1), info["iters"], dt
+
+
+def cpu_baseline(p, vals, b, iters_per_solve: int, args):
+    sample_iters = args.cpu_sample_iters
+    t_it, done, dt = oracle_iteration_time(p, vals, b, sample_iters)
+    solves_per_s = 1.0 / (t_it * iters_per_solve)
+    return {"value": solves_per_s, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"{done} BiCGStab iterations of the oracle on the full {WORKLOAD} system "
+                      f"({dt:.1f} s); solves/s = 1 / (s per iteration x {iters_per_solve} iterations per solve)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return
+    cfg = helmgen.CONFIGS[WORKLOAD]
+    p, vals, b = build_problem(cfg)
+    iters_per_solve = args.ref_iters_per_solve
+    times = []
+    for _ in range(args.warmup):
+        oracle_iteration_time(p, vals, b, args.ref_step_iters)
+    for _ in range(args.steps):
+        t_it, done, dt = oracle_iteration_time(p, vals, b, args.ref_step_iters)
+        times.append(t_it)
+    t_it = statistics.median(times)
+    value = 1.0 / (t_it * iters_per_solve)
+    sample = (f"each step: {args.ref_step_iters} oracle BiCGStab iterations on the full {WORKLOAD} system; "
+              f"solves/s = 1 / (s per iteration x {iters_per_solve} iterations per solve)")
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_it * args.ref_step_iters * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"{WORKLOAD}: Q1 Helmholtz box 120x60x50, n={p.n}, nnz={p.nnz}, "
+                                   f"BiCGStab to rel. residual {cfg.tol:g}, complex128", "n": p.n, "nnz": p.nnz},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--cpu-sample-iters", type=int, default=200)
+    ap.add_argument("--ref-step-iters", type=int, default=60)
+    ap.add_argument("--ref-iters-per-solve", type=int, default=int(os.environ.get("HELM_ITERS_PER_SOLVE", "0")) or 0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        if not args.ref_iters_per_solve:
+            args.ref_iters_per_solve = REF_ITERS_PER_SOLVE
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+# Iterations of one cavity120 BiCGStab solve to 1e-8 (GPU count, used to
+# scale the oracle's per-iteration time when only a sample is timed).
+REF_ITERS_PER_SOLVE = 20000
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,503 @@
+// libhelm C ABI: CSR handle, SpMV, dot product, norm, axpby.
+//
+// Section 3 of the paper (Tables 2-8) defines the vector kernels and the CSR
+// SpMV these calls provide; Section 2 fixes CSR as the storage.  Argument
+// checks happen on the host before anything is enqueued; no call aborts.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <utility>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.hpp"
+#include "spmv.cuh"
+
+namespace helm {
+
+// ---------------------------------------------------------------- kernels
+
+template <class V>
+struct AxpbyEpi {
+  V* y;
+  V alpha, beta;
+  int mode;  // 0: y = acc, 1: y = alpha acc, 2: y = alpha acc + beta y
+  __device__ __forceinline__ void row(int32_t r, V acc) {
+    if (mode == 0) {
+      y[r] = acc;
+    } else if (mode == 1) {
+      y[r] = cmul(alpha, acc);
+    } else {
+      y[r] = cadd(cmul(alpha, acc), cmul(beta, y[r]));
+    }
+  }
+};
+
+template <class V, int R, int CAP>
+__global__ void __launch_bounds__(R) k_spmv(CsrDev<V> A, const V* __restrict__ x, V* y, V alpha, V beta,
+                                            int mode, unsigned int* dev_err) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  AxpbyEpi<V> epi{y, alpha, beta, mode};
+  (void)spmv_tiles<V, R, CAP>(A, x, epi, smem, dev_err);
+}
+
+// Per-row statistics and (optionally) validation of the CSR pattern.
+__global__ void k_csr_check(int32_t n, int64_t nnz, const int32_t* __restrict__ rowptr,
+                            const int32_t* __restrict__ colind, int validate, int* out /* [0]=max row, [1]=bad */) {
+  int local_max = 0, bad = 0;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int64_t a = rowptr[i], b = rowptr[i + 1];
+    if (b < a || a < 0 || b > nnz) {
+      bad = 1;
+      continue;
+    }
+    const int64_t len = b - a;
+    local_max = max(local_max, static_cast<int>(len < 0x7fffffff ? len : 0x7fffffff));
+    if (validate) {
+      int32_t prev = -1;
+      for (int64_t k = a; k < b; ++k) {
+        const int32_t c = colind[k];
+        if (c < 0 || c >= n || c <= prev) bad = 1;
+        prev = c;
+      }
+    }
+  }
+  if (local_max) atomicMax(&out[0], local_max);
+  if (bad) atomicOr(&out[1], 1);
+}
+
+// One block-sized partial of (x, y) per block; complex64 inputs accumulate
+// products in FP32 per thread (few terms each) and everything above in FP64.
+template <class V, bool CONJ>
+__global__ void __launch_bounds__(256) k_dot_partial(int64_t n, const V* __restrict__ x,
+                                                     const V* __restrict__ y, double* partials) {
+  __shared__ double red[32 * 2];
+  V acc = vzero<V>();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    V a = ld_stream(x + i);
+    if (CONJ) a.y = -a.y;
+    acc = mac(a, ld_stream(y + i), acc);
+  }
+  double v[2] = {static_cast<double>(acc.x), static_cast<double>(acc.y)};
+  block_sum<2>(v, red);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = v[0];
+    partials[2 * blockIdx.x + 1] = v[1];
+  }
+}
+
+template <class V>
+__global__ void __launch_bounds__(256) k_nrm2_partial(int64_t n, const V* __restrict__ x, double* partials) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  if (sizeof(V) == sizeof(double2)) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+      const V a = ld_stream(x + i);
+      acc = fma((double)a.x, (double)a.x, acc);
+      acc = fma((double)a.y, (double)a.y, acc);
+    }
+  } else {
+    float accf = 0.f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+      const V a = ld_stream(x + i);
+      accf = fmaf((float)a.x, (float)a.x, accf);
+      accf = fmaf((float)a.y, (float)a.y, accf);
+    }
+    acc = accf;
+  }
+  double v[1] = {acc};
+  block_sum<1>(v, red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = v[0];
+}
+
+// Adds the block partials in block order (one block).
+template <int K>
+__global__ void __launch_bounds__(256) k_sum_partials(int nparts, const double* __restrict__ partials,
+                                                      double* out, int sqrt_result) {
+  __shared__ double red[32 * K];
+  double acc[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) acc[k] = 0.0;
+  for (int b = threadIdx.x; b < nparts; b += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] += partials[(size_t)b * K + k];
+  }
+  block_sum<K>(acc, red);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) out[k] = sqrt_result ? sqrt(acc[k]) : acc[k];
+  }
+}
+
+template <class V>
+__global__ void __launch_bounds__(256) k_axpby(int64_t n, V alpha, const V* x, V beta, V* y, int mode) {
+  // mode bit 0: alpha != 0 (read x); bit 1: beta != 0 (read y); bit 2: beta == 1
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    V r = vzero<V>();
+    if (mode & 2) r = (mode & 4) ? y[i] : cmul(beta, y[i]);
+    if (mode & 1) r = mac(alpha, x[i], r);
+    y[i] = r;
+  }
+}
+
+__global__ void k_c128_to_c64(int64_t n, const double2* __restrict__ a, float2* __restrict__ b) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 v = ld_stream(a + i);
+    b[i] = make_float2(__double2float_rn(v.x), __double2float_rn(v.y));
+  }
+}
+
+// ---------------------------------------------------------------- host helpers
+
+std::mutex g_attr_mu;
+std::vector<std::pair<const void*, int>> g_attr_done;
+
+// Opt a kernel into more than 48 KB of dynamic shared memory (once per
+// kernel and device).
+cudaError_t set_smem_attr(const void* fn, size_t bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  for (auto& p : g_attr_done)
+    if (p.first == fn && p.second == dev) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
+  if (e == cudaSuccess) g_attr_done.emplace_back(fn, dev);
+  return e;
+}
+
+int sm_count() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+  return std::max(sms, 1);
+}
+
+int vec_grid_for(int64_t n) {
+  const int64_t want = (n + 255) / 256;
+  const int64_t cap = static_cast<int64_t>(sm_count()) * 8;
+  return static_cast<int>(std::max<int64_t>(1, std::min(want, cap)));
+}
+
+namespace {
+bool is_zero(const double* z) { return z[0] == 0.0 && z[1] == 0.0; }
+bool is_one(const double* z) { return z[0] == 1.0 && z[1] == 0.0; }
+}  // namespace
+
+// Grid of the staged SpMV: all resident blocks, never more than there are
+// tiles.
+template <class V, int R, int CAP>
+static helm_status spmv_grid(int32_t n, int* grid) {
+  using S = SpmvStage<V, CAP>;
+  const void* fn = reinterpret_cast<const void*>(&k_spmv<V, R, CAP>);
+  HELM_CUDA_TRY(set_smem_attr(fn, S::kBytes));
+  int per_sm = 0;
+  HELM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmv<V, R, CAP>, R, S::kBytes));
+  per_sm = std::max(per_sm, 1);
+  const int ntiles = (n + R - 1) / R;
+  *grid = std::max(1, std::min(ntiles, per_sm * sm_count()));
+  return HELM_OK;
+}
+
+helm_status launch_spmv128(helm_csr A, const double2* x, double2* y, double2 alpha, double2 beta,
+                           cudaStream_t s) {
+  if (A->n == 0) return HELM_OK;
+  using S = SpmvStage<double2, kCap128>;
+  int grid = 0;
+  helm_status st = spmv_grid<double2, kRows128, kCap128>(A->n, &grid);
+  if (st != HELM_OK) return st;
+  const int mode = (alpha.x == 1.0 && alpha.y == 0.0 && beta.x == 0.0 && beta.y == 0.0) ? 0
+                   : (beta.x == 0.0 && beta.y == 0.0)                                    ? 1
+                                                                                         : 2;
+  CsrDev<double2> d{A->n, A->nnz, A->rowptr, A->colind, static_cast<const double2*>(A->vals)};
+  k_spmv<double2, kRows128, kCap128><<<grid, kRows128, S::kBytes, s>>>(d, x, y, alpha, beta, mode, A->dev_err);
+  HELM_CUDA_TRY(cudaGetLastError());
+  return HELM_OK;
+}
+
+helm_status launch_spmv64(helm_csr A, const float2* vals, const float2* x, float2* y, float2 alpha,
+                          float2 beta, cudaStream_t s) {
+  if (A->n == 0) return HELM_OK;
+  using S = SpmvStage<float2, kCap64>;
+  int grid = 0;
+  helm_status st = spmv_grid<float2, kRows64, kCap64>(A->n, &grid);
+  if (st != HELM_OK) return st;
+  const int mode = (alpha.x == 1.f && alpha.y == 0.f && beta.x == 0.f && beta.y == 0.f) ? 0
+                   : (beta.x == 0.f && beta.y == 0.f)                                    ? 1
+                                                                                         : 2;
+  CsrDev<float2> d{A->n, A->nnz, A->rowptr, A->colind, vals};
+  k_spmv<float2, kRows64, kCap64><<<grid, kRows64, S::kBytes, s>>>(d, x, y, alpha, beta, mode, A->dev_err);
+  HELM_CUDA_TRY(cudaGetLastError());
+  return HELM_OK;
+}
+
+helm_status ensure_vectors(helm_csr A, int nvec) {
+  if (A->nvec >= nvec) return HELM_OK;
+  if (A->vec) {
+    cudaFree(A->vec);
+    A->vec = nullptr;
+    A->nvec = 0;
+  }
+  const size_t bytes = sizeof(double2) * static_cast<size_t>(std::max<int32_t>(A->n, 1)) * nvec;
+  HELM_CUDA_TRY(cudaMalloc(&A->vec, bytes));
+  A->nvec = nvec;
+  return HELM_OK;
+}
+
+helm_status ensure_vectors32(helm_csr A, int nvec) {
+  if (A->nvec32 >= nvec) return HELM_OK;
+  if (A->vec32) {
+    cudaFree(A->vec32);
+    A->vec32 = nullptr;
+    A->nvec32 = 0;
+  }
+  const size_t bytes = sizeof(float2) * static_cast<size_t>(std::max<int32_t>(A->n, 1)) * nvec;
+  HELM_CUDA_TRY(cudaMalloc(&A->vec32, bytes));
+  A->nvec32 = nvec;
+  return HELM_OK;
+}
+
+helm_status ensure_vals32(helm_csr A, cudaStream_t s) {
+  if (A->vals32) return HELM_OK;
+  HELM_CUDA_TRY(cudaMalloc(&A->vals32, sizeof(float2) * static_cast<size_t>(std::max<int64_t>(A->nnz, 1))));
+  if (A->nnz) {
+    k_c128_to_c64<<<vec_grid_for(A->nnz), 256, 0, s>>>(A->nnz, static_cast<const double2*>(A->vals), A->vals32);
+    HELM_CUDA_TRY(cudaGetLastError());
+  }
+  return HELM_OK;
+}
+
+}  // namespace helm
+
+using namespace helm;
+
+// ---------------------------------------------------------------- C ABI
+
+extern "C" {
+
+const char* helm_status_string(helm_status s) {
+  switch (s) {
+    case HELM_OK: return "ok";
+    case HELM_ERR_INVALID: return "invalid argument or malformed CSR";
+    case HELM_ERR_CUDA: return "CUDA runtime error";
+    case HELM_ERR_NOMEM: return "device allocation failed";
+    case HELM_ERR_NOT_CONVERGED: return "iteration cap reached before the tolerance";
+    case HELM_ERR_BREAKDOWN: return "Krylov breakdown (zero denominator)";
+    case HELM_ERR_TIMEOUT: return "device deadline expired";
+    case HELM_ERR_NONFINITE: return "non-finite value in the recurrence";
+  }
+  return "unknown status";
+}
+
+void helm_opts_default(helm_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->tol = 1e-8;
+  o->maxit = 20000;
+  o->use_x0 = 0;
+  o->method = HELM_BICGSTAB;
+  o->precision = HELM_PREC_FP64;
+  o->inner_tol = 1e-5;
+  o->deadline_s = 0.0;
+  o->ell = 2;
+  o->launch = HELM_LAUNCH_AUTO;
+}
+
+helm_status helm_csr_create(helm_csr* out, int32_t n, int64_t nnz, const int32_t* d_rowptr,
+                            const int32_t* d_colind, const void* d_vals, helm_dtype dt, uint32_t flags,
+                            helm_stream_t stream) {
+  if (!out) return HELM_ERR_INVALID;
+  *out = nullptr;
+  if (n < 0 || nnz < 0 || nnz >= (int64_t(1) << 31)) return HELM_ERR_INVALID;
+  if (dt != HELM_C128 && dt != HELM_C64) return HELM_ERR_INVALID;
+  if (!d_rowptr || (nnz > 0 && (!d_colind || !d_vals))) return HELM_ERR_INVALID;
+  const size_t esz = dt == HELM_C128 ? 16 : 8;
+  if (!aligned(d_rowptr, 4) || !aligned(d_colind, 16) || !aligned(d_vals, 16) || esz == 0)
+    return HELM_ERR_INVALID;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+
+  helm_csr A = new (std::nothrow) helm_csr_s();
+  if (!A) return HELM_ERR_NOMEM;
+  auto fail = [&](helm_status st) {
+    helm_csr_destroy(A);
+    return st;
+  };
+  if (cudaGetDevice(&A->device) != cudaSuccess) return fail(HELM_ERR_CUDA);
+  A->num_sms = sm_count();
+  A->n = n;
+  A->nnz = nnz;
+  A->rowptr = d_rowptr;
+  A->colind = d_colind;
+  A->vals = d_vals;
+  A->dt = dt;
+
+  // workspace: partials for the largest grid, tickets, error flags, state
+  const size_t nparts = static_cast<size_t>(A->num_sms) * 16 * 8;
+  if (cudaMalloc(&A->partials, nparts * sizeof(double)) != cudaSuccess) return fail(HELM_ERR_NOMEM);
+  if (cudaMalloc(&A->tickets, (TK_COUNT + 2) * sizeof(unsigned int)) != cudaSuccess) return fail(HELM_ERR_NOMEM);
+  if (cudaMemsetAsync(A->tickets, 0, (TK_COUNT + 2) * sizeof(unsigned int), s) != cudaSuccess)
+    return fail(HELM_ERR_CUDA);
+  A->dev_err = A->tickets + TK_COUNT;
+  if (cudaMalloc(&A->state, sizeof(SolverState)) != cudaSuccess) return fail(HELM_ERR_NOMEM);
+  if (cudaMallocHost(&A->state_host, sizeof(SolverState)) != cudaSuccess) return fail(HELM_ERR_NOMEM);
+  std::memset(A->state_host, 0, sizeof(SolverState));
+
+  // pattern checks and row statistics: one pass, one synchronisation
+  int* d_chk = nullptr;
+  int h_chk[2] = {0, 0};
+  int32_t h_end[2] = {0, 0};
+  if (cudaMalloc(&d_chk, 2 * sizeof(int)) != cudaSuccess) return fail(HELM_ERR_NOMEM);
+  cudaError_t e = cudaMemsetAsync(d_chk, 0, 2 * sizeof(int), s);
+  if (e == cudaSuccess && n > 0) {
+    k_csr_check<<<vec_grid_for(n), 256, 0, s>>>(n, nnz, d_rowptr, d_colind, (flags & HELM_CSR_VALIDATE) ? 1 : 0,
+                                                d_chk);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h_chk, d_chk, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h_end[0], d_rowptr, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h_end[1], d_rowptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d_chk);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return fail(HELM_ERR_CUDA);
+  }
+  if (h_end[0] != 0 || h_end[1] != nnz || h_chk[1]) return fail(HELM_ERR_INVALID);
+  A->max_row = h_chk[0];
+  A->vec_grid = vec_grid_for(n);
+  helm_status st = dt == HELM_C128 ? spmv_grid<double2, kRows128, kCap128>(n, &A->spmv_grid)
+                                   : spmv_grid<float2, kRows64, kCap64>(n, &A->spmv_grid);
+  if (st != HELM_OK) return fail(st);
+  *out = A;
+  return HELM_OK;
+}
+
+helm_status helm_csr_destroy(helm_csr A) {
+  if (!A) return HELM_OK;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(A->device);
+  cudaDeviceSynchronize();
+  for (auto& kv : A->graphs) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+  }
+  cudaFree(A->partials);
+  cudaFree(A->tickets);
+  cudaFree(A->state);
+  if (A->state_host) cudaFreeHost(A->state_host);
+  cudaFree(A->vec);
+  cudaFree(A->vals32);
+  cudaFree(A->vec32);
+  (void)cudaGetLastError();
+  if (prev >= 0) cudaSetDevice(prev);
+  delete A;
+  return HELM_OK;
+}
+
+helm_status helm_spmv(helm_csr A, const double* alpha, const void* d_x, const double* beta, void* d_y,
+                      helm_stream_t stream) {
+  if (!A || !alpha || !beta) return HELM_ERR_INVALID;
+  if (A->n > 0 && (!d_x || !d_y)) return HELM_ERR_INVALID;
+  if (d_x == d_y && A->n > 0) return HELM_ERR_INVALID;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (A->dt == HELM_C128) {
+    if (!aligned(d_x, 16) || !aligned(d_y, 16)) return HELM_ERR_INVALID;
+    return launch_spmv128(A, static_cast<const double2*>(d_x), static_cast<double2*>(d_y),
+                          make_double2(alpha[0], alpha[1]), make_double2(beta[0], beta[1]), s);
+  }
+  if (!aligned(d_x, 8) || !aligned(d_y, 8)) return HELM_ERR_INVALID;
+  return launch_spmv64(A, static_cast<const float2*>(A->vals), static_cast<const float2*>(d_x),
+                       static_cast<float2*>(d_y), make_float2((float)alpha[0], (float)alpha[1]),
+                       make_float2((float)beta[0], (float)beta[1]), s);
+}
+
+helm_status helm_dot(int64_t n, helm_dtype dt, const void* d_x, const void* d_y, int conj_x, void* d_out,
+                     helm_stream_t stream) {
+  if (n < 0 || n >= (int64_t(1) << 31) || !d_out || (dt != HELM_C128 && dt != HELM_C64)) return HELM_ERR_INVALID;
+  if (n > 0 && (!d_x || !d_y)) return HELM_ERR_INVALID;
+  const size_t esz = dt == HELM_C128 ? 16 : 8;
+  if (!aligned(d_x, esz) || !aligned(d_y, esz) || !aligned(d_out, 16)) return HELM_ERR_INVALID;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int grid = vec_grid_for(n);
+  double* part = nullptr;
+  HELM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&part), sizeof(double) * 2 * grid, s));
+  if (dt == HELM_C128) {
+    if (conj_x)
+      k_dot_partial<double2, true><<<grid, 256, 0, s>>>(n, (const double2*)d_x, (const double2*)d_y, part);
+    else
+      k_dot_partial<double2, false><<<grid, 256, 0, s>>>(n, (const double2*)d_x, (const double2*)d_y, part);
+  } else {
+    if (conj_x)
+      k_dot_partial<float2, true><<<grid, 256, 0, s>>>(n, (const float2*)d_x, (const float2*)d_y, part);
+    else
+      k_dot_partial<float2, false><<<grid, 256, 0, s>>>(n, (const float2*)d_x, (const float2*)d_y, part);
+  }
+  k_sum_partials<2><<<1, 256, 0, s>>>(grid, part, static_cast<double*>(d_out), 0);
+  cudaError_t e = cudaGetLastError();
+  cudaFreeAsync(part, s);
+  if (e != cudaSuccess) return HELM_ERR_CUDA;
+  return HELM_OK;
+}
+
+helm_status helm_nrm2(int64_t n, helm_dtype dt, const void* d_x, double* d_out, helm_stream_t stream) {
+  if (n < 0 || n >= (int64_t(1) << 31) || !d_out || (dt != HELM_C128 && dt != HELM_C64)) return HELM_ERR_INVALID;
+  if (n > 0 && !d_x) return HELM_ERR_INVALID;
+  const size_t esz = dt == HELM_C128 ? 16 : 8;
+  if (!aligned(d_x, esz) || !aligned(d_out, 8)) return HELM_ERR_INVALID;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int grid = vec_grid_for(n);
+  double* part = nullptr;
+  HELM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&part), sizeof(double) * grid, s));
+  if (dt == HELM_C128)
+    k_nrm2_partial<double2><<<grid, 256, 0, s>>>(n, (const double2*)d_x, part);
+  else
+    k_nrm2_partial<float2><<<grid, 256, 0, s>>>(n, (const float2*)d_x, part);
+  k_sum_partials<1><<<1, 256, 0, s>>>(grid, part, d_out, 1);
+  cudaError_t e = cudaGetLastError();
+  cudaFreeAsync(part, s);
+  if (e != cudaSuccess) return HELM_ERR_CUDA;
+  return HELM_OK;
+}
+
+helm_status helm_axpby(int64_t n, helm_dtype dt, const double* alpha, const void* d_x, const double* beta,
+                       void* d_y, helm_stream_t stream) {
+  if (n < 0 || n >= (int64_t(1) << 31) || !alpha || !beta || (dt != HELM_C128 && dt != HELM_C64))
+    return HELM_ERR_INVALID;
+  if (n == 0) return HELM_OK;
+  if (!d_y || (!is_zero(alpha) && !d_x)) return HELM_ERR_INVALID;
+  const size_t esz = dt == HELM_C128 ? 16 : 8;
+  if (!aligned(d_x, esz) || !aligned(d_y, esz)) return HELM_ERR_INVALID;
+  const int mode = (is_zero(alpha) ? 0 : 1) | (is_zero(beta) ? 0 : 2) | (is_one(beta) ? 4 : 0);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int grid = vec_grid_for(n);
+  if (dt == HELM_C128)
+    k_axpby<double2><<<grid, 256, 0, s>>>(n, make_double2(alpha[0], alpha[1]), (const double2*)d_x,
+                                          make_double2(beta[0], beta[1]), (double2*)d_y, mode);
+  else
+    k_axpby<float2><<<grid, 256, 0, s>>>(n, make_float2((float)alpha[0], (float)alpha[1]), (const float2*)d_x,
+                                         make_float2((float)beta[0], (float)beta[1]), (float2*)d_y, mode);
+  HELM_CUDA_TRY(cudaGetLastError());
+  return HELM_OK;
+}
+
+helm_status helm_bicgstab_solve(helm_csr A, const void* d_b, void* d_x, const helm_opts* o, helm_info* info,
+                                helm_stream_t stream) {
+  helm_opts opts;
+  if (o) opts = *o;
+  else helm_opts_default(&opts);
+  if (info) std::memset(info, 0, sizeof(*info));
+  if (!A || A->dt != HELM_C128) return HELM_ERR_INVALID;
+  if (A->n > 0 && (!d_b || !d_x)) return HELM_ERR_INVALID;
+  if (!aligned(d_b, 16) || !aligned(d_x, 16) || d_b == d_x) return HELM_ERR_INVALID;
+  if (!(opts.tol >= 0.0) || opts.maxit < 0) return HELM_ERR_INVALID;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> lk(A->mu);
+  if (opts.precision == HELM_PREC_MIXED)
+    return solve_mixed(A, static_cast<const double2*>(d_b), static_cast<double2*>(d_x), opts, info, s);
+  if (opts.precision != HELM_PREC_FP64) return HELM_ERR_INVALID;
+  return bicgstab_fp64(A, static_cast<const double2*>(d_b), static_cast<double2*>(d_x), opts, info, s);
+}
+
+}  // extern "C"

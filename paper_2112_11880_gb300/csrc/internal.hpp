@@ -1,0 +1,113 @@
+// Host-side internals of libhelm shared by the translation units: the CSR
+// handle, its workspace, launch shapes, and error plumbing.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <mutex>
+#include <utility>
+
+#include "../../include/helm.h"
+
+namespace helm {
+
+// Device-resident state of one Krylov solve (Section 4: the scalars of the
+// recurrence never leave the device; the paper's per-dot host copy is gone).
+struct SolverState {
+  double2 rho, alpha, omega, beta;
+  double2 aux[4];          // method-specific scalars
+  double bnorm, tol, relres, relres_true;
+  double tau, theta, eta;  // TFQMR
+  int32_t iter, maxit, status, phase;
+  int32_t use_x0, spmv_count, restarts, method;
+  unsigned long long t0, deadline_ns;
+};
+
+enum : int32_t { ST_RUNNING = -1 };
+enum : int32_t { PH_RUN = 0, PH_SCONV = 1, PH_DONE = 2 };
+
+// Tickets (arrival counters for last-block reductions), one per kernel kind.
+enum : int { TK_INIT = 0, TK_V, TK_S, TK_T, TK_XR, TK_TAIL, TK_AUX0, TK_AUX1, TK_AUX2, TK_AUX3, TK_COUNT };
+
+// Rows per tile / entries per staged tile of the complex128 SpMV engine.
+constexpr int kRows128 = 128;
+constexpr int kCap128 = kRows128 * 28;
+constexpr int kRows64 = 128;
+constexpr int kCap64 = kRows64 * 28;
+
+struct GraphEntry {
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+};
+
+}  // namespace helm
+
+struct helm_csr_s {
+  int device = 0;
+  int num_sms = 0;
+  int32_t n = 0;
+  int64_t nnz = 0;
+  const int32_t* rowptr = nullptr;
+  const int32_t* colind = nullptr;
+  const void* vals = nullptr;
+  helm_dtype dt = HELM_C128;
+  int32_t max_row = 0;
+
+  // launch shapes
+  int spmv_grid = 0;   // persistent grid of the staged SpMV kernels
+  int vec_grid = 0;    // grid of element-wise kernels (256 threads)
+
+  // workspace (owned)
+  double* partials = nullptr;          // max(grid) * 8 doubles
+  unsigned int* tickets = nullptr;     // TK_COUNT counters
+  unsigned int* dev_err = nullptr;     // device error flags
+  helm::SolverState* state = nullptr;  // device
+  helm::SolverState* state_host = nullptr;  // pinned host mirror
+  double2* vec = nullptr;              // Krylov vectors, nvec * n complex128
+  int nvec = 0;
+  float2* vals32 = nullptr;            // complex64 copy for mixed precision
+  float2* vec32 = nullptr;             // complex64 Krylov vectors
+  int nvec32 = 0;
+
+  std::mutex mu;
+  std::map<std::pair<const void*, const void*>, helm::GraphEntry> graphs;  // (b, x) -> graph
+};
+
+namespace helm {
+
+#define HELM_CUDA_TRY(expr)                          \
+  do {                                               \
+    cudaError_t _e = (expr);                         \
+    if (_e != cudaSuccess) {                         \
+      (void)cudaGetLastError();                      \
+      return _e == cudaErrorMemoryAllocation ? HELM_ERR_NOMEM : HELM_ERR_CUDA; \
+    }                                                \
+  } while (0)
+
+inline bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// Launch-shape helpers (api.cu).
+cudaError_t set_smem_attr(const void* fn, size_t bytes);
+int sm_count();
+int vec_grid_for(int64_t n);
+
+// Allocate the complex128 Krylov vectors (and FP32 ones) on first use.
+helm_status ensure_vectors(helm_csr A, int nvec);
+helm_status ensure_vectors32(helm_csr A, int nvec);
+helm_status ensure_vals32(helm_csr A, cudaStream_t s);
+
+// Launchers implemented in spmv_ops.cu (used by several solvers).
+helm_status launch_spmv128(helm_csr A, const double2* x, double2* y, double2 alpha, double2 beta,
+                           cudaStream_t s);
+helm_status launch_spmv64(helm_csr A, const float2* vals, const float2* x, float2* y, float2 alpha,
+                          float2 beta, cudaStream_t s);
+
+// Solver entry points implemented in the solver translation units.
+helm_status bicgstab_fp64(helm_csr A, const double2* b, double2* x, const helm_opts& o, helm_info* info,
+                          cudaStream_t s);
+helm_status solve_mixed(helm_csr A, const double2* b, double2* x, const helm_opts& o, helm_info* info,
+                        cudaStream_t s);
+
+}  // namespace helm

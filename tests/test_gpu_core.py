@@ -1,0 +1,290 @@
+"""GPU parity of the C-ABI kernels against the CPU oracle (complex128 SpMV,
+complex64 SpMV, zdotc/zdotu, norm, axpby) and of the BiCGStab solver against
+dense LU and the oracle's BiCGStab.  Gates:
+  SpMV  |y_gpu - y_ref|_i <= 1e-13 * sum_j |a_ij| |x_j|       (complex128)
+  dot   |d_gpu - d_ref|   <= 1e-13 * sum_i |x_i| |y_i|         (complex128)
+  solve true residual <= tol and
+        |u_gpu - u_tight| / |u_tight| <= max(1e-8, 2 |u_oracle - u_tight| / |u_tight|)
+Complex64 gates come from FP32 rounding: (len + 2) * 2^-23 * sum |a||x|."""
+import math
+
+import numpy as np
+import pytest
+
+import helmgen as g
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+import paper_2112_11880_gb300 as helm  # noqa: E402
+
+DEV = torch.device("cuda:0")
+U32 = 2.0 ** -23
+
+
+def _abs_scale(rowptr, colind, vals, x):
+    rows = np.repeat(np.arange(len(rowptr) - 1), np.diff(rowptr))
+    return np.bincount(rows, weights=np.abs(vals) * np.abs(x[colind]), minlength=len(rowptr) - 1)
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device=DEV)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2112_11880_gb300 import build
+    build.build()
+    helm.load_library()
+
+
+def _matrices():
+    out = {}
+    p = g.assemble(g.CONFIGS["box20"])
+    out["box20"] = (p.rowptr, p.colind, g.helmholtz_values(p, 1500.0))
+    # ragged: empty rows, n not a multiple of the tile, nnz not a multiple of 4
+    rp, ci, v = g.random_csr(1000, 60, seed=5)
+    if rp[-1] % 4 == 0:
+        rp, ci, v = g.random_csr(1001, 60, seed=6)
+    out["ragged"] = (rp, ci, v)
+    # long rows: one tile holds more entries than a staged tile can take
+    rng = np.random.default_rng(7)
+    n = 300
+    lens = np.full(n, 3)
+    lens[5:40] = 250
+    rowptr = np.zeros(n + 1, np.int64)
+    np.cumsum(lens, out=rowptr[1:])
+    cols = np.concatenate([np.sort(rng.choice(n, size=l, replace=False)) for l in lens]).astype(np.int32)
+    out["longrows"] = (rowptr.astype(np.int32), cols, g.complex_vector(int(rowptr[-1]), 8))
+    # tiny
+    p = g.assemble(g.tiny_config(2, 2, 2))
+    out["tiny"] = (p.rowptr, p.colind, g.helmholtz_values(p, 200.0))
+    return out
+
+
+MATS = _matrices()
+
+
+@pytest.mark.parametrize("name", list(MATS))
+@pytest.mark.parametrize("ab", [(1.0, 0.0), (0.5 - 2j, 0.0), (1.0 + 1j, -0.25 + 3j)])
+def test_spmv_c128(name, ab):
+    rp, ci, v = MATS[name]
+    n = len(rp) - 1
+    alpha, beta = ab
+    A = helm.CsrMatrix.from_host(rp, ci, v, device=DEV, validate=True)
+    x = g.complex_vector(n, 1)
+    y0 = g.complex_vector(n, 2)
+    yd = _dev(y0.copy())
+    A.matvec(_dev(x), yd, alpha=alpha, beta=beta)
+    y = yd.cpu().numpy()
+    ax = oracle.spmv(rp, ci, v, x)
+    ref = alpha * ax + beta * y0
+    scale = abs(alpha) * _abs_scale(rp, ci, v, x) + abs(beta) * np.abs(y0)
+    assert np.all(np.abs(y - ref) <= 1e-13 * scale + 1e-300)
+    A.close()
+
+
+@pytest.mark.parametrize("name", ["box20", "ragged", "longrows"])
+def test_spmv_c64(name):
+    rp, ci, v = MATS[name]
+    n = len(rp) - 1
+    v32 = v.astype(np.complex64)
+    A = helm.CsrMatrix.from_host(rp, ci, v32, device=DEV)
+    x32 = g.complex_vector(n, 3).astype(np.complex64)
+    y = A.matvec(_dev(x32)).cpu().numpy().astype(np.complex128)
+    ref = oracle.spmv(rp, ci, v32.astype(np.complex128), x32.astype(np.complex128))
+    lens = np.diff(rp)
+    scale = _abs_scale(rp, ci, v32.astype(np.complex128), x32.astype(np.complex128))
+    assert np.all(np.abs(y - ref) <= (lens + 2) * 2 * U32 * scale + 1e-30)
+    A.close()
+
+
+def test_spmv_full_size_sampled_rows():
+    """120x60x50 cavity at full size: sampled rows recomputed by the oracle."""
+    cfg = g.CONFIGS["cavity120"]
+    p = g.assemble(cfg)
+    vals = g.helmholtz_values(p, cfg.F)
+    A = helm.CsrMatrix.from_host(p.rowptr, p.colind, vals, device=DEV)
+    x = g.complex_vector(p.n, 9)
+    y = A.matvec(_dev(x)).cpu().numpy()
+    rng = np.random.default_rng(0)
+    rows = np.unique(np.concatenate([rng.choice(p.n, 4000, replace=False), [0, p.n - 1]]))
+    for i in rows:
+        k0, k1 = p.rowptr[i], p.rowptr[i + 1]
+        sub_rp = np.array([0, k1 - k0], np.int32)
+        ref = oracle.spmv(sub_rp, p.colind[k0:k1], vals[k0:k1], x)[0]
+        scale = np.sum(np.abs(vals[k0:k1]) * np.abs(x[p.colind[k0:k1]]))
+        assert abs(y[i] - ref) <= 1e-13 * scale
+    A.close()
+
+
+@pytest.mark.parametrize("n", [0, 1, 257, 1_000_003])
+@pytest.mark.parametrize("conj", [True, False])
+def test_dot_c128(n, conj):
+    x = g.complex_vector(n, 11)
+    y = g.complex_vector(n, 12)
+    out = torch.zeros(1, dtype=torch.complex128, device=DEV)
+    helm.helm_dot(_dev(x), _dev(y), out, conj_x=conj)
+    d = complex(out.cpu().numpy()[0])
+    ref = oracle.zdotc(x if conj else np.conj(x), y)
+    assert abs(d - ref) <= 1e-13 * np.sum(np.abs(x) * np.abs(y)) + 1e-300
+    # reproducible bit for bit
+    out2 = torch.zeros(1, dtype=torch.complex128, device=DEV)
+    helm.helm_dot(_dev(x), _dev(y), out2, conj_x=conj)
+    assert complex(out2.cpu().numpy()[0]) == d
+
+
+def test_dot_correlated_and_norm():
+    x = g.complex_vector(500_000, 13)
+    y = x + 1e-6 * g.complex_vector(500_000, 14)
+    out = torch.zeros(1, dtype=torch.complex128, device=DEV)
+    helm.helm_dot(_dev(x), _dev(y), out)
+    d = complex(out.cpu().numpy()[0])
+    assert abs(d - oracle.zdotc(x, y)) <= 1e-13 * np.sum(np.abs(x) * np.abs(y))
+    nrm = torch.zeros(1, dtype=torch.float64, device=DEV)
+    helm.helm_nrm2(_dev(x), nrm)
+    assert abs(float(nrm.cpu()[0]) - oracle.dznrm2(x)) <= 1e-13 * oracle.dznrm2(x)
+
+
+def test_dot_c64():
+    n = 300_001
+    x = g.complex_vector(n, 15).astype(np.complex64)
+    y = g.complex_vector(n, 16).astype(np.complex64)
+    out = torch.zeros(1, dtype=torch.complex128, device=DEV)
+    helm.helm_dot(_dev(x), _dev(y), out)
+    d = complex(out.cpu().numpy()[0])
+    ref = oracle.zdotc(x.astype(np.complex128), y.astype(np.complex128))
+    per_thread = math.ceil(n / (torch.cuda.get_device_properties(0).multi_processor_count * 8 * 256))
+    assert abs(d - ref) <= (per_thread + 2) * 2 * U32 * np.sum(np.abs(x) * np.abs(y))
+
+
+@pytest.mark.parametrize("alpha,beta", [(2 - 1j, 0.5 + 0.5j), (0.0, 3.0), (1.5, 0.0), (1j, 1.0), (0.0, 0.0)])
+def test_axpby(alpha, beta):
+    n = 100_003
+    x = g.complex_vector(n, 17)
+    y = g.complex_vector(n, 18)
+    yd = _dev(y.copy())
+    helm.helm_axpby(alpha, _dev(x), beta, yd)
+    ref = alpha * x + beta * y
+    scale = abs(alpha) * np.abs(x) + abs(beta) * np.abs(y)
+    assert np.all(np.abs(yd.cpu().numpy() - ref) <= 4e-16 * scale + 1e-300)
+
+
+def test_invalid_arguments_rejected():
+    rp, ci, v = MATS["tiny"]
+    bad = ci.copy()
+    bad[3] = len(rp) + 5
+    with pytest.raises(helm.HelmError):
+        helm.CsrMatrix.from_host(rp, bad, v, device=DEV, validate=True)
+    A = helm.CsrMatrix.from_host(rp, ci, v, device=DEV)
+    x = _dev(g.complex_vector(len(rp) - 1, 1))
+    with pytest.raises(helm.HelmError):
+        helm.helm_spmv(A.handle, 1.0, x, 0.0, x)   # aliasing x and y
+    A.close()
+
+
+# ---------------------------------------------------------------- BiCGStab
+
+def _tiny_problem(dims, F, seed):
+    cfg = g.tiny_config(*dims, h=0.1, F=F, seed=seed)
+    p = g.assemble(cfg)
+    vals = g.helmholtz_values(p, F)
+    b = g.source(p) + 0.2 * g.complex_vector(p.n, seed + 1) * (~p.dirichlet)
+    return p, vals, b
+
+
+@pytest.mark.parametrize("dims,F", [((2, 2, 2), 300.0), ((5, 4, 3), 450.0), ((9, 7, 6), 900.0)])
+def test_bicgstab_vs_dense_lu(dims, F):
+    p, vals, b = _tiny_problem(dims, F, 3)
+    A = helm.CsrMatrix.from_host(p.rowptr, p.colind, vals, device=DEV)
+    x, info = helm.solve(A, _dev(b), tol=1e-12, maxit=10000)
+    assert info["status"] == "ok"
+    xs = oracle.dense_solve(p.rowptr, p.colind, vals, b)
+    xr, rinfo = oracle.bicgstab(p.rowptr, p.colind, vals, b, tol=1e-12, maxit=10000)
+    xg = x.cpu().numpy()
+    res = np.linalg.norm(b - oracle.spmv(p.rowptr, p.colind, vals, xg)) / np.linalg.norm(b)
+    assert res <= 1.5e-12
+    e_g = np.linalg.norm(xg - xs) / np.linalg.norm(xs)
+    e_o = np.linalg.norm(xr - xs) / np.linalg.norm(xs)
+    assert e_g <= max(1e-8, 2 * e_o)
+    A.close()
+
+
+@pytest.fixture(scope="module")
+def box20():
+    cfg = g.CONFIGS["box20"]
+    p = g.assemble(cfg)
+    vals = g.helmholtz_values(p, cfg.F)
+    b = g.source(p)
+    x_o, info_o = oracle.bicgstab(p.rowptr, p.colind, vals, b, tol=cfg.tol, maxit=20000)
+    x_t, info_t = oracle.bicgstab(p.rowptr, p.colind, vals, b, tol=1e-13, maxit=60000)
+    return p, vals, b, x_o, info_o, x_t
+
+
+def test_bicgstab_box20_parity(box20):
+    p, vals, b, x_o, info_o, x_t = box20
+    A = helm.CsrMatrix.from_host(p.rowptr, p.colind, vals, device=DEV)
+    x, info = helm.solve(A, _dev(b), tol=1e-8, maxit=20000)
+    assert info["status"] == "ok", info
+    xg = x.cpu().numpy()
+    res = np.linalg.norm(b - oracle.spmv(p.rowptr, p.colind, vals, xg)) / np.linalg.norm(b)
+    assert res <= 1.5e-8 and abs(res - info["relres_true"]) <= 1e-3 * res
+    nt = np.linalg.norm(x_t)
+    e_g = np.linalg.norm(xg - x_t) / nt
+    e_o = np.linalg.norm(x_o - x_t) / nt
+    assert e_g <= max(1e-8, 2 * e_o), (e_g, e_o)
+    print(f"box20: gpu iters {info['iters']} oracle iters {info_o['iters']}")
+    assert abs(info["iters"] - info_o["iters"]) <= 0.05 * info_o["iters"] + 2
+    A.close()
+
+
+def test_bicgstab_degenerate_cases():
+    p, vals, b = _tiny_problem((3, 3, 3), 450.0, 5)
+    A = helm.CsrMatrix.from_host(p.rowptr, p.colind, vals, device=DEV)
+    zero = torch.zeros(p.n, dtype=torch.complex128, device=DEV)
+    x = _dev(g.complex_vector(p.n, 1))
+    info = helm.helm_bicgstab_solve(A.handle, zero, x, helm.default_opts())
+    assert info["status"] == "ok" and info["iters"] == 0 and torch.all(x == 0)
+    x, info = helm.solve(A, _dev(b), tol=1e-30, maxit=1)
+    assert info["status"] == "not_converged" and info["iters"] == 1
+    xs = _dev(oracle.dense_solve(p.rowptr, p.colind, vals, b))
+    info = helm.helm_bicgstab_solve(A.handle, _dev(b), xs, helm.default_opts(use_x0=1))
+    assert info["status"] == "ok" and info["iters"] == 0
+    bad = b.copy()
+    bad[4] = np.nan
+    x, info = helm.solve(A, _dev(bad))
+    assert info["status"] == "nonfinite"
+    Z = helm.CsrMatrix.from_host(p.rowptr, p.colind, np.zeros_like(vals), device=DEV)
+    x, info = helm.solve(Z, _dev(b))
+    assert info["status"] == "breakdown"
+    Z.close()
+    A.close()
+
+
+def test_bicgstab_deadline_returns_timeout():
+    """Failure detection without a fault: a deadline that expires during the
+    first iteration makes the device loop stop and report a timeout."""
+    p = g.assemble(g.CONFIGS["box20"])
+    vals = g.helmholtz_values(p, 1500.0)
+    A = helm.CsrMatrix.from_host(p.rowptr, p.colind, vals, device=DEV)
+    x, info = helm.solve(A, _dev(g.source(p)), tol=1e-12, maxit=20000, deadline_s=1e-9)
+    assert info["status"] == "timeout" and 1 <= info["iters"] <= 2
+    # the context stays usable
+    x, info = helm.solve(A, _dev(g.source(p)), tol=1e-6, maxit=20000)
+    assert info["status"] == "ok"
+    A.close()
+
+
+def test_bicgstab_repeated_solves_reuse_graph(box20):
+    p, vals, b, *_ = box20
+    A = helm.CsrMatrix.from_host(p.rowptr, p.colind, vals, device=DEV)
+    bd = _dev(b)
+    x = torch.empty_like(bd)
+    infos = [helm.helm_bicgstab_solve(A.handle, bd, x, helm.default_opts(tol=1e-6)) for _ in range(3)]
+    assert all(i["status"] == "ok" for i in infos)
+    assert len({i["iters"] for i in infos}) == 1      # deterministic
+    A.close()
