@@ -142,7 +142,10 @@ typedef enum {
 typedef enum {
   HELM_LAUNCH_AUTO = 0,
   HELM_LAUNCH_GRAPH = 1,      /* CUDA graph with a device-driven while node */
-  HELM_LAUNCH_PERSISTENT = 2  /* one cooperative kernel with grid barriers */
+  HELM_LAUNCH_PERSISTENT = 2, /* one cooperative kernel with grid barriers */
+  HELM_LAUNCH_HOST = 3        /* host-driven loop of the same kernels, state
+                                 polled every 16 iterations (profiling: tools
+                                 that cannot see inside conditional graphs) */
 } helm_launch;
 
 typedef struct {

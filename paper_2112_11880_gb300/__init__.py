@@ -42,6 +42,7 @@ HELM_PREC_MIXED = 1
 HELM_LAUNCH_AUTO = 0
 HELM_LAUNCH_GRAPH = 1
 HELM_LAUNCH_PERSISTENT = 2
+HELM_LAUNCH_HOST = 3
 
 
 class helm_opts(ctypes.Structure):

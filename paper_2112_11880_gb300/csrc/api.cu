@@ -34,12 +34,28 @@ struct AxpbyEpi {
   }
 };
 
-template <class V, int R, int CAP>
-__global__ void __launch_bounds__(R) k_spmv(CsrDev<V> A, const V* __restrict__ x, V* y, V alpha, V beta,
-                                            int mode, unsigned int* dev_err) {
+template <class V>
+__global__ void __launch_bounds__(Engine<V>::R) k_spmv(CsrDev<V> A, const V* __restrict__ x, V* y, V alpha, V beta,
+                                                       int mode, unsigned int* dev_err) {
   extern __shared__ __align__(16) unsigned char smem[];
   AxpbyEpi<V> epi{y, alpha, beta, mode};
-  (void)spmv_tiles<V, R, CAP>(A, x, epi, smem, dev_err);
+  (void)spmv_run<V>(A, x, epi, smem, dev_err);
+}
+
+// real_blk[b] = 1 when every entry of rows [32 b, 32 b + 32) is real.
+__global__ void k_real_blocks(int32_t n, const int32_t* __restrict__ rowptr, const double2* __restrict__ vals,
+                              uint8_t* __restrict__ real_blk) {
+  const int32_t nblk = (n + 31) / 32;
+  for (int32_t blk = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); blk < nblk;
+       blk += gridDim.x * (blockDim.x / 32)) {
+    const int32_t r0 = blk * 32, r1 = min(r0 + 32, n);
+    const int64_t k0 = rowptr[r0], k1 = rowptr[r1];
+    bool real = true;
+    for (int64_t k = k0 + (threadIdx.x & 31); k < k1; k += 32)
+      if (reinterpret_cast<const double*>(vals)[2 * k + 1] != 0.0) real = false;
+    real = __all_sync(0xffffffffu, real);
+    if ((threadIdx.x & 31) == 0) real_blk[blk] = real ? 1 : 0;
+  }
 }
 
 // Per-row statistics and (optionally) validation of the CSR pattern.
@@ -187,13 +203,13 @@ bool is_one(const double* z) { return z[0] == 1.0 && z[1] == 0.0; }
 
 // Grid of the staged SpMV: all resident blocks, never more than there are
 // tiles.
-template <class V, int R, int CAP>
+template <class V>
 static helm_status spmv_grid(int32_t n, int* grid) {
-  using S = SpmvStage<V, CAP>;
-  const void* fn = reinterpret_cast<const void*>(&k_spmv<V, R, CAP>);
-  HELM_CUDA_TRY(set_smem_attr(fn, S::kBytes));
+  constexpr int R = Engine<V>::R;
+  const void* fn = reinterpret_cast<const void*>(&k_spmv<V>);
+  HELM_CUDA_TRY(set_smem_attr(fn, Engine<V>::kSmem));
   int per_sm = 0;
-  HELM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmv<V, R, CAP>, R, S::kBytes));
+  HELM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmv<V>, R, Engine<V>::kSmem));
   per_sm = std::max(per_sm, 1);
   const int ntiles = (n + R - 1) / R;
   *grid = std::max(1, std::min(ntiles, per_sm * sm_count()));
@@ -203,15 +219,14 @@ static helm_status spmv_grid(int32_t n, int* grid) {
 helm_status launch_spmv128(helm_csr A, const double2* x, double2* y, double2 alpha, double2 beta,
                            cudaStream_t s) {
   if (A->n == 0) return HELM_OK;
-  using S = SpmvStage<double2, kCap128>;
   int grid = 0;
-  helm_status st = spmv_grid<double2, kRows128, kCap128>(A->n, &grid);
+  helm_status st = spmv_grid<double2>(A->n, &grid);
   if (st != HELM_OK) return st;
   const int mode = (alpha.x == 1.0 && alpha.y == 0.0 && beta.x == 0.0 && beta.y == 0.0) ? 0
                    : (beta.x == 0.0 && beta.y == 0.0)                                    ? 1
                                                                                          : 2;
-  CsrDev<double2> d{A->n, A->nnz, A->rowptr, A->colind, static_cast<const double2*>(A->vals)};
-  k_spmv<double2, kRows128, kCap128><<<grid, kRows128, S::kBytes, s>>>(d, x, y, alpha, beta, mode, A->dev_err);
+  CsrDev<double2> d{A->n, A->nnz, A->rowptr, A->colind, static_cast<const double2*>(A->vals), A->real_blk};
+  k_spmv<double2><<<grid, Engine<double2>::R, Engine<double2>::kSmem, s>>>(d, x, y, alpha, beta, mode, A->dev_err);
   HELM_CUDA_TRY(cudaGetLastError());
   return HELM_OK;
 }
@@ -219,15 +234,14 @@ helm_status launch_spmv128(helm_csr A, const double2* x, double2* y, double2 alp
 helm_status launch_spmv64(helm_csr A, const float2* vals, const float2* x, float2* y, float2 alpha,
                           float2 beta, cudaStream_t s) {
   if (A->n == 0) return HELM_OK;
-  using S = SpmvStage<float2, kCap64>;
   int grid = 0;
-  helm_status st = spmv_grid<float2, kRows64, kCap64>(A->n, &grid);
+  helm_status st = spmv_grid<float2>(A->n, &grid);
   if (st != HELM_OK) return st;
   const int mode = (alpha.x == 1.f && alpha.y == 0.f && beta.x == 0.f && beta.y == 0.f) ? 0
                    : (beta.x == 0.f && beta.y == 0.f)                                    ? 1
                                                                                          : 2;
-  CsrDev<float2> d{A->n, A->nnz, A->rowptr, A->colind, vals};
-  k_spmv<float2, kRows64, kCap64><<<grid, kRows64, S::kBytes, s>>>(d, x, y, alpha, beta, mode, A->dev_err);
+  CsrDev<float2> d{A->n, A->nnz, A->rowptr, A->colind, vals, nullptr};
+  k_spmv<float2><<<grid, Engine<float2>::R, Engine<float2>::kSmem, s>>>(d, x, y, alpha, beta, mode, A->dev_err);
   HELM_CUDA_TRY(cudaGetLastError());
   return HELM_OK;
 }
@@ -333,15 +347,17 @@ helm_status helm_csr_create(helm_csr* out, int32_t n, int64_t nnz, const int32_t
   A->dt = dt;
 
   // workspace: partials for the largest grid, tickets, error flags, state
-  const size_t nparts = static_cast<size_t>(A->num_sms) * 16 * 8;
+  const size_t nparts = static_cast<size_t>(A->num_sms) * 32 * 8;  // <= 32 blocks/SM x 8 sums
   if (cudaMalloc(&A->partials, nparts * sizeof(double)) != cudaSuccess) return fail(HELM_ERR_NOMEM);
   if (cudaMalloc(&A->tickets, (TK_COUNT + 2) * sizeof(unsigned int)) != cudaSuccess) return fail(HELM_ERR_NOMEM);
   if (cudaMemsetAsync(A->tickets, 0, (TK_COUNT + 2) * sizeof(unsigned int), s) != cudaSuccess)
     return fail(HELM_ERR_CUDA);
   A->dev_err = A->tickets + TK_COUNT;
-  if (cudaMalloc(&A->state, sizeof(SolverState)) != cudaSuccess) return fail(HELM_ERR_NOMEM);
-  if (cudaMallocHost(&A->state_host, sizeof(SolverState)) != cudaSuccess) return fail(HELM_ERR_NOMEM);
-  std::memset(A->state_host, 0, sizeof(SolverState));
+  // two solver states: [0] the Krylov loop, [1] an outer loop (refinement)
+  if (cudaMalloc(&A->state, 2 * sizeof(SolverState)) != cudaSuccess) return fail(HELM_ERR_NOMEM);
+  if (cudaMemsetAsync(A->state, 0, 2 * sizeof(SolverState), s) != cudaSuccess) return fail(HELM_ERR_CUDA);
+  if (cudaMallocHost(&A->state_host, 2 * sizeof(SolverState)) != cudaSuccess) return fail(HELM_ERR_NOMEM);
+  std::memset(A->state_host, 0, 2 * sizeof(SolverState));
 
   // pattern checks and row statistics: one pass, one synchronisation
   int* d_chk = nullptr;
@@ -366,9 +382,14 @@ helm_status helm_csr_create(helm_csr* out, int32_t n, int64_t nnz, const int32_t
   if (h_end[0] != 0 || h_end[1] != nnz || h_chk[1]) return fail(HELM_ERR_INVALID);
   A->max_row = h_chk[0];
   A->vec_grid = vec_grid_for(n);
-  helm_status st = dt == HELM_C128 ? spmv_grid<double2, kRows128, kCap128>(n, &A->spmv_grid)
-                                   : spmv_grid<float2, kRows64, kCap64>(n, &A->spmv_grid);
+  helm_status st = dt == HELM_C128 ? spmv_grid<double2>(n, &A->spmv_grid) : spmv_grid<float2>(n, &A->spmv_grid);
   if (st != HELM_OK) return fail(st);
+  if (dt == HELM_C128 && n > 0) {
+    // rows blocks with only real entries take the cheaper product
+    if (cudaMalloc(&A->real_blk, (n + 31) / 32) != cudaSuccess) return fail(HELM_ERR_NOMEM);
+    k_real_blocks<<<vec_grid_for(n / 32 + 1), 256, 0, s>>>(n, d_rowptr, static_cast<const double2*>(d_vals), A->real_blk);
+    if (cudaGetLastError() != cudaSuccess) return fail(HELM_ERR_CUDA);
+  }
   *out = A;
   return HELM_OK;
 }
@@ -389,6 +410,7 @@ helm_status helm_csr_destroy(helm_csr A) {
   if (A->state_host) cudaFreeHost(A->state_host);
   cudaFree(A->vec);
   cudaFree(A->vals32);
+  cudaFree(A->real_blk);
   cudaFree(A->vec32);
   (void)cudaGetLastError();
   if (prev >= 0) cudaSetDevice(prev);

@@ -82,6 +82,27 @@ __device__ __forceinline__ float2 cfma32(float2 a, float2 b, float2 acc) {
   return acc;
 }
 
+// complex64 counterparts (FP32 pipe)
+__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 acc) { return cfma32(a, b, acc); }
+__device__ __forceinline__ float2 cfms(float2 a, float2 b, float2 acc) {
+  acc.x = fmaf(-a.x, b.x, acc.x);
+  acc.x = fmaf(a.y, b.y, acc.x);
+  acc.y = fmaf(-a.x, b.y, acc.y);
+  acc.y = fmaf(-a.y, b.x, acc.y);
+  return acc;
+}
+__device__ __forceinline__ float2 cfma_conj(float2 a, float2 b, float2 acc) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(-a.y, b.x, acc.y);
+  return acc;
+}
+__device__ __forceinline__ float cabs2_acc(float2 a, float acc) {
+  acc = fmaf(a.x, a.x, acc);
+  return fmaf(a.y, a.y, acc);
+}
+
 // ---------------------------------------------------------------- loads
 
 // Matrix entries are read once per SpMV: stream them (evict-first).
@@ -144,15 +165,31 @@ __device__ __forceinline__ bool grid_sum_last(double (&v)[K], double* partials,
   __syncthreads();
   if (!s_last) return false;
   __threadfence();
-  double acc[K];
+  // Thread j sums partials j + T (4 m + q) into accumulator q, then adds the
+  // four accumulators in order: a fixed order for every addition (four
+  // independent FP64 chains hide the DADD latency); the block tree follows.
+  double acc[K], acc4[4][K];
 #pragma unroll
-  for (int k = 0; k < K; ++k) acc[k] = 0.0;
-  // Thread j sums partials j, j+T, j+2T, ... in order; the block tree and
-  // the in-order warp sum fix the order of every addition.
-  for (unsigned int b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+  for (int q = 0; q < 4; ++q)
 #pragma unroll
-    for (int k = 0; k < K; ++k) acc[k] += ld_cg(&partials[(size_t)b * K + k]);
+    for (int k = 0; k < K; ++k) acc4[q][k] = 0.0;
+  const unsigned int T = blockDim.x;
+  unsigned int b = threadIdx.x;
+  for (; b + 3 * T < gridDim.x; b += 4 * T) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int k = 0; k < K; ++k) acc4[q][k] += ld_cg(&partials[(size_t)(b + q * T) * K + k]);
   }
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    if (b + q * T < gridDim.x) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) acc4[q][k] += ld_cg(&partials[(size_t)(b + q * T) * K + k]);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) acc[k] = (acc4[0][k] + acc4[1][k]) + (acc4[2][k] + acc4[3][k]);
   block_sum<K>(acc, red);
 #pragma unroll
   for (int k = 0; k < K; ++k) tot[k] = acc[k];

@@ -31,11 +31,15 @@ enum : int32_t { PH_RUN = 0, PH_SCONV = 1, PH_DONE = 2 };
 // Tickets (arrival counters for last-block reductions), one per kernel kind.
 enum : int { TK_INIT = 0, TK_V, TK_S, TK_T, TK_XR, TK_TAIL, TK_AUX0, TK_AUX1, TK_AUX2, TK_AUX3, TK_COUNT };
 
-// Rows per tile / entries per staged tile of the complex128 SpMV engine.
-constexpr int kRows128 = 128;
+// SpMV engine shape (measured on GB300, 120x60x50 Q1 matrix): one warp per
+// block, 32-row tiles of up to 28 entries per row staged by one TMA bulk copy
+// each, a single buffer per block and 12 (complex128) to 19 (complex64)
+// blocks per SM overlapping one another.
+constexpr int kRows128 = 32;
 constexpr int kCap128 = kRows128 * 28;
-constexpr int kRows64 = 128;
+constexpr int kRows64 = 32;
 constexpr int kCap64 = kRows64 * 28;
+constexpr int kStages = 1;
 
 struct GraphEntry {
   cudaGraphExec_t exec = nullptr;
@@ -68,6 +72,7 @@ struct helm_csr_s {
   double2* vec = nullptr;              // Krylov vectors, nvec * n complex128
   int nvec = 0;
   float2* vals32 = nullptr;            // complex64 copy for mixed precision
+  uint8_t* real_blk = nullptr;         // per 32-row block: all entries real
   float2* vec32 = nullptr;             // complex64 Krylov vectors
   int nvec32 = 0;
 

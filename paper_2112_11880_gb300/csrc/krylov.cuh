@@ -1,0 +1,534 @@
+// BiCGStab kernels with device-resident scalars, generic over the vector
+// precision (complex128 for the FP64 solver, complex64 for the inner solve of
+// mixed precision).  Section 4 of the paper: P-BiCGSTAB with residual
+// tolerance, zero initial guess and an iteration cap; identity
+// preconditioner; the recurrence of van der Vorst 1992 / Saad 2003
+// Algorithm 7.7 with conjugated inner products.
+//
+// One iteration is five kernels; each dot product the recurrence needs is
+// fused into the kernel that produces its operands, and the scalar it feeds
+// is formed in FP64 on the device by the last block to finish (ticket
+// counter):
+//   K1  p = r + beta (p - omega v)
+//   K2  v = A p          + (r^, v)        -> alpha = rho / (r^, v)
+//   K3  s = r - alpha v  + ||s||^2        -> stop at s if ||s|| / ||b|| <= tol
+//   K4  t = A s          + (t, s), ||t||^2 -> omega = (t, s) / (t, t)
+//   K5  x += alpha p + omega s, r = s - omega t + (r^, r), ||r||^2
+//                                         -> stop test, rho, beta
+// For complex64 the products and each thread's partial sums are FP32; block
+// and grid sums and every scalar of the recurrence are FP64.
+//
+// The loop runs inside one CUDA graph: an init kernel, a conditional WHILE
+// node whose body is K1..K5 (K5's last block sets the condition) and, for
+// the FP64 solver, a tail kernel that recomputes the true residual b - A x.
+#pragma once
+
+#include <cstring>
+
+#include "common.cuh"
+#include "internal.hpp"
+#include "spmv.cuh"
+
+namespace helm {
+
+template <class V> struct Prec;
+template <> struct Prec<double2> {
+  using S = double;
+  static constexpr int R = Engine<double2>::R;
+  __device__ static __forceinline__ double2 cvt(double2 z) { return z; }
+};
+template <> struct Prec<float2> {
+  using S = float;
+  static constexpr int R = Engine<float2>::R;
+  __device__ static __forceinline__ float2 cvt(double2 z) {
+    return make_float2(static_cast<float>(z.x), static_cast<float>(z.y));
+  }
+};
+
+template <class V>
+struct KArgs {
+  CsrDev<V> A;
+  const V* b;
+  V* x;
+  V *r, *rh, *p, *v, *s, *t;
+  SolverState* st;
+  double* partials;
+  unsigned int* tickets;
+  unsigned int* dev_err;
+  cudaGraphConditionalHandle cond;
+  int has_cond;
+};
+
+template <class V>
+__device__ __forceinline__ void set_cond(const KArgs<V>& a, bool cont) {
+  if (a.has_cond) cudaGraphSetConditional(a.cond, cont ? 1u : 0u);
+}
+
+__device__ __forceinline__ bool deadline_passed(const SolverState* st) {
+  return st->deadline_ns != 0ull && (globaltimer_ns() - st->t0) > st->deadline_ns;
+}
+
+__global__ void k_configure(SolverState* st, double tol, int32_t maxit, int32_t use_x0, double deadline_s,
+                            int32_t fresh);
+
+// r = b - A x (or r = b, x = 0), r^ = r, p = v = 0; ||b||, ||r||, rho.
+template <class V>
+__global__ void __launch_bounds__(Prec<V>::R) k_init(KArgs<V> a) {
+  using S = typename Prec<V>::S;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[32 * 4];
+  SolverState* st = a.st;
+  const int use_x0 = st->use_x0;
+  S acc[4] = {S(0), S(0), S(0), S(0)};  // |b|^2, |r|^2, (r, r)
+  if (use_x0) {
+    struct Epi {
+      const KArgs<V>* a;
+      S part[4];
+      __device__ __forceinline__ void row(int32_t i, V ax) {
+        const V bi = a->b[i];
+        const V ri = csub(bi, ax);
+        a->r[i] = ri;
+        a->rh[i] = ri;
+        a->p[i] = vzero<V>();
+        a->v[i] = vzero<V>();
+        part[0] = cabs2_acc(bi, part[0]);
+        part[1] = cabs2_acc(ri, part[1]);
+        V d;
+        d.x = part[2];
+        d.y = part[3];
+        d = cfma_conj(ri, ri, d);
+        part[2] = d.x;
+        part[3] = d.y;
+      }
+    } epi{&a, {S(0), S(0), S(0), S(0)}};
+    spmv_run<V>(a.A, a.x, epi, smem, a.dev_err);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[k] = epi.part[k];
+  } else {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.A.n; i += gridDim.x * blockDim.x) {
+      const V bi = a.b[i];
+      a.x[i] = vzero<V>();
+      a.r[i] = bi;
+      a.rh[i] = bi;
+      a.p[i] = vzero<V>();
+      a.v[i] = vzero<V>();
+      acc[0] = cabs2_acc(bi, acc[0]);
+      V d;
+      d.x = acc[2];
+      d.y = acc[3];
+      d = cfma_conj(bi, bi, d);
+      acc[2] = d.x;
+      acc[3] = d.y;
+    }
+    acc[1] = acc[0];
+  }
+  double part[4] = {double(acc[0]), double(acc[1]), double(acc[2]), double(acc[3])};
+  double tot[4];
+  if (!grid_sum_last<4>(part, a.partials, a.tickets + TK_INIT, red, tot)) return;
+  if (threadIdx.x != 0) return;
+  const double bnorm = sqrt(tot[0]);
+  st->bnorm = bnorm;
+  if (use_x0) st->spmv_count += 1;
+  int status = ST_RUNNING;
+  if (!isfinite(bnorm)) {
+    status = HELM_ERR_NONFINITE;
+  } else if (bnorm == 0.0) {
+    status = HELM_OK;  // b = 0: x = 0 (written by the tail kernel / caller)
+    st->relres = 0.0;
+  } else {
+    const double relres = sqrt(tot[1]) / bnorm;
+    st->relres = relres;
+    const double2 rho = make_double2(tot[2], tot[3]);
+    if (!isfinite(relres)) {
+      status = HELM_ERR_NONFINITE;
+    } else if (relres <= st->tol) {
+      status = HELM_OK;
+    } else if (st->iter >= st->maxit) {
+      status = HELM_ERR_NOT_CONVERGED;
+    } else if (!cfinite(rho)) {
+      status = HELM_ERR_NONFINITE;
+      st->iter += 1;
+    } else if (czero(rho)) {
+      status = HELM_ERR_BREAKDOWN;
+      st->iter += 1;
+    } else {
+      // beta = (rho / 1) (1 / 1): the first p update gives p = r
+      st->rho = rho;
+      st->beta = rho;
+    }
+  }
+  st->status = status;
+  set_cond(a, status == ST_RUNNING);
+}
+
+// Element-wise kernels: one wave of blocks (grid = resident blocks), each
+// thread takes two elements per step with all loads issued before the
+// arithmetic, so the 64-clock FP64 latency and the memory latency of one
+// element overlap the other's.
+constexpr int kVecThreads = 256;
+
+// K1: p = r + beta (p - omega v)
+template <class V>
+__global__ void __launch_bounds__(kVecThreads) k_p(KArgs<V> a) {
+  const SolverState* st = a.st;
+  if (st->status != ST_RUNNING) return;
+  const V beta = Prec<V>::cvt(st->beta), omega = Prec<V>::cvt(st->omega);
+  const int32_t n = a.A.n;
+  const int32_t stride = gridDim.x * blockDim.x;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += 2 * stride) {
+    const int32_t j = i + stride;
+    const bool two = j < n;
+    const V v0 = a.v[i], p0 = a.p[i], r0 = a.r[i];
+    V v1 = vzero<V>(), p1 = vzero<V>(), r1 = vzero<V>();
+    if (two) {
+      v1 = a.v[j];
+      p1 = a.p[j];
+      r1 = a.r[j];
+    }
+    a.p[i] = cfma(beta, cfms(omega, v0, p0), r0);
+    if (two) a.p[j] = cfma(beta, cfms(omega, v1, p1), r1);
+  }
+}
+
+// K2: v = A p, (r^, v) -> alpha
+template <class V>
+__global__ void __launch_bounds__(Prec<V>::R) k_v(KArgs<V> a) {
+  using S = typename Prec<V>::S;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[32 * 2];
+  SolverState* st = a.st;
+  if (st->status != ST_RUNNING) return;
+  struct Epi {
+    const KArgs<V>* a;
+    V part;
+    __device__ __forceinline__ void row(int32_t i, V ax) {
+      a->v[i] = ax;
+      part = cfma_conj(a->rh[i], ax, part);
+    }
+  } epi{&a, vzero<V>()};
+  spmv_run<V>(a.A, a.p, epi, smem, a.dev_err);
+  double part[2] = {double(epi.part.x), double(epi.part.y)};
+  double tot[2];
+  if (!grid_sum_last<2>(part, a.partials, a.tickets + TK_V, red, tot)) return;
+  if (threadIdx.x != 0) return;
+  st->iter += 1;
+  st->spmv_count += 1;
+  const double2 rv = make_double2(tot[0], tot[1]);
+  if (!cfinite(rv)) {
+    st->status = HELM_ERR_NONFINITE;
+  } else if (czero(rv)) {
+    st->status = HELM_ERR_BREAKDOWN;
+  } else {
+    const double2 alpha = cdiv(st->rho, rv);
+    if (!cfinite(alpha)) st->status = HELM_ERR_NONFINITE;
+    else st->alpha = alpha;
+  }
+}
+
+// K3: s = r - alpha v, ||s||
+template <class V>
+__global__ void __launch_bounds__(kVecThreads) k_s(KArgs<V> a) {
+  using S = typename Prec<V>::S;
+  __shared__ double red[32];
+  SolverState* st = a.st;
+  if (st->status != ST_RUNNING) return;
+  const V alpha = Prec<V>::cvt(st->alpha);
+  S acc = S(0), acc1 = S(0);
+  const int32_t n = a.A.n;
+  const int32_t stride = gridDim.x * blockDim.x;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += 2 * stride) {
+    const int32_t j = i + stride;
+    const bool two = j < n;
+    const V v0 = a.v[i], r0 = a.r[i];
+    V v1 = vzero<V>(), r1 = vzero<V>();
+    if (two) {
+      v1 = a.v[j];
+      r1 = a.r[j];
+    }
+    const V s0 = cfms(alpha, v0, r0);
+    a.s[i] = s0;
+    acc = cabs2_acc(s0, acc);
+    if (two) {
+      const V s1 = cfms(alpha, v1, r1);
+      a.s[j] = s1;
+      acc1 = cabs2_acc(s1, acc1);
+    }
+  }
+  double part[1] = {double(acc) + double(acc1)};
+  double tot[1];
+  if (!grid_sum_last<1>(part, a.partials, a.tickets + TK_S, red, tot)) return;
+  if (threadIdx.x != 0) return;
+  const double snorm = sqrt(tot[0]);
+  if (!isfinite(snorm)) {
+    st->status = HELM_ERR_NONFINITE;
+  } else if (snorm / st->bnorm <= st->tol) {
+    st->phase = PH_SCONV;
+    st->relres = snorm / st->bnorm;
+  }
+}
+
+// K4: t = A s, (t, s), (t, t) -> omega
+template <class V>
+__global__ void __launch_bounds__(Prec<V>::R) k_t(KArgs<V> a) {
+  using S = typename Prec<V>::S;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[32 * 3];
+  SolverState* st = a.st;
+  if (st->status != ST_RUNNING || st->phase != PH_RUN) return;
+  struct Epi {
+    const KArgs<V>* a;
+    V ts;
+    S tt;
+    __device__ __forceinline__ void row(int32_t i, V ax) {
+      a->t[i] = ax;
+      ts = cfma_conj(ax, a->s[i], ts);
+      tt = cabs2_acc(ax, tt);
+    }
+  } epi{&a, vzero<V>(), S(0)};
+  spmv_run<V>(a.A, a.s, epi, smem, a.dev_err);
+  double part[3] = {double(epi.ts.x), double(epi.ts.y), double(epi.tt)};
+  double tot[3];
+  if (!grid_sum_last<3>(part, a.partials, a.tickets + TK_T, red, tot)) return;
+  if (threadIdx.x != 0) return;
+  st->spmv_count += 1;
+  const double2 ts = make_double2(tot[0], tot[1]);
+  const double tt = tot[2];
+  if (!cfinite(ts) || !isfinite(tt)) {
+    st->status = HELM_ERR_NONFINITE;
+  } else if (tt == 0.0) {
+    st->status = HELM_ERR_BREAKDOWN;
+  } else {
+    const double2 omega = make_double2(ts.x / tt, ts.y / tt);
+    if (!cfinite(omega)) st->status = HELM_ERR_NONFINITE;
+    else st->omega = omega;
+  }
+}
+
+// K5: x += alpha p + omega s, r = s - omega t; stop test; rho, beta
+template <class V>
+__global__ void __launch_bounds__(kVecThreads) k_xr(KArgs<V> a) {
+  using S = typename Prec<V>::S;
+  __shared__ double red[32 * 3];
+  SolverState* st = a.st;
+  const int status0 = st->status;
+  if (status0 != ST_RUNNING) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(a, false);
+    return;
+  }
+  const double2 alpha64 = st->alpha, omega64 = st->omega;
+  const V alpha = Prec<V>::cvt(alpha64), omega = Prec<V>::cvt(omega64);
+  const int phase = st->phase;
+  V rr = vzero<V>(), rr1 = vzero<V>();
+  S r2 = S(0), r21 = S(0);
+  const int32_t n = a.A.n;
+  const int32_t stride = gridDim.x * blockDim.x;
+  if (phase == PH_SCONV) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) a.x[i] = cfma(alpha, a.p[i], a.x[i]);
+  } else {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += 2 * stride) {
+      const int32_t j = i + stride;
+      const bool two = j < n;
+      const V s0 = a.s[i], x0 = a.x[i], p0 = a.p[i], t0 = a.t[i], h0 = a.rh[i];
+      V s1 = vzero<V>(), x1 = vzero<V>(), p1 = vzero<V>(), t1 = vzero<V>(), h1 = vzero<V>();
+      if (two) {
+        s1 = a.s[j];
+        x1 = a.x[j];
+        p1 = a.p[j];
+        t1 = a.t[j];
+        h1 = a.rh[j];
+      }
+      a.x[i] = cfma(omega, s0, cfma(alpha, p0, x0));
+      const V r0 = cfms(omega, t0, s0);
+      a.r[i] = r0;
+      rr = cfma_conj(h0, r0, rr);
+      r2 = cabs2_acc(r0, r2);
+      if (two) {
+        a.x[j] = cfma(omega, s1, cfma(alpha, p1, x1));
+        const V r1 = cfms(omega, t1, s1);
+        a.r[j] = r1;
+        rr1 = cfma_conj(h1, r1, rr1);
+        r21 = cabs2_acc(r1, r21);
+      }
+    }
+  }
+  double part[3] = {double(rr.x) + double(rr1.x), double(rr.y) + double(rr1.y), double(r2) + double(r21)};
+  double tot[3];
+  if (!grid_sum_last<3>(part, a.partials, a.tickets + TK_XR, red, tot)) return;
+  if (threadIdx.x != 0) return;
+  int status = ST_RUNNING;
+  if (phase == PH_SCONV) {
+    status = HELM_OK;
+    st->phase = PH_DONE;
+  } else {
+    const double relres = sqrt(tot[2]) / st->bnorm;
+    st->relres = relres;
+    if (!isfinite(relres)) {
+      status = HELM_ERR_NONFINITE;
+    } else if (relres <= st->tol) {
+      status = HELM_OK;
+    } else if (czero(omega64)) {
+      status = HELM_ERR_BREAKDOWN;
+    } else if (st->iter >= st->maxit) {
+      status = HELM_ERR_NOT_CONVERGED;
+    } else if (deadline_passed(st)) {
+      status = HELM_ERR_TIMEOUT;
+    } else {
+      const double2 rho_new = make_double2(tot[0], tot[1]);
+      const double2 beta = cmul(cdiv(rho_new, st->rho), cdiv(alpha64, omega64));
+      if (!cfinite(rho_new) || !cfinite(beta)) {
+        status = HELM_ERR_NONFINITE;
+        st->iter += 1;
+      } else if (czero(rho_new)) {
+        status = HELM_ERR_BREAKDOWN;
+        st->iter += 1;
+      } else {
+        st->rho = rho_new;
+        st->beta = beta;
+      }
+    }
+  }
+  st->status = status;
+  set_cond(a, status == ST_RUNNING);
+}
+
+template <class V>
+struct KShapes {
+  int spmv_grid, vec_grid;
+  int grid_p, grid_s, grid_xr;  // one wave of each element-wise kernel
+};
+
+template <class V>
+inline void enqueue_init(const KArgs<V>& a, const KShapes<V>& sh, cudaStream_t s) {
+  k_init<V><<<sh.spmv_grid, Prec<V>::R, Engine<V>::kSmem, s>>>(a);
+}
+template <class V>
+inline void enqueue_body(const KArgs<V>& a, const KShapes<V>& sh, cudaStream_t s) {
+  constexpr size_t smem = Engine<V>::kSmem;
+  k_p<V><<<sh.grid_p, kVecThreads, 0, s>>>(a);
+  k_v<V><<<sh.spmv_grid, Prec<V>::R, smem, s>>>(a);
+  k_s<V><<<sh.grid_s, kVecThreads, 0, s>>>(a);
+  k_t<V><<<sh.spmv_grid, Prec<V>::R, smem, s>>>(a);
+  k_xr<V><<<sh.grid_xr, kVecThreads, 0, s>>>(a);
+}
+
+template <class V>
+inline helm_status prepare_krylov_kernels() {
+  constexpr size_t smem = Engine<V>::kSmem;
+  HELM_CUDA_TRY(set_smem_attr(reinterpret_cast<const void*>(&k_init<V>), smem));
+  HELM_CUDA_TRY(set_smem_attr(reinterpret_cast<const void*>(&k_v<V>), smem));
+  HELM_CUDA_TRY(set_smem_attr(reinterpret_cast<const void*>(&k_t<V>), smem));
+  return HELM_OK;
+}
+
+// Grid of the staged SpMV kernels of the solver: resident blocks per SM x SMs
+// (the same for every SpMV-shaped kernel of the solver: they share the
+// engine's shared-memory footprint).
+template <class V>
+inline helm_status krylov_shapes(helm_csr A, KShapes<V>* sh) {
+  constexpr size_t smem = Engine<V>::kSmem;
+  int per_sm = 0;
+  HELM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_v<V>, Prec<V>::R, smem));
+  per_sm = per_sm < 1 ? 1 : per_sm;
+  const int ntiles = (A->n + Prec<V>::R - 1) / Prec<V>::R;
+  int g = per_sm * A->num_sms;
+  sh->spmv_grid = ntiles < g ? (ntiles < 1 ? 1 : ntiles) : g;
+  sh->vec_grid = A->vec_grid;
+  const int64_t want = (static_cast<int64_t>(A->n) + 2 * kVecThreads - 1) / (2 * kVecThreads);
+  auto wave = [&](const void* fn, int* out) -> helm_status {
+    int b = 0;
+    HELM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, kVecThreads, 0));
+    int64_t gg = static_cast<int64_t>(b < 1 ? 1 : b) * A->num_sms;
+    if (want < gg) gg = want < 1 ? 1 : want;
+    *out = static_cast<int>(gg);
+    return HELM_OK;
+  };
+  helm_status st = wave(reinterpret_cast<const void*>(&k_p<V>), &sh->grid_p);
+  if (st == HELM_OK) st = wave(reinterpret_cast<const void*>(&k_s<V>), &sh->grid_s);
+  if (st == HELM_OK) st = wave(reinterpret_cast<const void*>(&k_xr<V>), &sh->grid_xr);
+  return st;
+}
+
+// Build a graph  init -> while(body) [-> tail]  for fixed vectors.  `tail`
+// enqueues the kernels after the loop (may be empty).
+template <class V, class Tail>
+helm_status build_krylov_graph(const KArgs<V>& base, const KShapes<V>& sh, Tail tail, GraphEntry* out) {
+  cudaStream_t cs = nullptr;
+  HELM_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  helm_status result = HELM_ERR_CUDA;
+  do {
+    if (cudaGraphCreate(&graph, 0) != cudaSuccess) break;
+    cudaGraphConditionalHandle cond;
+    if (cudaGraphConditionalHandleCreate(&cond, graph, 1u, cudaGraphCondAssignDefault) != cudaSuccess) break;
+    KArgs<V> a = base;
+    a.cond = cond;
+    a.has_cond = 1;
+    if (cudaStreamBeginCaptureToGraph(cs, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+        cudaSuccess)
+      break;
+    enqueue_init(a, sh, cs);
+    cudaStreamCaptureStatus cst;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &deps, nullptr, &ndeps);
+    cudaGraphNode_t init_node = (e == cudaSuccess && ndeps == 1) ? deps[0] : nullptr;
+    cudaGraph_t tmp = nullptr;
+    if (cudaStreamEndCapture(cs, &tmp) != cudaSuccess || e != cudaSuccess || !init_node) break;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    if (cudaGraphAddNode(&wnode, graph, &init_node, nullptr, 1, &cp) != cudaSuccess) break;
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+        cudaSuccess)
+      break;
+    enqueue_body(a, sh, cs);
+    if (cudaStreamEndCapture(cs, &tmp) != cudaSuccess) break;
+    if (cudaStreamBeginCaptureToGraph(cs, graph, &wnode, nullptr, 1, cudaStreamCaptureModeThreadLocal) !=
+        cudaSuccess)
+      break;
+    tail(a, cs);
+    if (cudaStreamEndCapture(cs, &tmp) != cudaSuccess) break;
+    if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) break;
+    result = HELM_OK;
+  } while (false);
+  cudaStreamDestroy(cs);
+  if (result != HELM_OK) {
+    (void)cudaGetLastError();
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    return result;
+  }
+  out->exec = exec;
+  out->graph = graph;
+  return HELM_OK;
+}
+
+// Run init -> loop -> tail once: through the cached graph when there is one,
+// else host-driven (chunks of 16 iterations, state polled between chunks).
+template <class V, class Tail>
+helm_status run_krylov(helm_csr A, const KArgs<V>& a, const KShapes<V>& sh, GraphEntry* g, Tail tail,
+                       cudaStream_t s) {
+  if (g && g->exec) {
+    HELM_CUDA_TRY(cudaGraphLaunch(g->exec, s));
+    return HELM_OK;
+  }
+  enqueue_init(a, sh, s);
+  HELM_CUDA_TRY(cudaGetLastError());
+  for (;;) {
+    for (int k = 0; k < 16; ++k) enqueue_body(a, sh, s);
+    HELM_CUDA_TRY(cudaGetLastError());
+    HELM_CUDA_TRY(cudaMemcpyAsync(A->state_host, a.st, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
+    HELM_CUDA_TRY(cudaStreamSynchronize(s));
+    if (A->state_host->status != ST_RUNNING) break;
+  }
+  tail(a, s);
+  HELM_CUDA_TRY(cudaGetLastError());
+  return HELM_OK;
+}
+
+}  // namespace helm

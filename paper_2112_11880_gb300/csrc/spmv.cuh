@@ -24,7 +24,10 @@
 //     group of the array, where the few trailing entries are read directly.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
+#include "internal.hpp"
 
 namespace helm {
 
@@ -35,7 +38,30 @@ struct CsrDev {
   const int32_t* rowptr;
   const int32_t* colind;
   const V* vals;
+  // Optional (complex128 only): real_blk[r >> 5] != 0 when every stored
+  // entry of rows [32 (r >> 5), 32 (r >> 5) + 32) has a zero imaginary part.
+  // Those rows take the real x complex product (2 FMA per entry instead of
+  // 4); for finite x the result is bit-identical to the complex product,
+  // since the skipped terms are exact zeros.  Helmholtz FEM rows away from
+  // the impedance boundary are of this kind (A = K - k^2 M + i k B).
+  const uint8_t* real_blk;
 };
+
+// Row sum of a complex128 row whose entries are all real: reads only the
+// real parts.
+__device__ __forceinline__ double2 mac_real(double a, double2 x, double2 acc) {
+  acc.x = fma(a, x.x, acc.x);
+  acc.y = fma(a, x.y, acc.y);
+  return acc;
+}
+template <class V>
+__device__ __forceinline__ bool row_block_real(const CsrDev<V>& A, int64_t r) {
+  return false;
+}
+template <>
+__device__ __forceinline__ bool row_block_real<double2>(const CsrDev<double2>& A, int64_t r) {
+  return A.real_blk != nullptr && A.real_blk[r >> 5] != 0;
+}
 
 __device__ __forceinline__ double2 mac(double2 a, double2 x, double2 acc) { return cfma(a, x, acc); }
 __device__ __forceinline__ float2 mac(float2 a, float2 x, float2 acc) { return cfma32(a, x, acc); }
@@ -43,29 +69,50 @@ template <class V> __device__ __forceinline__ V vzero();
 template <> __device__ __forceinline__ double2 vzero<double2>() { return make_double2(0.0, 0.0); }
 template <> __device__ __forceinline__ float2 vzero<float2>() { return make_float2(0.f, 0.f); }
 
-// Shared-memory footprint of the staged engine for CAP entries per tile.
-template <class V, int CAP>
+// Shared-memory footprint of the staged engine: STAGES buffers of CAP
+// entries each.
+template <class V, int CAP, int STAGES = 2>
 struct SpmvStage {
   static_assert(CAP % 4 == 0, "CAP must be a multiple of 4");
+  static_assert(STAGES == 1 || STAGES == 2, "one or two buffers");
   static constexpr int kVG = 16 / sizeof(V);  // values per 16-byte group
   static constexpr size_t kValsBytes = sizeof(V) * (CAP + 2 * kVG);
   static constexpr size_t kColsBytes = sizeof(int32_t) * (CAP + 8);
-  static constexpr size_t kBytes = 2 * (kValsBytes + kColsBytes) + 2 * sizeof(uint64_t);
+  static constexpr size_t kBytes = STAGES * (kValsBytes + kColsBytes) + 2 * sizeof(uint64_t);
   static_assert(kValsBytes % 16 == 0 && kColsBytes % 16 == 0, "16-byte aligned buffers");
 };
+
+template <class V> __device__ __forceinline__ V vadd(V a, V b) { return cadd(a, b); }
 
 // Walk this block's tiles; call epi.row(r, acc) for each row r with
 // acc = sum_k vals[k] * x[colind[k]].  Returns false if a bulk copy never
 // completed (error flag set).  Must be called by all threads of the block.
-template <class V, int R, int CAP, class Epi>
+//
+// STAGES = 2: the copy of a block's next tile overlaps the current tile.
+// STAGES = 1: half the shared memory per block, so more blocks share an SM
+// and overlap one another instead.  NACC = 2 splits each row's sum into two
+// interleaved partial sums (more independent FP64 chains per thread).
+//
+// SPLIT > 1: the block has R * SPLIT threads and thread t takes the entries
+// k = k0 + (t / R), k0 + (t / R) + SPLIT, ... of row t % R (more warps per
+// staged tile, each with a shorter dependent chain); the SPLIT partial sums
+// of a row are added in a fixed order through shared memory, and only the
+// threads t < R call epi.row.
+template <class V, int R, int CAP, class Epi, int STAGES = 2, int NACC = 1, int SPLIT = 1>
 __device__ __forceinline__ bool spmv_tiles(const CsrDev<V>& A, const V* __restrict__ x, Epi& epi,
                                            unsigned char* smem, unsigned int* dev_err) {
-  using S = SpmvStage<V, CAP>;
+  using S = SpmvStage<V, CAP, STAGES>;
+  static_assert(SPLIT == 1 || NACC == 1, "split rows use one accumulator per thread");
+  __shared__ V s_part[SPLIT > 1 ? (SPLIT - 1) * R : 1];
+  const int part = SPLIT > 1 ? static_cast<int>(threadIdx.x) / R : 0;
+  const int lrow = SPLIT > 1 ? static_cast<int>(threadIdx.x) % R : static_cast<int>(threadIdx.x);
   constexpr int VG = S::kVG;
-  // buffer b: values at smem + b * kValsBytes, columns after both value buffers
+  // buffer b: values at smem + b * kValsBytes, columns after the value buffers
   auto sv = [&](int b) { return reinterpret_cast<V*>(smem + b * S::kValsBytes); };
-  auto sc = [&](int b) { return reinterpret_cast<int32_t*>(smem + 2 * S::kValsBytes + b * S::kColsBytes); };
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * (S::kValsBytes + S::kColsBytes));
+  auto sc = [&](int b) {
+    return reinterpret_cast<int32_t*>(smem + STAGES * S::kValsBytes + b * S::kColsBytes);
+  };
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + STAGES * (S::kValsBytes + S::kColsBytes));
 
   const int32_t n = A.n;
   const int32_t ntiles = (n + R - 1) / R;
@@ -114,38 +161,71 @@ __device__ __forceinline__ bool spmv_tiles(const CsrDev<V>& A, const V* __restri
   int fail_it = 0;
   bool fail_next = false;
   int32_t tile = blockIdx.x;
-  if (threadIdx.x == 0 && tile < ntiles) issue(tile, 0);
+  if (STAGES == 2 && threadIdx.x == 0 && tile < ntiles) issue(tile, 0);
   for (int it = 0; tile < ntiles; tile += gridDim.x, ++it) {
-    const int b = it & 1;
+    const int b = STAGES == 2 ? (it & 1) : 0;
     const int32_t next = tile + gridDim.x;
-    if (threadIdx.x == 0 && next < ntiles) {
-      fence_proxy_async();  // buffer b^1 was last read through the generic proxy
-      issue(next, b ^ 1);
+    if (threadIdx.x == 0) {
+      if (STAGES == 2) {
+        if (next < ntiles) {
+          fence_proxy_async();  // buffer b^1 was last read through the generic proxy
+          issue(next, b ^ 1);
+        }
+      } else {
+        fence_proxy_async();  // the single buffer was last read through the generic proxy
+        issue(tile, 0);
+      }
     }
     const Range g = range_of(tile);
+    const uint32_t parity = STAGES == 2 ? ((it >> 1) & 1) : (it & 1);
     // Every thread observes the phase (visibility of the async-proxy
     // writes); the give-up decision is made block-uniform by the vote.
-    const bool got = mbar_wait_bounded(&bar[b], (it >> 1) & 1, 2000000000ull);
+    const bool got = mbar_wait_bounded(&bar[b], parity, 2000000000ull);
     if (!__syncthreads_and(got)) {
       if (threadIdx.x == 0) atomicOr(dev_err, DEVERR_MBAR_TIMEOUT);
       ok = false;
       fail_it = it;
-      fail_next = next < ntiles;
+      fail_next = STAGES == 2 && next < ntiles;
       break;
     }
-    const int32_t r = tile * R + threadIdx.x;
-    if (r < min(tile * R + R, n)) {
-      const int64_t k0 = A.rowptr[r], k1 = A.rowptr[r + 1];
+    const int32_t r = tile * R + lrow;
+    const bool row_ok = r < min(tile * R + R, n);
+    V acc_split = vzero<V>();
+    if (row_ok) {
+      const int64_t k0 = A.rowptr[r] + part, k1 = A.rowptr[r + 1];
+      constexpr int KS = SPLIT;
       V acc = vzero<V>();
       if (g.staged) {
         const V* v = sv(b) - g.va0;
         const int32_t* c = sc(b) - g.ca0;
-        if (g.e <= g.va1 && g.e <= g.ca1) {
+        bool real_done = false;
+        if constexpr (std::is_same<V, double2>::value) {
+          if (g.e <= g.va1 && g.e <= g.ca1 && row_block_real(A, r)) {
+            const double* vr = reinterpret_cast<const double*>(v);
 #pragma unroll 4
-          for (int64_t k = k0; k < k1; ++k) acc = mac(v[k], ld_gather(x + c[k]), acc);
+            for (int64_t k = k0; k < k1; k += KS) acc = mac_real(vr[2 * k], ld_gather(x + c[k]), acc);
+            real_done = true;
+          }
+        }
+        if (real_done) {
+        } else if (g.e <= g.va1 && g.e <= g.ca1) {
+          if (NACC == 2) {
+            V acc1 = vzero<V>();
+            int64_t k = k0;
+#pragma unroll 2
+            for (; k + 1 < k1; k += 2) {
+              acc = mac(v[k], ld_gather(x + c[k]), acc);
+              acc1 = mac(v[k + 1], ld_gather(x + c[k + 1]), acc1);
+            }
+            if (k < k1) acc = mac(v[k], ld_gather(x + c[k]), acc);
+            acc = vadd(acc, acc1);
+          } else {
+#pragma unroll 4
+            for (int64_t k = k0; k < k1; k += KS) acc = mac(v[k], ld_gather(x + c[k]), acc);
+          }
         } else {  // entries past the last whole 16-byte group: plain loads
 #pragma unroll 2
-          for (int64_t k = k0; k < k1; ++k) {
+          for (int64_t k = k0; k < k1; k += KS) {
             const V a = (k < g.va1) ? v[k] : ld_stream(A.vals + k);
             const int32_t col = (k < g.ca1) ? c[k] : ld_stream(A.colind + k);
             acc = mac(a, ld_gather(x + col), acc);
@@ -153,21 +233,94 @@ __device__ __forceinline__ bool spmv_tiles(const CsrDev<V>& A, const V* __restri
         }
       } else {
 #pragma unroll 4
-        for (int64_t k = k0; k < k1; ++k)
+        for (int64_t k = k0; k < k1; k += KS)
           acc = mac(ld_stream(A.vals + k), ld_gather(x + ld_stream(A.colind + k)), acc);
       }
-      epi.row(r, acc);
+      acc_split = acc;
     }
+    if (SPLIT > 1) {
+      if (part > 0) s_part[(part - 1) * R + lrow] = acc_split;
+      __syncthreads();
+      if (part == 0 && row_ok) {
+#pragma unroll
+        for (int q = 1; q < SPLIT; ++q) acc_split = vadd(acc_split, s_part[(q - 1) * R + lrow]);
+      }
+    }
+    if (part == 0 && row_ok) epi.row(r, acc_split);
     __syncthreads();  // buffer b fully consumed before it is refilled
   }
   if (!ok) {
     // Let the copies still in flight land (bounded) before the block's
     // shared memory is released.
-    (void)mbar_wait_bounded(&bar[fail_it & 1], (fail_it >> 1) & 1, 100000000ull);
-    if (fail_next)
-      (void)mbar_wait_bounded(&bar[(fail_it + 1) & 1], ((fail_it + 1) >> 1) & 1, 100000000ull);
+    if (STAGES == 2) {
+      (void)mbar_wait_bounded(&bar[fail_it & 1], (fail_it >> 1) & 1, 100000000ull);
+      if (fail_next)
+        (void)mbar_wait_bounded(&bar[(fail_it + 1) & 1], ((fail_it + 1) >> 1) & 1, 100000000ull);
+    } else {
+      (void)mbar_wait_bounded(&bar[0], fail_it & 1, 100000000ull);
+    }
   }
   return ok;
+}
+
+// Direct-load engine: LANES threads per row (1, 2, 4, 8, 16 or 32), no shared
+// memory, so occupancy is limited only by registers.  Entries are read
+// through L1 (consecutive k of a lane group share sectors); the lane sums
+// are combined with a fixed xor-shuffle tree (log2 LANES FP64 adds).  The
+// warp walks rows in uniform steps so every shuffle has all 32 lanes.
+template <class V, int LANES, class Epi>
+__device__ __forceinline__ void spmv_lanes(const CsrDev<V>& A, const V* __restrict__ x, Epi& epi) {
+  static_assert(LANES >= 1 && LANES <= 32 && (LANES & (LANES - 1)) == 0, "power of two");
+  constexpr int RPW = 32 / LANES;  // rows per warp step
+  const int lane = threadIdx.x & 31;
+  const int sub = lane % LANES;
+  const int64_t warp = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t base = warp * RPW; base < A.n; base += nwarps * RPW) {
+    const int64_t r = base + lane / LANES;
+    const bool valid = r < A.n;
+    V acc = vzero<V>();
+    if (valid) {
+      const int64_t k0 = A.rowptr[r], k1 = A.rowptr[r + 1];
+      bool real_done = false;
+      if constexpr (std::is_same<V, double2>::value) {
+        if (row_block_real(A, r)) {
+          const double* vr = reinterpret_cast<const double*>(A.vals);
+#pragma unroll 4
+          for (int64_t k = k0 + sub; k < k1; k += LANES)
+            acc = mac_real(__ldg(vr + 2 * k), ld_gather(x + __ldg(A.colind + k)), acc);
+          real_done = true;
+        }
+      }
+      if (!real_done) {
+#pragma unroll 4
+        for (int64_t k = k0 + sub; k < k1; k += LANES)
+          acc = mac(__ldg(A.vals + k), ld_gather(x + __ldg(A.colind + k)), acc);
+      }
+    }
+#pragma unroll
+    for (int off = LANES / 2; off > 0; off >>= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+    }
+    if (valid && sub == 0) epi.row(static_cast<int32_t>(r), acc);
+  }
+}
+
+// The engine configuration every SpMV-shaped kernel of the library uses.
+template <class V> struct Engine;
+template <> struct Engine<double2> {
+  static constexpr int R = kRows128, CAP = kCap128;
+  static constexpr size_t kSmem = SpmvStage<double2, CAP, kStages>::kBytes;
+};
+template <> struct Engine<float2> {
+  static constexpr int R = kRows64, CAP = kCap64;
+  static constexpr size_t kSmem = SpmvStage<float2, CAP, kStages>::kBytes;
+};
+template <class V, class Epi>
+__device__ __forceinline__ bool spmv_run(const CsrDev<V>& A, const V* __restrict__ x, Epi& epi, unsigned char* smem,
+                                         unsigned int* dev_err) {
+  return spmv_tiles<V, Engine<V>::R, Engine<V>::CAP, Epi, kStages, 1>(A, x, epi, smem, dev_err);
 }
 
 }  // namespace helm
