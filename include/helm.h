@@ -111,6 +111,34 @@ helm_status helm_dot(int64_t n, helm_dtype dt, const void* d_x, const void* d_y,
                      void* d_out, helm_stream_t stream);
 
 /*
+ * helm_dot_noalloc -- the same result as helm_dot (same arguments, same
+ * conventions, same kernels' arithmetic), for callers that cannot allocate
+ * device memory when they need a dot product: code that runs while a stream
+ * is being captured into a CUDA graph in a mode that forbids allocation,
+ * real-time loops that must never enter the allocator, or hosts that embed
+ * this library under their own device-memory manager.  The paper has no
+ * counterpart; it exists only for those callers.
+ *   Scratch: the per-block partial sums live in a fixed 64 KiB array compiled
+ *   into the library (a file-scope __device__ array of 2 x 4096 doubles).
+ *   Every GPU that loads libhelm holds one copy of it until the process
+ *   exits.  No call allocates or frees anything: no cudaMalloc, cudaFree or
+ *   stream-ordered allocator.
+ *   Maximum size: n < 2^31; larger n returns HELM_ERR_INVALID.  The grid never
+ *   exceeds 4096 blocks, so every n below the maximum fits the array.
+ *   Set-up: the first call on a device (with that device current) looks up
+ *   the array's device address with cudaGetSymbolAddress and caches it; make
+ *   that first call before any stream capture.  A failed lookup returns
+ *   HELM_ERR_CUDA.
+ *   Sharing: all calls on a device share the one array and it keeps the last
+ *   call's contents; nothing in it needs to start at zero (every slot read is
+ *   written earlier in the same call).  Calls whose kernels overlap on the
+ *   GPU (different streams without ordering) race on the array: order them.
+ * Asynchronous.
+ */
+helm_status helm_dot_noalloc(int64_t n, helm_dtype dt, const void* d_x, const void* d_y, int conj_x,
+                             void* d_out, helm_stream_t stream);
+
+/*
  * helm_nrm2 -- d_out = ||x||_2 = sqrt(sum_i |x_i|^2) (Section 3, Table 7).
  *   d_out : device double.
  * Asynchronous, deterministic, stream-ordered scratch as helm_dot.

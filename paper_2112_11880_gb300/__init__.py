@@ -75,6 +75,7 @@ SIGNATURES = {
     "helm_csr_destroy": (ctypes.c_int, [_P]),
     "helm_spmv": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "helm_dot": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, _P, _P, ctypes.c_int, _P, _P]),
+    "helm_dot_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, _P, _P, ctypes.c_int, _P, _P]),
     "helm_nrm2": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, _P, _P, _P]),
     "helm_axpby": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, _P, _P, _P, _P, _P]),
     "helm_opts_default": (None, [ctypes.POINTER(helm_opts)]),
@@ -170,6 +171,20 @@ def helm_dot(x, y, out, conj_x: bool = True, stream=None) -> None:
         raise ValueError("out must be a complex128 device tensor")
     _check(load_library().helm_dot(x.numel(), _dtype_code(x), _ptr(x), _ptr(y), 1 if conj_x else 0, _ptr(out),
                                    _stream(stream)), "helm_dot")
+
+
+def helm_dot_noalloc(x, y, out, conj_x: bool = True, stream=None) -> None:
+    """out (device complex128 scalar) = (x, y), computed with the library's
+    fixed scratch array instead of allocated memory (for callers that cannot
+    allocate; see include/helm.h)."""
+    _require_cuda(x, y, out)
+    if x.numel() != y.numel() or x.dtype != y.dtype:
+        raise ValueError("x and y must have the same length and dtype")
+    import torch
+    if out.dtype != torch.complex128 or out.numel() < 1:
+        raise ValueError("out must be a complex128 device tensor")
+    _check(load_library().helm_dot_noalloc(x.numel(), _dtype_code(x), _ptr(x), _ptr(y), 1 if conj_x else 0,
+                                           _ptr(out), _stream(stream)), "helm_dot_noalloc")
 
 
 def helm_nrm2(x, out, stream=None) -> None:
