@@ -392,6 +392,109 @@ def run_spmv_only(args):
     A.close()
 
 
+def run_extensions(args):
+    """Throughput of the three extensions against plain FP64 solves on the same
+    GPU (one JSON line): the 64-frequency sweep on the 60x30x25 cavity, mixed
+    precision on the 200x100x80 cavity, and the adjoint gradient on the
+    80x40x32 cavity."""
+    import torch
+
+    import paper_2112_11880_gb300 as helm
+    from paper_2112_11880_gb300 import autograd as hgrad
+    from paper_2112_11880_gb300 import build as hbuild
+    hbuild.build()
+    dev = torch.device("cuda", 0)
+    out = {"mode": "extensions"}
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return r, time.perf_counter() - t0
+
+    # (1) frequency sweep: batched vs one solve per frequency
+    cfg = helmgen.CONFIGS["sweep60"]
+    p = helmgen.assemble(cfg)
+    b = torch.as_tensor(helmgen.source(p), device=dev)
+    w = [helmgen.omega(f) for f in cfg.freqs]
+    S = helm.Sweep(p.rowptr, p.colind, p.K, p.Mc, p.Bc, device=dev)
+    S.solve(w, b, tol=cfg.tol, maxit=50000)          # warm-up (and autotune)
+    (X, infos), t_sweep = timed(lambda: S.solve(w, b, tol=cfg.tol, maxit=50000))
+    ok = all(i["status"] == "ok" for i in infos)
+    t_single = 0.0
+    it_single = 0
+    for j, F in enumerate(cfg.freqs):
+        vals = helmgen.helmholtz_values(p, F)
+        A = helm.CsrMatrix.from_host(p.rowptr, p.colind, vals, device=dev)
+        x = torch.empty_like(b)
+        helm.helm_bicgstab_solve(A.handle, b, x, helm.default_opts(tol=cfg.tol, maxit=50000))
+        info, dt = timed(lambda: helm.helm_bicgstab_solve(A.handle, b, x, helm.default_opts(tol=cfg.tol,
+                                                                                           maxit=50000)))
+        t_single += dt
+        it_single += info["iters"]
+        A.close()
+    out["sweep60"] = {"frequencies": len(w), "converged": ok, "batched_s": round(t_sweep, 4),
+                      "batched_freq_solves_per_s": round(len(w) / t_sweep, 3),
+                      "single_s": round(t_single, 4), "single_freq_solves_per_s": round(len(w) / t_single, 3),
+                      "speedup": round(t_single / t_sweep, 3),
+                      "iters_total_batched": sum(i["iters"] for i in infos), "iters_total_single": it_single,
+                      "iters_min_max": [min(i["iters"] for i in infos), max(i["iters"] for i in infos)]}
+    S.close()
+    print(json.dumps(out), flush=True)
+
+    # (2) mixed precision vs FP64 on the 200x100x80 cavity, to 1e-10
+    cfg = helmgen.CONFIGS["cavity200"]
+    p = helmgen.assemble(cfg)
+    vals = helmgen.helmholtz_values(p, cfg.F)
+    bh = helmgen.source(p)
+    b = torch.as_tensor(bh, device=dev)
+    A = helm.CsrMatrix.from_host(p.rowptr, p.colind, vals, device=dev)
+    x64 = torch.empty_like(b)
+    x32 = torch.empty_like(b)
+    info64, t64 = timed(lambda: helm.helm_bicgstab_solve(A.handle, b, x64, helm.default_opts(
+        tol=cfg.tol, maxit=args.mixed_maxit, deadline_s=600.0)))
+    info32, t32 = timed(lambda: helm.helm_bicgstab_solve(A.handle, b, x32, helm.default_opts(
+        tol=cfg.tol, maxit=args.mixed_maxit, precision=helm.HELM_PREC_MIXED, inner_tol=args.inner_tol,
+        deadline_s=600.0)))
+    err = float(torch.linalg.vector_norm(x32 - x64) / torch.linalg.vector_norm(x64))
+    out["cavity200_mixed"] = {"n": p.n, "nnz": p.nnz, "tol": cfg.tol, "fp64": {"s": round(t64, 3), **info64},
+                              "mixed": {"s": round(t32, 3), "inner_tol": args.inner_tol, **info32},
+                              "speedup": round(t64 / t32, 3), "rel_err_mixed_vs_fp64": err}
+    A.close()
+    print(json.dumps(out), flush=True)
+
+    # (3) adjoint gradient on the 80x40x32 cavity
+    cfg = helmgen.CONFIGS["adjoint80"]
+    p = helmgen.assemble(cfg)
+    m = helmgen.element_nnz_map(p)
+    se, sp = helmgen.slot_elements(p, m)
+    _, Me, Bf = helmgen.element_matrices(cfg.h)
+    fem = hgrad.HelmholtzFEM(p.rowptr, p.colind, p.K, se, sp, m, Me, Bf, helmgen.top_elements(cfg),
+                             helmgen.omega(cfg.F), dev)
+    rec = torch.as_tensor(helmgen.receivers(p, 64, seed=1), device=dev)
+    b = torch.as_tensor(helmgen.source(p), device=dev)
+    opts = helm.default_opts(tol=cfg.tol, maxit=100000)
+    with torch.no_grad():
+        d = hgrad.solve_sound_speed(torch.as_tensor(helmgen.sound_speed(cfg, seed=2), device=dev), b, fem, opts)[rec]
+
+    def fwd_bwd():
+        c = torch.as_tensor(p.c, device=dev).requires_grad_(True)
+        u = hgrad.solve_sound_speed(c, b, fem, opts)
+        e = u[rec] - d
+        L = torch.sum(e.real ** 2 + e.imag ** 2)
+        L.backward()
+        return c.grad
+
+    fwd_bwd()
+    _, t_grad = timed(fwd_bwd)
+    with torch.no_grad():
+        _, t_fwd = timed(lambda: hgrad.solve_sound_speed(torch.as_tensor(p.c, device=dev), b, fem, opts))
+    out["adjoint80"] = {"n": p.n, "params": cfg.n_elem, "forward_s": round(t_fwd, 4),
+                        "forward_backward_s": round(t_grad, 4), "backward_over_forward": round((t_grad - t_fwd) / t_fwd, 3)}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -401,7 +504,9 @@ def main():
     ap.add_argument("--cpu-sample-iters", type=int, default=200)
     ap.add_argument("--ref-step-iters", type=int, default=60)
     ap.add_argument("--ref-iters-per-solve", type=int, default=int(os.environ.get("HELM_ITERS_PER_SOLVE", "0")) or 0)
-    ap.add_argument("--mode", default="bench", choices=["bench", "spmv"],
+    ap.add_argument("--mixed-maxit", type=int, default=200000)
+    ap.add_argument("--inner-tol", type=float, default=1e-4)
+    ap.add_argument("--mode", default="bench", choices=["bench", "spmv", "extensions"],
                     help="spmv: only the complex128 SpMV loop on the same matrix (profiling target)")
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--launch", default="graph", choices=["graph", "host"],
@@ -410,6 +515,8 @@ def main():
     args = ap.parse_args()
     if args.mode == "spmv":
         run_spmv_only(args)
+    elif args.mode == "extensions":
+        run_extensions(args)
     elif args.impl == "reference":
         if not args.ref_iters_per_solve:
             args.ref_iters_per_solve = REF_ITERS_PER_SOLVE

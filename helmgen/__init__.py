@@ -332,6 +332,39 @@ def element_nnz_map(prob: Problem) -> np.ndarray:
     return out.reshape(-1, 64).astype(np.int32)
 
 
+def slot_elements(prob: Problem, elem_map: Optional[np.ndarray] = None, width: int = 8):
+    """Inverse of element_nnz_map: for each CSR slot, the (element, pair)
+    contributions, sorted by element index, padded with element -1.
+    Returns (elem int32[nnz, width], pair uint8[nnz, width]); pair = 8 a + b."""
+    if elem_map is None:
+        elem_map = element_nnz_map(prob)
+    E = elem_map.shape[0]
+    e_idx = np.repeat(np.arange(E, dtype=np.int64), 64)
+    ab = np.tile(np.arange(64, dtype=np.int64), E)
+    slot = elem_map.reshape(-1).astype(np.int64)
+    keep = slot >= 0
+    e_idx, ab, slot = e_idx[keep], ab[keep], slot[keep]
+    order = np.lexsort((e_idx, slot))
+    e_idx, ab, slot = e_idx[order], ab[order], slot[order]
+    counts = np.bincount(slot, minlength=prob.nnz)
+    if counts.max() > width:
+        raise ValueError("more contributions per slot than the table width")
+    start = np.zeros(prob.nnz + 1, dtype=np.int64)
+    np.cumsum(counts, out=start[1:])
+    pos = np.arange(slot.size) - start[slot]
+    elem = np.full((prob.nnz, width), -1, dtype=np.int32)
+    pair = np.zeros((prob.nnz, width), dtype=np.uint8)
+    elem[slot, pos] = e_idx
+    pair[slot, pos] = ab
+    return elem, pair
+
+
+def top_elements(cfg: Config) -> np.ndarray:
+    """uint8[E]: 1 for elements with a face on z = Lz (the impedance face)."""
+    e = np.arange(cfg.n_elem)
+    return ((e // (cfg.nx * cfg.ny)) == cfg.nz - 1).astype(np.uint8)
+
+
 # ----------------------------------------------------------------------------
 # Seeded vectors and generic CSR for tests and microbenchmarks
 # ----------------------------------------------------------------------------

@@ -238,6 +238,91 @@ helm_status helm_bicgstab_solve(helm_csr A, const void* d_b, void* d_x, const he
 helm_status helm_adjoint(helm_csr A, const void* d_u, const void* d_dLdu, const helm_opts* o,
                          void* d_mu, void* d_dLdvals, helm_info* info, helm_stream_t stream);
 
+/*
+ * helm_grad_sound_speed -- chain dL/dA onto per-element sound speed c (the
+ * velocity "different in space" of Section 1): with A = K - w^2 M_c + i w B_c,
+ * M_c = sum_e M_e / c_e^2 and B_c = sum_{top e} B_f / c_e,
+ *   grad[e] = 2 Re sum_{a,b} dLdvals[map[e][8a+b]] *
+ *             ((2 w^2 / c_e^3) Me[8a+b] - i (w / c_e^2) Bf[8a+b] [top[e]]).
+ *   d_dLdvals  : complex128[nnz], holomorphic dL/dA (as helm_adjoint writes).
+ *   d_elem_map : int32[n_elem][64], CSR slot of local pair (a, b) of each
+ *                element, -1 for pairs eliminated by a Dirichlet condition.
+ *   h_Me, h_Bf : host double[64], the element mass matrix and the impedance
+ *                face matrix (8x8 row-major; Bf zero off the face nodes).
+ *   d_top      : uint8[n_elem], 1 for elements carrying the impedance face.
+ *   d_c        : double[n_elem]; omega = 2 pi F; d_grad : double[n_elem] out.
+ * Asynchronous.
+ */
+helm_status helm_grad_sound_speed(int32_t n_elem, const void* d_dLdvals, const int32_t* d_elem_map,
+                                  const double* h_Me, const double* h_Bf, const uint8_t* d_top,
+                                  const double* d_c, double omega, double* d_grad,
+                                  helm_stream_t stream);
+
+/*
+ * helm_assemble_helmholtz -- the complex values of A(c) = K - w^2 M_c + i w B_c
+ * (Section 1: k = w / c with c varying in space) on a fixed CSR pattern, for
+ * per-element speeds c, so that c can be a differentiable input.
+ *   d_K         : double[nnz], the c-independent stiffness (and identity rows).
+ *   d_slot_elem : int32[nnz][8], elements contributing to each slot, in
+ *                 increasing element order, padded with -1.
+ *   d_slot_pair : uint8[nnz][8], local pair 8a+b of each contribution.
+ *   h_Me, h_Bf, d_top, d_c, omega as helm_grad_sound_speed.
+ *   d_vals      : complex128[nnz] out.
+ * Every sum is taken in element order with round-to-nearest steps and no
+ * contraction, so equal inputs give the same values bit for bit (and a
+ * symmetric pattern gives A == A^T exactly).  Asynchronous.
+ */
+helm_status helm_assemble_helmholtz(int64_t nnz, const double* d_K, const int32_t* d_slot_elem,
+                                    const uint8_t* d_slot_pair, const double* h_Me, const double* h_Bf,
+                                    const uint8_t* d_top, const double* d_c, double omega,
+                                    void* d_vals, helm_stream_t stream);
+
+/*
+ * helm_conj_scale -- d_y = alpha * conj(d_x) on complex128[n] (d_y may equal
+ * d_x).  Converts gradients between the holomorphic convention of
+ * helm_adjoint and PyTorch's (grad = 2 conj(dL/dz)).  Asynchronous.
+ */
+helm_status helm_conj_scale(int64_t n, const double* alpha, const void* d_x, void* d_y,
+                            helm_stream_t stream);
+
+/*
+ * Frequency sweep (the extension of Section 4's solvers to many wavenumbers
+ * k_j = w_j / c on one mesh): BiCGStab for all frequencies at once on
+ *   A_j = K - w_j^2 M + i w_j B,
+ * K, M, B real on one CSR pattern (stiffness, mass scaled by 1/c^2, impedance
+ * face scaled by 1/c), A_j formed on the fly inside the SpMV.  Converged
+ * frequencies are frozen; the whole sweep is one graph launch.
+ */
+typedef struct helm_sweep_s* helm_sweep; /* opaque */
+
+/*
+ * helm_sweep_create -- borrow the pattern and the three real value arrays
+ * (double[nnz] each, same layout rules as helm_csr_create).  One device pass
+ * flags the 32-row blocks where B is zero.  Synchronises `stream`.
+ */
+helm_status helm_sweep_create(helm_sweep* out, int32_t n, int64_t nnz, const int32_t* d_rowptr,
+                              const int32_t* d_colind, const double* d_K, const double* d_M,
+                              const double* d_B, helm_stream_t stream);
+helm_status helm_sweep_destroy(helm_sweep S);
+
+/*
+ * helm_sweep_solve -- solve A_j x_j = b_j for j < nfreq (1 <= nfreq <= 128).
+ *   h_omega : host double[nfreq], angular frequencies w_j = 2 pi F_j.
+ *   d_b     : complex128 right-hand sides, b_j[i] = d_b[i * b_ld + j] for
+ *             b_ld >= nfreq, or b_j[i] = d_b[i] (one b shared by all
+ *             frequencies) for b_ld = 0.
+ *   d_X     : complex128 solutions, x_j[i] = d_X[i * ldx + j], ldx >= nfreq
+ *             (read first when o->use_x0).
+ *   o       : tol, maxit, use_x0, deadline_s used (BiCGStab, FP64 only).
+ *   h_infos : host helm_info[nfreq] or NULL; filled after one synchronisation.
+ * The first call on a sweep times three tile shapes of the batched SpMV and
+ * keeps the fastest (autotuning).  Returns HELM_OK when every frequency
+ * converged, else the first failing frequency's status.
+ */
+helm_status helm_sweep_solve(helm_sweep S, int32_t nfreq, const double* h_omega, const void* d_b,
+                             int32_t b_ld, void* d_X, int32_t ldx, const helm_opts* o,
+                             helm_info* h_infos, helm_stream_t stream);
+
 /* helm_status_string -- static description of a status code. */
 const char* helm_status_string(helm_status s);
 

@@ -57,6 +57,11 @@ def _load():
             lib.oracle_bicgstab.argtypes = [ctypes.c_int32, P, P, P, P, P, ctypes.c_double,
                                             ctypes.c_int32, ctypes.c_int, P, P, P]
             lib.oracle_bicgstab.restype = ctypes.c_int
+            lib.oracle_tfqmr.argtypes = lib.oracle_bicgstab.argtypes
+            lib.oracle_tfqmr.restype = ctypes.c_int
+            lib.oracle_bicgstabl.argtypes = [ctypes.c_int32, P, P, P, P, P, ctypes.c_int, ctypes.c_double,
+                                             ctypes.c_int32, ctypes.c_int, P, P, P]
+            lib.oracle_bicgstabl.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -99,6 +104,20 @@ def dznrm2(x) -> float:
 
 def bicgstab(rowptr, colind, vals, b, tol=1e-8, maxit=20000, x0=None):
     """Textbook BiCGStab; returns (x, info dict)."""
+    return _krylov("oracle_bicgstab", rowptr, colind, vals, b, tol, maxit, x0)
+
+
+def tfqmr(rowptr, colind, vals, b, tol=1e-8, maxit=20000, x0=None):
+    """Transpose-free QMR (Saad 2003, Algorithm 7.8); returns (x, info dict)."""
+    return _krylov("oracle_tfqmr", rowptr, colind, vals, b, tol, maxit, x0)
+
+
+def bicgstabl(rowptr, colind, vals, b, ell=2, tol=1e-8, maxit=20000, x0=None):
+    """BiCGStab(l) (Sleijpen & Fokkema 1993); one iteration = one outer cycle."""
+    return _krylov("oracle_bicgstabl", rowptr, colind, vals, b, tol, maxit, x0, ell=ell)
+
+
+def _krylov(fname, rowptr, colind, vals, b, tol, maxit, x0, ell=None):
     lib = _load()
     n = len(rowptr) - 1
     rp, prp = _c(rowptr, np.int32)
@@ -109,8 +128,10 @@ def bicgstab(rowptr, colind, vals, b, tol=1e-8, maxit=20000, x0=None):
     it = ctypes.c_int32(0)
     rr = ctypes.c_double(0.0)
     rt = ctypes.c_double(0.0)
-    st = lib.oracle_bicgstab(n, prp, pci, pv, pb, x.ctypes.data_as(ctypes.c_void_p), float(tol),
-                             int(maxit), 0 if x0 is None else 1, ctypes.byref(it),
+    head = (n, prp, pci, pv, pb, x.ctypes.data_as(ctypes.c_void_p))
+    if ell is not None:
+        head = head + (int(ell),)
+    st = getattr(lib, fname)(*head, float(tol), int(maxit), 0 if x0 is None else 1, ctypes.byref(it),
                              ctypes.byref(rr), ctypes.byref(rt))
     return x, {"status": STATUS.get(st, st), "iters": it.value, "relres_recur": rr.value,
                "relres_true": rt.value}

@@ -172,6 +172,220 @@ int bicgstab(const Csr& A, const cplx* b, cplx* x, double tol, int32_t maxit, in
   return status;
 }
 
+// Transpose-free QMR (Freund 1993; Saad 2003, Algorithm 7.8), the "P-TFQMR"
+// of Section 4 with the identity as preconditioner; complex version, inner
+// products (x, y) = sum conj(x_i) y_i with the shadow vector r~ = r0 as first
+// argument.  One iteration = two half-steps = two products with A.  The
+// quasi-residual bound tau sqrt(m + 1) >= ||r_m|| triggers a true-residual
+// check; the solve stops when ||b - A x|| / ||b|| <= tol.  Breakdown:
+// (r~, v) == 0 or rho == 0 exactly, or a non-finite scalar.
+int tfqmr(const Csr& A, const cplx* b, cplx* x, double tol, int32_t maxit, int use_x0,
+          int32_t* iters_out, double* relres_recur_out, double* relres_true_out) {
+  const int32_t n = A.n;
+  std::vector<cplx> r0(n), w(n), u(n), u_next(n), v(n), Au(n), Au_next(n), d(n), tmp(n);
+  if (!use_x0) for (int32_t i = 0; i < n; ++i) x[i] = cplx(0.0, 0.0);
+  const double bnorm = dznrm2(n, b);
+  *iters_out = 0;
+  *relres_recur_out = 0.0;
+  *relres_true_out = 0.0;
+  if (!std::isfinite(bnorm)) return ST_NONFINITE;
+  if (bnorm == 0.0) {
+    for (int32_t i = 0; i < n; ++i) x[i] = cplx(0.0, 0.0);
+    return ST_OK;
+  }
+  auto true_relres = [&]() {
+    A.apply(x, tmp.data());
+    for (int32_t i = 0; i < n; ++i) tmp[i] = b[i] - tmp[i];
+    return dznrm2(n, tmp.data()) / bnorm;
+  };
+  // w = u = r0 = b - A x ; v = A u ; d = 0
+  A.apply(x, tmp.data());
+  for (int32_t i = 0; i < n; ++i) { r0[i] = b[i] - tmp[i]; w[i] = r0[i]; u[i] = r0[i]; d[i] = 0.0; }
+  A.apply(u.data(), v.data());
+  for (int32_t i = 0; i < n; ++i) Au[i] = v[i];
+  double tau = dznrm2(n, r0.data());
+  double theta = 0.0;
+  cplx eta(0.0, 0.0), alpha(0.0, 0.0);
+  cplx rho = zdotc(n, r0.data(), r0.data());
+  double relres = tau / bnorm;
+  *relres_true_out = relres;
+  if (!std::isfinite(relres)) return ST_NONFINITE;
+  if (relres <= tol) { *relres_recur_out = relres; return ST_OK; }
+  int32_t it = 0;
+  int status = ST_NOT_CONVERGED;
+  for (int64_t m = 0;; ++m) {
+    const bool even = (m % 2) == 0;
+    if (even) {
+      if (it >= maxit) break;
+      ++it;
+      const cplx sigma = zdotc(n, r0.data(), v.data());
+      if (!finite(sigma) || !finite(rho)) { status = ST_NONFINITE; break; }
+      if (sigma == cplx(0.0, 0.0) || rho == cplx(0.0, 0.0)) { status = ST_BREAKDOWN; break; }
+      alpha = rho / sigma;
+      for (int32_t i = 0; i < n; ++i) u_next[i] = u[i] - alpha * v[i];
+    }
+    // w = w - alpha A u ; d = u + (theta^2 / alpha) eta d
+    const cplx dcoef = (theta * theta / alpha) * eta;
+    for (int32_t i = 0; i < n; ++i) {
+      w[i] -= alpha * Au[i];
+      d[i] = u[i] + dcoef * d[i];
+    }
+    theta = dznrm2(n, w.data()) / tau;
+    const double c = 1.0 / std::sqrt(1.0 + theta * theta);
+    tau = tau * theta * c;
+    eta = (c * c) * alpha;
+    if (!std::isfinite(theta) || !std::isfinite(tau) || !finite(eta)) { status = ST_NONFINITE; break; }
+    for (int32_t i = 0; i < n; ++i) x[i] += eta * d[i];
+    relres = tau * std::sqrt(static_cast<double>(m + 2)) / bnorm;
+    if (relres <= tol) {
+      const double rt = true_relres();
+      *relres_true_out = rt;
+      if (rt <= tol) { status = ST_OK; break; }
+    }
+    if (even) {
+      for (int32_t i = 0; i < n; ++i) u[i] = u_next[i];
+      A.apply(u.data(), Au.data());
+    } else {
+      const cplx rho_new = zdotc(n, r0.data(), w.data());
+      if (!finite(rho_new)) { status = ST_NONFINITE; break; }
+      if (rho == cplx(0.0, 0.0)) { status = ST_BREAKDOWN; break; }
+      const cplx beta = rho_new / rho;
+      rho = rho_new;
+      for (int32_t i = 0; i < n; ++i) u[i] = w[i] + beta * u[i];
+      A.apply(u.data(), Au_next.data());
+      for (int32_t i = 0; i < n; ++i) {
+        v[i] = Au_next[i] + beta * (Au[i] + beta * v[i]);
+        Au[i] = Au_next[i];
+      }
+    }
+  }
+  *relres_true_out = true_relres();
+  *iters_out = it;
+  *relres_recur_out = relres;
+  return status;
+}
+
+// BiCGStab(l) (Sleijpen & Fokkema 1993, Algorithm 3.1), the "P-BiCGSTAB(l)"
+// of Section 4 with the identity as preconditioner: l BiCG steps build
+// r_0..r_l, u_0..u_l, then a minimal-residual step over r_1..r_l (modified
+// Gram-Schmidt) updates x, r_0, u_0.  Complex version: (x, y) = sum conj(x_i)
+// y_i, shadow vector r~ = r_0 as first argument of the BiCG inner products;
+// the Gram-Schmidt coefficients are the projections <r_i, r_j> / sigma_i.
+// One iteration = one outer cycle = 2 l products with A.  Stop when the
+// recurrence residual ||r_0|| / ||b|| <= tol, tested after each BiCG step and
+// after the minimal-residual step; the true residual is then recomputed and,
+// as for BiCGStab, the method restarts from x if it exceeds 1.5 tol while
+// iterations remain.  Breakdown: rho0, gamma or sigma_j exactly 0, or a
+// non-finite scalar.
+int bicgstabl(const Csr& A, const cplx* b, cplx* x, int ell, double tol, int32_t maxit, int use_x0,
+              int32_t* iters_out, double* relres_recur_out, double* relres_true_out) {
+  const int32_t n = A.n;
+  if (ell < 1 || ell > 16) return ST_INVALID;
+  std::vector<std::vector<cplx>> r(ell + 1, std::vector<cplx>(n)), u(ell + 1, std::vector<cplx>(n));
+  std::vector<cplx> rt(n), tmp(n);
+  if (!use_x0) for (int32_t i = 0; i < n; ++i) x[i] = cplx(0.0, 0.0);
+  const double bnorm = dznrm2(n, b);
+  *iters_out = 0;
+  *relres_recur_out = 0.0;
+  *relres_true_out = 0.0;
+  if (!std::isfinite(bnorm)) return ST_NONFINITE;
+  if (bnorm == 0.0) {
+    for (int32_t i = 0; i < n; ++i) x[i] = cplx(0.0, 0.0);
+    return ST_OK;
+  }
+  int status = ST_NOT_CONVERGED;
+  int32_t it = 0;
+  double relres = 0.0;
+  std::vector<std::vector<cplx>> tau(ell + 1, std::vector<cplx>(ell + 1));
+  std::vector<double> sigma(ell + 1);
+  std::vector<cplx> g1(ell + 1), g2(ell + 1), g3(ell + 1);  // gamma', gamma, gamma''
+  for (;;) {  // one pass per (re)start
+  A.apply(x, tmp.data());
+  for (int32_t i = 0; i < n; ++i) { r[0][i] = b[i] - tmp[i]; rt[i] = r[0][i]; u[0][i] = 0.0; }
+  cplx rho0(1.0, 0.0), alpha(0.0, 0.0), omega(1.0, 0.0);
+  relres = dznrm2(n, r[0].data()) / bnorm;
+  if (!std::isfinite(relres)) return ST_NONFINITE;
+  if (relres <= tol) status = ST_OK;
+  while (status != ST_OK && it < maxit) {
+    ++it;
+    rho0 = -omega * rho0;
+    bool bad = false;
+    // BiCG part
+    for (int j = 0; j < ell && !bad; ++j) {
+      const cplx rho1 = zdotc(n, rt.data(), r[j].data());
+      if (!finite(rho1)) { status = ST_NONFINITE; bad = true; break; }
+      if (rho0 == cplx(0.0, 0.0)) { status = ST_BREAKDOWN; bad = true; break; }
+      const cplx beta = alpha * rho1 / rho0;
+      rho0 = rho1;
+      for (int i = 0; i <= j; ++i)
+        for (int32_t q = 0; q < n; ++q) u[i][q] = r[i][q] - beta * u[i][q];
+      A.apply(u[j].data(), u[j + 1].data());
+      const cplx gamma = zdotc(n, rt.data(), u[j + 1].data());
+      if (!finite(gamma)) { status = ST_NONFINITE; bad = true; break; }
+      if (gamma == cplx(0.0, 0.0)) { status = ST_BREAKDOWN; bad = true; break; }
+      alpha = rho0 / gamma;
+      for (int i = 0; i <= j; ++i)
+        for (int32_t q = 0; q < n; ++q) r[i][q] -= alpha * u[i + 1][q];
+      A.apply(r[j].data(), r[j + 1].data());
+      for (int32_t q = 0; q < n; ++q) x[q] += alpha * u[0][q];
+      relres = dznrm2(n, r[0].data()) / bnorm;
+      if (!std::isfinite(relres)) { status = ST_NONFINITE; bad = true; break; }
+      if (relres <= tol) { status = ST_OK; bad = true; break; }
+    }
+    if (bad) break;
+    // MR part: modified Gram-Schmidt on r_1..r_l
+    for (int j = 1; j <= ell && !bad; ++j) {
+      for (int i = 1; i < j; ++i) {
+        tau[i][j] = zdotc(n, r[i].data(), r[j].data()) / sigma[i];
+        for (int32_t q = 0; q < n; ++q) r[j][q] -= tau[i][j] * r[i][q];
+      }
+      sigma[j] = zdotc(n, r[j].data(), r[j].data()).real();
+      if (!std::isfinite(sigma[j])) { status = ST_NONFINITE; bad = true; break; }
+      if (sigma[j] == 0.0) { status = ST_BREAKDOWN; bad = true; break; }
+      g1[j] = zdotc(n, r[j].data(), r[0].data()) / sigma[j];
+    }
+    if (bad) break;
+    g2[ell] = g1[ell];
+    omega = g2[ell];
+    for (int j = ell - 1; j >= 1; --j) {
+      cplx acc = g1[j];
+      for (int i = j + 1; i <= ell; ++i) acc -= tau[j][i] * g2[i];
+      g2[j] = acc;
+    }
+    for (int j = 1; j <= ell - 1; ++j) {
+      cplx acc = g2[j + 1];
+      for (int i = j + 1; i <= ell - 1; ++i) acc += tau[j][i] * g2[i + 1];
+      g3[j] = acc;
+    }
+    for (int32_t q = 0; q < n; ++q) {
+      x[q] += g2[1] * r[0][q];
+      r[0][q] -= g1[ell] * r[ell][q];
+      u[0][q] -= g2[ell] * u[ell][q];
+    }
+    for (int j = 1; j <= ell - 1; ++j)
+      for (int32_t q = 0; q < n; ++q) {
+        u[0][q] -= g2[j] * u[j][q];
+        x[q] += g3[j] * r[j][q];
+        r[0][q] -= g1[j] * r[j][q];
+      }
+    if (!finite(omega)) { status = ST_NONFINITE; break; }
+    relres = dznrm2(n, r[0].data()) / bnorm;
+    if (!std::isfinite(relres)) { status = ST_NONFINITE; break; }
+    if (relres <= tol) { status = ST_OK; break; }
+    if (omega == cplx(0.0, 0.0)) { status = ST_BREAKDOWN; break; }
+  }
+  A.apply(x, tmp.data());
+  for (int32_t i = 0; i < n; ++i) tmp[i] = b[i] - tmp[i];
+  const double rtrue = dznrm2(n, tmp.data()) / bnorm;
+  *relres_true_out = rtrue;
+  if (status == ST_OK && rtrue > 1.5 * tol && it < maxit) { status = ST_NOT_CONVERGED; continue; }
+  break;
+  }
+  *iters_out = it;
+  *relres_recur_out = relres;
+  return status;
+}
+
 }  // namespace
 
 extern "C" {
@@ -199,6 +413,24 @@ int oracle_bicgstab(int32_t n, const int32_t* rowptr, const int32_t* colind, con
   Csr A{n, rowptr, colind, reinterpret_cast<const cplx*>(vals)};
   return bicgstab(A, reinterpret_cast<const cplx*>(b), reinterpret_cast<cplx*>(x), tol, maxit,
                   use_x0, iters, relres_recur, relres_true);
+}
+
+int oracle_tfqmr(int32_t n, const int32_t* rowptr, const int32_t* colind, const double* vals, const double* b,
+                 double* x, double tol, int32_t maxit, int use_x0, int32_t* iters, double* relres_recur,
+                 double* relres_true) {
+  if (n < 0 || maxit < 0 || !(tol >= 0.0)) return ST_INVALID;
+  Csr A{n, rowptr, colind, reinterpret_cast<const cplx*>(vals)};
+  return tfqmr(A, reinterpret_cast<const cplx*>(b), reinterpret_cast<cplx*>(x), tol, maxit, use_x0, iters,
+               relres_recur, relres_true);
+}
+
+int oracle_bicgstabl(int32_t n, const int32_t* rowptr, const int32_t* colind, const double* vals,
+                     const double* b, double* x, int ell, double tol, int32_t maxit, int use_x0, int32_t* iters,
+                     double* relres_recur, double* relres_true) {
+  if (n < 0 || maxit < 0 || !(tol >= 0.0)) return ST_INVALID;
+  Csr A{n, rowptr, colind, reinterpret_cast<const cplx*>(vals)};
+  return bicgstabl(A, reinterpret_cast<const cplx*>(b), reinterpret_cast<cplx*>(x), ell, tol, maxit, use_x0, iters,
+                   relres_recur, relres_true);
 }
 
 }  // extern "C"

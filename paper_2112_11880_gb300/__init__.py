@@ -82,6 +82,14 @@ SIGNATURES = {
     "helm_bicgstab_solve": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(helm_opts), ctypes.POINTER(helm_info), _P]),
     "helm_adjoint": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(helm_opts), _P, _P, ctypes.POINTER(helm_info), _P]),
     "helm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "helm_grad_sound_speed": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P, _P, _P, ctypes.c_double, _P, _P]),
+    "helm_assemble_helmholtz": (ctypes.c_int, [ctypes.c_int64, _P, _P, _P, _P, _P, _P, _P, ctypes.c_double, _P,
+                                               _P]),
+    "helm_conj_scale": (ctypes.c_int, [ctypes.c_int64, _P, _P, _P, _P]),
+    "helm_sweep_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, ctypes.c_int64, _P, _P, _P, _P, _P, _P]),
+    "helm_sweep_destroy": (ctypes.c_int, [_P]),
+    "helm_sweep_solve": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, ctypes.c_int32, _P, ctypes.c_int32,
+                                        ctypes.POINTER(helm_opts), _P, _P]),
 }
 
 _lib = None
@@ -237,6 +245,104 @@ def helm_adjoint(handle, u, dLdu, mu, dLdvals=None, opts: Optional[helm_opts] = 
     if st in (HELM_ERR_INVALID, HELM_ERR_CUDA, HELM_ERR_NOMEM):
         raise HelmError(st, "helm_adjoint")
     return info.as_dict()
+
+
+def _host_f64(a):
+    import numpy as np
+    arr = np.ascontiguousarray(a, dtype=np.float64)
+    return arr, arr.ctypes.data_as(ctypes.c_void_p)
+
+
+def helm_grad_sound_speed(dLdvals, elem_map, Me, Bf, top, c, omega, grad, stream=None) -> None:
+    _require_cuda(dLdvals, elem_map, top, c, grad)
+    me, pme = _host_f64(Me)
+    bf, pbf = _host_f64(Bf)
+    if me.size != 64 or bf.size != 64:
+        raise ValueError("Me and Bf must have 64 entries")
+    _check(load_library().helm_grad_sound_speed(c.numel(), _ptr(dLdvals), _ptr(elem_map), pme, pbf, _ptr(top),
+                                                _ptr(c), float(omega), _ptr(grad), _stream(stream)),
+           "helm_grad_sound_speed")
+
+
+def helm_assemble_helmholtz(K, slot_elem, slot_pair, Me, Bf, top, c, omega, vals, stream=None) -> None:
+    _require_cuda(K, slot_elem, slot_pair, top, c, vals)
+    me, pme = _host_f64(Me)
+    bf, pbf = _host_f64(Bf)
+    _check(load_library().helm_assemble_helmholtz(K.numel(), _ptr(K), _ptr(slot_elem), _ptr(slot_pair), pme, pbf,
+                                                  _ptr(top), _ptr(c), float(omega), _ptr(vals), _stream(stream)),
+           "helm_assemble_helmholtz")
+
+
+def helm_conj_scale(alpha, x, y, stream=None) -> None:
+    """y = alpha conj(x) (complex128)."""
+    _require_cuda(x, y)
+    _check(load_library().helm_conj_scale(x.numel(), _c2(alpha), _ptr(x), _ptr(y), _stream(stream)),
+           "helm_conj_scale")
+
+
+def helm_sweep_create(n, nnz, d_rowptr, d_colind, d_K, d_M, d_B, stream=None) -> int:
+    h = _P()
+    _check(load_library().helm_sweep_create(ctypes.byref(h), int(n), int(nnz), d_rowptr, d_colind, d_K, d_M, d_B,
+                                            _stream(stream)), "helm_sweep_create")
+    return h.value
+
+
+def helm_sweep_destroy(handle) -> None:
+    _check(load_library().helm_sweep_destroy(handle), "helm_sweep_destroy")
+
+
+def helm_sweep_solve(handle, omegas, b, X, opts: Optional[helm_opts] = None, stream=None):
+    """Solve all frequencies; b is [n] (shared) or [n, F]; X is [n, F]
+    complex128 (row-major).  Returns a list of per-frequency info dicts."""
+    import numpy as np
+    _require_cuda(b, X)
+    w = np.ascontiguousarray(omegas, dtype=np.float64)
+    F = int(w.size)
+    b_ld = 0 if b.dim() == 1 else int(b.shape[1])
+    infos = (helm_info * F)()
+    o = opts if opts is not None else default_opts()
+    st = load_library().helm_sweep_solve(handle, F, w.ctypes.data_as(ctypes.c_void_p), _ptr(b), b_ld, _ptr(X),
+                                         int(X.shape[1]), ctypes.byref(o), ctypes.cast(infos, ctypes.c_void_p),
+                                         _stream(stream))
+    if st in (HELM_ERR_INVALID, HELM_ERR_CUDA, HELM_ERR_NOMEM):
+        raise HelmError(st, "helm_sweep_solve")
+    return [infos[j].as_dict() for j in range(F)]
+
+
+class Sweep:
+    """Frequency sweep on one pattern: A_j = K - w_j^2 M + i w_j B."""
+
+    def __init__(self, rowptr, colind, K, M, B, device="cuda"):
+        import torch
+        dev = torch.device(device)
+        self.rowptr = torch.as_tensor(rowptr, dtype=torch.int32).to(dev).contiguous()
+        self.colind = torch.as_tensor(colind, dtype=torch.int32).to(dev).contiguous()
+        self.K = torch.as_tensor(K, dtype=torch.float64).to(dev).contiguous()
+        self.M = torch.as_tensor(M, dtype=torch.float64).to(dev).contiguous()
+        self.B = torch.as_tensor(B, dtype=torch.float64).to(dev).contiguous()
+        self.n = self.rowptr.numel() - 1
+        self.nnz = self.colind.numel()
+        self.handle = helm_sweep_create(self.n, self.nnz, _ptr(self.rowptr), _ptr(self.colind), _ptr(self.K),
+                                        _ptr(self.M), _ptr(self.B))
+
+    def solve(self, omegas, b, X=None, **opts):
+        import torch
+        F = len(omegas)
+        if X is None:
+            X = torch.zeros((self.n, F), dtype=torch.complex128, device=b.device)
+        infos = helm_sweep_solve(self.handle, omegas, b, X, default_opts(**opts))
+        return X, infos
+
+    def close(self):
+        if getattr(self, "handle", None):
+            helm_sweep_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def helm_status_string(status: int) -> str:

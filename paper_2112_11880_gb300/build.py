@@ -40,7 +40,7 @@ def _deps():
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or os.environ.get("HELM_NVCC_EXTRA"):
         return False
     t = os.path.getmtime(LIB)
     return all(os.path.getmtime(p) <= t for p in _deps())
@@ -51,7 +51,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
         return LIB
     os.makedirs(os.path.join(OUT_DIR, "obj"), exist_ok=True)
     cc = nvcc()
-    flags = FLAGS + list(extra_flags or [])
+    # HELM_NVCC_EXTRA: extra nvcc flags (engine-shape experiments, e.g. -DHELM_SPLIT=2)
+    flags = FLAGS + list(extra_flags or []) + os.environ.get("HELM_NVCC_EXTRA", "").split()
 
     def compile_one(src):
         obj = os.path.join(OUT_DIR, "obj", os.path.basename(src) + ".o")

@@ -23,22 +23,26 @@ struct AxpbyEpi {
   V* y;
   V alpha, beta;
   int mode;  // 0: y = acc, 1: y = alpha acc, 2: y = alpha acc + beta y
+  V y_old;
+  __device__ __forceinline__ void prefetch(int32_t r) {
+    if (mode == 2) y_old = y[r];
+  }
   __device__ __forceinline__ void row(int32_t r, V acc) {
     if (mode == 0) {
       y[r] = acc;
     } else if (mode == 1) {
       y[r] = cmul(alpha, acc);
     } else {
-      y[r] = cadd(cmul(alpha, acc), cmul(beta, y[r]));
+      y[r] = cadd(cmul(alpha, acc), cmul(beta, y_old));
     }
   }
 };
 
 template <class V>
-__global__ void __launch_bounds__(Engine<V>::R) k_spmv(CsrDev<V> A, const V* __restrict__ x, V* y, V alpha, V beta,
+__global__ void __launch_bounds__(Engine<V>::kThreads) k_spmv(CsrDev<V> A, const V* __restrict__ x, V* y, V alpha, V beta,
                                                        int mode, unsigned int* dev_err) {
   extern __shared__ __align__(16) unsigned char smem[];
-  AxpbyEpi<V> epi{y, alpha, beta, mode};
+  AxpbyEpi<V> epi{y, alpha, beta, mode, vzero<V>()};
   (void)spmv_run<V>(A, x, epi, smem, dev_err);
 }
 
@@ -209,7 +213,7 @@ static helm_status spmv_grid(int32_t n, int* grid) {
   const void* fn = reinterpret_cast<const void*>(&k_spmv<V>);
   HELM_CUDA_TRY(set_smem_attr(fn, Engine<V>::kSmem));
   int per_sm = 0;
-  HELM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmv<V>, R, Engine<V>::kSmem));
+  HELM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmv<V>, Engine<V>::kThreads, Engine<V>::kSmem));
   per_sm = std::max(per_sm, 1);
   const int ntiles = (n + R - 1) / R;
   *grid = std::max(1, std::min(ntiles, per_sm * sm_count()));
@@ -226,7 +230,7 @@ helm_status launch_spmv128(helm_csr A, const double2* x, double2* y, double2 alp
                    : (beta.x == 0.0 && beta.y == 0.0)                                    ? 1
                                                                                          : 2;
   CsrDev<double2> d{A->n, A->nnz, A->rowptr, A->colind, static_cast<const double2*>(A->vals), A->real_blk};
-  k_spmv<double2><<<grid, Engine<double2>::R, Engine<double2>::kSmem, s>>>(d, x, y, alpha, beta, mode, A->dev_err);
+  k_spmv<double2><<<grid, Engine<double2>::kThreads, Engine<double2>::kSmem, s>>>(d, x, y, alpha, beta, mode, A->dev_err);
   HELM_CUDA_TRY(cudaGetLastError());
   return HELM_OK;
 }
@@ -241,13 +245,23 @@ helm_status launch_spmv64(helm_csr A, const float2* vals, const float2* x, float
                    : (beta.x == 0.f && beta.y == 0.f)                                    ? 1
                                                                                          : 2;
   CsrDev<float2> d{A->n, A->nnz, A->rowptr, A->colind, vals, nullptr};
-  k_spmv<float2><<<grid, Engine<float2>::R, Engine<float2>::kSmem, s>>>(d, x, y, alpha, beta, mode, A->dev_err);
+  k_spmv<float2><<<grid, Engine<float2>::kThreads, Engine<float2>::kSmem, s>>>(d, x, y, alpha, beta, mode, A->dev_err);
   HELM_CUDA_TRY(cudaGetLastError());
   return HELM_OK;
 }
 
+// Graphs capture buffer addresses: drop them whenever a buffer is replaced.
+static void drop_graphs(helm_csr A) {
+  for (auto& kv : A->graphs) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+  }
+  A->graphs.clear();
+}
+
 helm_status ensure_vectors(helm_csr A, int nvec) {
   if (A->nvec >= nvec) return HELM_OK;
+  drop_graphs(A);
   if (A->vec) {
     cudaFree(A->vec);
     A->vec = nullptr;
@@ -261,6 +275,7 @@ helm_status ensure_vectors(helm_csr A, int nvec) {
 
 helm_status ensure_vectors32(helm_csr A, int nvec) {
   if (A->nvec32 >= nvec) return HELM_OK;
+  drop_graphs(A);
   if (A->vec32) {
     cudaFree(A->vec32);
     A->vec32 = nullptr;
@@ -516,9 +531,14 @@ helm_status helm_bicgstab_solve(helm_csr A, const void* d_b, void* d_x, const he
   if (!(opts.tol >= 0.0) || opts.maxit < 0) return HELM_ERR_INVALID;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   std::lock_guard<std::mutex> lk(A->mu);
-  if (opts.precision == HELM_PREC_MIXED)
+  if (opts.precision == HELM_PREC_MIXED) {
+    if (opts.method != HELM_BICGSTAB) return HELM_ERR_INVALID;
     return solve_mixed(A, static_cast<const double2*>(d_b), static_cast<double2*>(d_x), opts, info, s);
+  }
   if (opts.precision != HELM_PREC_FP64) return HELM_ERR_INVALID;
+  if (opts.method == HELM_TFQMR)
+    return tfqmr_fp64(A, static_cast<const double2*>(d_b), static_cast<double2*>(d_x), opts, info, s);
+  if (opts.method != HELM_BICGSTAB) return HELM_ERR_INVALID;
   return bicgstab_fp64(A, static_cast<const double2*>(d_b), static_cast<double2*>(d_x), opts, info, s);
 }
 

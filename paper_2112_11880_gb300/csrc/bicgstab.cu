@@ -40,7 +40,7 @@ __global__ void k_configure(SolverState* st, double tol, int32_t maxit, int32_t 
 namespace {
 
 using V = double2;
-constexpr int R = Engine<V>::R;
+constexpr int R = Engine<V>::kThreads;  // threads per SpMV block
 constexpr size_t kSmem = Engine<V>::kSmem;
 
 // Tail: ||b - A x|| / ||b|| (x = 0 when b = 0).
@@ -57,8 +57,10 @@ __global__ void __launch_bounds__(R) k_tail(KArgs<V> a) {
     struct Epi {
       const KArgs<V>* a;
       double part;
-      __device__ __forceinline__ void row(int32_t i, double2 acc) { part = cabs2_acc(csub(a->b[i], acc), part); }
-    } epi{&a, 0.0};
+      double2 bi;
+      __device__ __forceinline__ void prefetch(int32_t i) { bi = a->b[i]; }
+      __device__ __forceinline__ void row(int32_t i, double2 acc) { part = cabs2_acc(csub(bi, acc), part); }
+    } epi{&a, 0.0, make_double2(0.0, 0.0)};
     spmv_run<V>(a.A, a.x, epi, smem, a.dev_err);
     part[0] = epi.part;
   }
@@ -82,7 +84,7 @@ struct TailFp64 {
 
 helm_status bicgstab_fp64(helm_csr A, const double2* b, double2* x, const helm_opts& o, helm_info* info,
                           cudaStream_t s) {
-  helm_status st = ensure_vectors(A, 6);
+  helm_status st = ensure_vectors(A, kNumVec);
   if (st != HELM_OK) return st;
   st = prepare_krylov_kernels<V>();
   if (st != HELM_OK) return st;

@@ -66,6 +66,15 @@ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
     return make_double2((a.x * r + a.y) / d, (a.y * r - a.x) / d);
   }
 }
+// a / b with one real division: a conj(b) / |b|^2 (the scalar recurrences run
+// in one thread between kernels, where every dependent division is latency);
+// Smith's algorithm when |b|^2 under- or overflows.
+__device__ __forceinline__ double2 cdiv_fast(double2 a, double2 b) {
+  const double d = fma(b.x, b.x, b.y * b.y);
+  if (!(d > 0.0) || !isfinite(d) || d < 1e-290) return cdiv(a, b);
+  const double inv = 1.0 / d;
+  return make_double2(fma(a.x, b.x, a.y * b.y) * inv, fma(a.y, b.x, -a.x * b.y) * inv);
+}
 __device__ __forceinline__ bool cfinite(double2 a) { return isfinite(a.x) && isfinite(a.y); }
 __device__ __forceinline__ bool czero(double2 a) { return a.x == 0.0 && a.y == 0.0; }
 

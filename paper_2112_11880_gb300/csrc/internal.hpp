@@ -31,15 +31,22 @@ enum : int32_t { PH_RUN = 0, PH_SCONV = 1, PH_DONE = 2 };
 // Tickets (arrival counters for last-block reductions), one per kernel kind.
 enum : int { TK_INIT = 0, TK_V, TK_S, TK_T, TK_XR, TK_TAIL, TK_AUX0, TK_AUX1, TK_AUX2, TK_AUX3, TK_COUNT };
 
-// SpMV engine shape (measured on GB300, 120x60x50 Q1 matrix): one warp per
-// block, 32-row tiles of up to 28 entries per row staged by one TMA bulk copy
-// each, a single buffer per block and 12 (complex128) to 19 (complex64)
-// blocks per SM overlapping one another.
+// SpMV engine shape (measured on GB300, 120x60x50 Q1 matrix): 32-row tiles
+// of up to 28 entries per row staged by TMA bulk copies into a single buffer
+// per block; each row split over 4 threads in 4 different warps (128-thread
+// blocks, 11 blocks per SM overlapping one another).
 constexpr int kRows128 = 32;
 constexpr int kCap128 = kRows128 * 28;
 constexpr int kRows64 = 32;
 constexpr int kCap64 = kRows64 * 28;
 constexpr int kStages = 1;
+#ifndef HELM_SPLIT
+#define HELM_SPLIT 4
+#endif
+constexpr int kSplit = HELM_SPLIT;
+
+// complex128 Krylov vectors per handle (BiCGStab uses 6, TFQMR 8)
+constexpr int kNumVec = 8;
 
 struct GraphEntry {
   cudaGraphExec_t exec = nullptr;
@@ -112,6 +119,8 @@ helm_status launch_spmv64(helm_csr A, const float2* vals, const float2* x, float
 // Solver entry points implemented in the solver translation units.
 helm_status bicgstab_fp64(helm_csr A, const double2* b, double2* x, const helm_opts& o, helm_info* info,
                           cudaStream_t s);
+helm_status tfqmr_fp64(helm_csr A, const double2* b, double2* x, const helm_opts& o, helm_info* info,
+                       cudaStream_t s);
 helm_status solve_mixed(helm_csr A, const double2* b, double2* x, const helm_opts& o, helm_info* info,
                         cudaStream_t s);
 

@@ -34,12 +34,12 @@ namespace helm {
 template <class V> struct Prec;
 template <> struct Prec<double2> {
   using S = double;
-  static constexpr int R = Engine<double2>::R;
+  static constexpr int R = Engine<double2>::kThreads;  // threads per SpMV block
   __device__ static __forceinline__ double2 cvt(double2 z) { return z; }
 };
 template <> struct Prec<float2> {
   using S = float;
-  static constexpr int R = Engine<float2>::R;
+  static constexpr int R = Engine<float2>::kThreads;  // threads per SpMV block
   __device__ static __forceinline__ float2 cvt(double2 z) {
     return make_float2(static_cast<float>(z.x), static_cast<float>(z.y));
   }
@@ -84,8 +84,10 @@ __global__ void __launch_bounds__(Prec<V>::R) k_init(KArgs<V> a) {
     struct Epi {
       const KArgs<V>* a;
       S part[4];
+      V bpre;
+      __device__ __forceinline__ void prefetch(int32_t i) { bpre = a->b[i]; }
       __device__ __forceinline__ void row(int32_t i, V ax) {
-        const V bi = a->b[i];
+        const V bi = bpre;
         const V ri = csub(bi, ax);
         a->r[i] = ri;
         a->rh[i] = ri;
@@ -100,7 +102,7 @@ __global__ void __launch_bounds__(Prec<V>::R) k_init(KArgs<V> a) {
         part[2] = d.x;
         part[3] = d.y;
       }
-    } epi{&a, {S(0), S(0), S(0), S(0)}};
+    } epi{&a, {S(0), S(0), S(0), S(0)}, vzero<V>()};
     spmv_run<V>(a.A, a.x, epi, smem, a.dev_err);
 #pragma unroll
     for (int k = 0; k < 4; ++k) acc[k] = epi.part[k];
@@ -201,11 +203,13 @@ __global__ void __launch_bounds__(Prec<V>::R) k_v(KArgs<V> a) {
   struct Epi {
     const KArgs<V>* a;
     V part;
+    V rh;
+    __device__ __forceinline__ void prefetch(int32_t i) { rh = a->rh[i]; }
     __device__ __forceinline__ void row(int32_t i, V ax) {
       a->v[i] = ax;
-      part = cfma_conj(a->rh[i], ax, part);
+      part = cfma_conj(rh, ax, part);
     }
-  } epi{&a, vzero<V>()};
+  } epi{&a, vzero<V>(), vzero<V>()};
   spmv_run<V>(a.A, a.p, epi, smem, a.dev_err);
   double part[2] = {double(epi.part.x), double(epi.part.y)};
   double tot[2];
@@ -219,7 +223,7 @@ __global__ void __launch_bounds__(Prec<V>::R) k_v(KArgs<V> a) {
   } else if (czero(rv)) {
     st->status = HELM_ERR_BREAKDOWN;
   } else {
-    const double2 alpha = cdiv(st->rho, rv);
+    const double2 alpha = cdiv_fast(st->rho, rv);
     if (!cfinite(alpha)) st->status = HELM_ERR_NONFINITE;
     else st->alpha = alpha;
   }
@@ -258,12 +262,14 @@ __global__ void __launch_bounds__(kVecThreads) k_s(KArgs<V> a) {
   double tot[1];
   if (!grid_sum_last<1>(part, a.partials, a.tickets + TK_S, red, tot)) return;
   if (threadIdx.x != 0) return;
-  const double snorm = sqrt(tot[0]);
-  if (!isfinite(snorm)) {
+  // ||s|| / ||b|| <= tol compared squared: no square root on the critical path
+  const double s2 = tot[0];
+  const double bt = st->bnorm * st->tol;
+  if (!isfinite(s2)) {
     st->status = HELM_ERR_NONFINITE;
-  } else if (snorm / st->bnorm <= st->tol) {
+  } else if (s2 <= bt * bt) {
     st->phase = PH_SCONV;
-    st->relres = snorm / st->bnorm;
+    st->relres = sqrt(s2) / st->bnorm;
   }
 }
 
@@ -279,12 +285,14 @@ __global__ void __launch_bounds__(Prec<V>::R) k_t(KArgs<V> a) {
     const KArgs<V>* a;
     V ts;
     S tt;
+    V si;
+    __device__ __forceinline__ void prefetch(int32_t i) { si = a->s[i]; }
     __device__ __forceinline__ void row(int32_t i, V ax) {
       a->t[i] = ax;
-      ts = cfma_conj(ax, a->s[i], ts);
+      ts = cfma_conj(ax, si, ts);
       tt = cabs2_acc(ax, tt);
     }
-  } epi{&a, vzero<V>(), S(0)};
+  } epi{&a, vzero<V>(), S(0), vzero<V>()};
   spmv_run<V>(a.A, a.s, epi, smem, a.dev_err);
   double part[3] = {double(epi.ts.x), double(epi.ts.y), double(epi.tt)};
   double tot[3];
@@ -298,7 +306,8 @@ __global__ void __launch_bounds__(Prec<V>::R) k_t(KArgs<V> a) {
   } else if (tt == 0.0) {
     st->status = HELM_ERR_BREAKDOWN;
   } else {
-    const double2 omega = make_double2(ts.x / tt, ts.y / tt);
+    const double inv_tt = 1.0 / tt;
+    const double2 omega = make_double2(ts.x * inv_tt, ts.y * inv_tt);
     if (!cfinite(omega)) st->status = HELM_ERR_NONFINITE;
     else st->omega = omega;
   }
@@ -360,11 +369,13 @@ __global__ void __launch_bounds__(kVecThreads) k_xr(KArgs<V> a) {
     status = HELM_OK;
     st->phase = PH_DONE;
   } else {
-    const double relres = sqrt(tot[2]) / st->bnorm;
-    st->relres = relres;
-    if (!isfinite(relres)) {
+    // ||r|| / ||b|| <= tol compared squared; the square root is taken for the
+    // report only when the loop stops
+    const double r2 = tot[2];
+    const double bt = st->bnorm * st->tol;
+    if (!isfinite(r2)) {
       status = HELM_ERR_NONFINITE;
-    } else if (relres <= st->tol) {
+    } else if (r2 <= bt * bt) {
       status = HELM_OK;
     } else if (czero(omega64)) {
       status = HELM_ERR_BREAKDOWN;
@@ -374,7 +385,8 @@ __global__ void __launch_bounds__(kVecThreads) k_xr(KArgs<V> a) {
       status = HELM_ERR_TIMEOUT;
     } else {
       const double2 rho_new = make_double2(tot[0], tot[1]);
-      const double2 beta = cmul(cdiv(rho_new, st->rho), cdiv(alpha64, omega64));
+      // beta = (rho_new / rho) (alpha / omega) = (rho_new alpha) / (rho omega)
+      const double2 beta = cdiv_fast(cmul(rho_new, alpha64), cmul(st->rho, omega64));
       if (!cfinite(rho_new) || !cfinite(beta)) {
         status = HELM_ERR_NONFINITE;
         st->iter += 1;
@@ -387,6 +399,7 @@ __global__ void __launch_bounds__(kVecThreads) k_xr(KArgs<V> a) {
       }
     }
   }
+  if (phase != PH_SCONV && status != ST_RUNNING) st->relres = sqrt(tot[2]) / st->bnorm;
   st->status = status;
   set_cond(a, status == ST_RUNNING);
 }
@@ -429,7 +442,7 @@ inline helm_status krylov_shapes(helm_csr A, KShapes<V>* sh) {
   int per_sm = 0;
   HELM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_v<V>, Prec<V>::R, smem));
   per_sm = per_sm < 1 ? 1 : per_sm;
-  const int ntiles = (A->n + Prec<V>::R - 1) / Prec<V>::R;
+  const int ntiles = (A->n + Engine<V>::R - 1) / Engine<V>::R;
   int g = per_sm * A->num_sms;
   sh->spmv_grid = ntiles < g ? (ntiles < 1 ? 1 : ntiles) : g;
   sh->vec_grid = A->vec_grid;
@@ -448,10 +461,11 @@ inline helm_status krylov_shapes(helm_csr A, KShapes<V>* sh) {
   return st;
 }
 
-// Build a graph  init -> while(body) [-> tail]  for fixed vectors.  `tail`
-// enqueues the kernels after the loop (may be empty).
-template <class V, class Tail>
-helm_status build_krylov_graph(const KArgs<V>& base, const KShapes<V>& sh, Tail tail, GraphEntry* out) {
+// Build a graph  init -> while(body) -> tail.  Each callable enqueues its
+// kernels on the capture stream with the loop's conditional handle:
+// init(cond, stream), body(cond, stream), tail(cond, stream).
+template <class Init, class Body, class Tail>
+helm_status build_while_graph(Init init, Body body, Tail tail, GraphEntry* out) {
   cudaStream_t cs = nullptr;
   HELM_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   cudaGraph_t graph = nullptr;
@@ -461,13 +475,10 @@ helm_status build_krylov_graph(const KArgs<V>& base, const KShapes<V>& sh, Tail 
     if (cudaGraphCreate(&graph, 0) != cudaSuccess) break;
     cudaGraphConditionalHandle cond;
     if (cudaGraphConditionalHandleCreate(&cond, graph, 1u, cudaGraphCondAssignDefault) != cudaSuccess) break;
-    KArgs<V> a = base;
-    a.cond = cond;
-    a.has_cond = 1;
     if (cudaStreamBeginCaptureToGraph(cs, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
         cudaSuccess)
       break;
-    enqueue_init(a, sh, cs);
+    init(cond, cs);
     cudaStreamCaptureStatus cst;
     const cudaGraphNode_t* deps = nullptr;
     size_t ndeps = 0;
@@ -482,16 +493,16 @@ helm_status build_krylov_graph(const KArgs<V>& base, const KShapes<V>& sh, Tail 
     cp.conditional.size = 1;
     cudaGraphNode_t wnode;
     if (cudaGraphAddNode(&wnode, graph, &init_node, nullptr, 1, &cp) != cudaSuccess) break;
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
-    if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+    cudaGraph_t bodyg = cp.conditional.phGraph_out[0];
+    if (cudaStreamBeginCaptureToGraph(cs, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
         cudaSuccess)
       break;
-    enqueue_body(a, sh, cs);
+    body(cond, cs);
     if (cudaStreamEndCapture(cs, &tmp) != cudaSuccess) break;
     if (cudaStreamBeginCaptureToGraph(cs, graph, &wnode, nullptr, 1, cudaStreamCaptureModeThreadLocal) !=
         cudaSuccess)
       break;
-    tail(a, cs);
+    tail(cond, cs);
     if (cudaStreamEndCapture(cs, &tmp) != cudaSuccess) break;
     if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) break;
     result = HELM_OK;
@@ -506,6 +517,20 @@ helm_status build_krylov_graph(const KArgs<V>& base, const KShapes<V>& sh, Tail 
   out->exec = exec;
   out->graph = graph;
   return HELM_OK;
+}
+
+// BiCGStab graph  init -> while(K1..K5) -> tail  for fixed vectors.
+template <class V, class Tail>
+helm_status build_krylov_graph(const KArgs<V>& base, const KShapes<V>& sh, Tail tail, GraphEntry* out) {
+  auto with = [&](cudaGraphConditionalHandle cond) {
+    KArgs<V> a = base;
+    a.cond = cond;
+    a.has_cond = 1;
+    return a;
+  };
+  return build_while_graph([&](cudaGraphConditionalHandle c, cudaStream_t s) { enqueue_init(with(c), sh, s); },
+                           [&](cudaGraphConditionalHandle c, cudaStream_t s) { enqueue_body(with(c), sh, s); },
+                           [&](cudaGraphConditionalHandle c, cudaStream_t s) { tail(with(c), s); }, out);
 }
 
 // Run init -> loop -> tail once: through the cached graph when there is one,

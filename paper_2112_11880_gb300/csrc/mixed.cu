@@ -23,7 +23,7 @@ namespace helm {
 
 namespace {
 
-constexpr int R128 = Engine<double2>::R;
+constexpr int R128 = Engine<double2>::kThreads;  // threads per SpMV block
 constexpr size_t kSmem128 = Engine<double2>::kSmem;
 
 struct IrArgs {
@@ -56,14 +56,16 @@ __global__ void __launch_bounds__(R128) k_ir_residual(IrArgs a, int zero_x) {
     struct Epi {
       const IrArgs* a;
       double r2, b2;
+      double2 bpre;
+      __device__ __forceinline__ void prefetch(int32_t i) { bpre = a->b[i]; }
       __device__ __forceinline__ void row(int32_t i, double2 ax) {
-        const double2 bi = a->b[i];
+        const double2 bi = bpre;
         const double2 ri = csub(bi, ax);
         a->r[i] = ri;
         r2 = cabs2_acc(ri, r2);
         b2 = cabs2_acc(bi, b2);
       }
-    } epi{&a, 0.0, 0.0};
+    } epi{&a, 0.0, 0.0, make_double2(0.0, 0.0)};
     spmv_run<double2>(a.A, a.x, epi, smem, a.dev_err);
     part[0] = epi.r2;
     part[1] = epi.b2;
@@ -110,7 +112,7 @@ struct NoTail {
 helm_status solve_mixed(helm_csr A, const double2* b, double2* x, const helm_opts& o, helm_info* info,
                         cudaStream_t s) {
   helm_status st = ensure_vals32(A, s);
-  if (st == HELM_OK) st = ensure_vectors(A, 6);
+  if (st == HELM_OK) st = ensure_vectors(A, kNumVec);
   if (st == HELM_OK) st = ensure_vectors32(A, 8);
   if (st == HELM_OK) st = prepare_krylov_kernels<float2>();
   if (st != HELM_OK) return st;
@@ -123,7 +125,7 @@ helm_status solve_mixed(helm_csr A, const double2* b, double2* x, const helm_opt
     int per_sm = 0;
     HELM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ir_residual, R128, kSmem128));
     per_sm = per_sm < 1 ? 1 : per_sm;
-    const int ntiles = (A->n + R128 - 1) / R128;
+    const int ntiles = (A->n + Engine<double2>::R - 1) / Engine<double2>::R;
     grid128 = per_sm * A->num_sms;
     if (ntiles < grid128) grid128 = ntiles < 1 ? 1 : ntiles;
   }

@@ -85,7 +85,9 @@ struct SpmvStage {
 template <class V> __device__ __forceinline__ V vadd(V a, V b) { return cadd(a, b); }
 
 // Walk this block's tiles; call epi.row(r, acc) for each row r with
-// acc = sum_k vals[k] * x[colind[k]].  Returns false if a bulk copy never
+// acc = sum_k vals[k] * x[colind[k]].  epi.prefetch(r) is called by the same
+// thread before the row's sum starts, so the epilogue can issue its own loads
+// early.  Returns false if a bulk copy never
 // completed (error flag set).  Must be called by all threads of the block.
 //
 // STAGES = 2: the copy of a block's next tile overlaps the current tile.
@@ -191,6 +193,7 @@ __device__ __forceinline__ bool spmv_tiles(const CsrDev<V>& A, const V* __restri
     const int32_t r = tile * R + lrow;
     const bool row_ok = r < min(tile * R + R, n);
     V acc_split = vzero<V>();
+    if (row_ok && part == 0) epi.prefetch(r);  // epilogue operands load under the row's gathers
     if (row_ok) {
       const int64_t k0 = A.rowptr[r] + part, k1 = A.rowptr[r + 1];
       constexpr int KS = SPLIT;
@@ -280,6 +283,7 @@ __device__ __forceinline__ void spmv_lanes(const CsrDev<V>& A, const V* __restri
     const int64_t r = base + lane / LANES;
     const bool valid = r < A.n;
     V acc = vzero<V>();
+    if (valid && sub == 0) epi.prefetch(static_cast<int32_t>(r));
     if (valid) {
       const int64_t k0 = A.rowptr[r], k1 = A.rowptr[r + 1];
       bool real_done = false;
@@ -310,17 +314,19 @@ __device__ __forceinline__ void spmv_lanes(const CsrDev<V>& A, const V* __restri
 // The engine configuration every SpMV-shaped kernel of the library uses.
 template <class V> struct Engine;
 template <> struct Engine<double2> {
-  static constexpr int R = kRows128, CAP = kCap128;
+  static constexpr int R = kRows128, CAP = kCap128, SPLIT = kSplit;
+  static constexpr int kThreads = R * SPLIT;
   static constexpr size_t kSmem = SpmvStage<double2, CAP, kStages>::kBytes;
 };
 template <> struct Engine<float2> {
-  static constexpr int R = kRows64, CAP = kCap64;
+  static constexpr int R = kRows64, CAP = kCap64, SPLIT = kSplit;
+  static constexpr int kThreads = R * SPLIT;
   static constexpr size_t kSmem = SpmvStage<float2, CAP, kStages>::kBytes;
 };
 template <class V, class Epi>
 __device__ __forceinline__ bool spmv_run(const CsrDev<V>& A, const V* __restrict__ x, Epi& epi, unsigned char* smem,
                                          unsigned int* dev_err) {
-  return spmv_tiles<V, Engine<V>::R, Engine<V>::CAP, Epi, kStages, 1>(A, x, epi, smem, dev_err);
+  return spmv_tiles<V, Engine<V>::R, Engine<V>::CAP, Epi, kStages, 1, Engine<V>::SPLIT>(A, x, epi, smem, dev_err);
 }
 
 }  // namespace helm

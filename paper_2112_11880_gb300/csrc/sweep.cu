@@ -1,0 +1,898 @@
+// Batched frequency sweep: BiCGStab for F frequencies on one sparsity pattern,
+// A_j = K - w_j^2 M + i w_j B formed on the fly (the Helmholtz operator of
+// Section 1 at wavenumbers k = w_j / c, with the impedance term).
+//
+// Layout: every Krylov vector is node-major, frequency-minor: V[i * Fp + j],
+// Fp = F rounded up to a multiple of 32.  A warp owns one row and 32
+// frequencies: the row's K, M, B values and column indices are warp-uniform
+// loads (one transaction serves 32 frequencies), each gathered V[col][j..j+31]
+// is one 512-byte coalesced access, and every FP64 instruction does useful
+// work in all 32 lanes.  Per stored entry and frequency the work is 1 FMA to
+// form Re(A_j) = K - w_j^2 M and 2 FMA for the real x complex product (rows
+// whose 32-row block has B = 0), or the complex product where B != 0.
+//
+// All per-frequency scalars (rho, alpha, omega, beta, norms, status, counts)
+// live on the device; each dot product is a per-frequency partial sum per
+// block, added in block order by the last block to arrive.  A frequency that
+// has converged (or failed) is frozen: its lanes do no arithmetic and write
+// nothing, and a 32-frequency group whose frequencies have all stopped is
+// skipped by every kernel.  The loop is one CUDA graph (conditional WHILE
+// node), as for the single solve.
+//
+// Tile shape autotuning: at creation the sweep times the batched SpMV with
+// 4, 8 and 16 warps per block on the actual matrix and keeps the fastest.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.hpp"
+
+namespace helm {
+
+namespace {
+
+constexpr int kMaxF = 128;  // frequencies per sweep (<= threads per block: one thread per frequency)
+
+struct SweepDev {
+  int32_t n;
+  int64_t nnz;
+  const int32_t* rowptr;
+  const int32_t* colind;
+  const double* K;
+  const double* M;
+  const double* B;
+  const uint8_t* bzero_blk;  // [ceil(n / 32)]: 1 when B = 0 on every entry of the 32-row block
+};
+
+struct SweepArgs {
+  SweepDev A;
+  int32_t F, Fp, G;      // frequencies, padded count, 32-frequency groups
+  const double* w;       // [Fp] angular frequencies (padding: 0)
+  const double2* b;      // right-hand side: b[i * b_ld + j], or b[i] for all j when b_ld = 0
+  int32_t b_ld;          // 0 (one b for all frequencies) or Fp
+  double2 *x, *r, *rh, *p, *v, *s, *t;  // [n][Fp]
+  double2 *rho, *alpha, *omg, *beta;    // [Fp]
+  double *bnorm, *relres, *relres_true; // [Fp]
+  int32_t *status, *iters, *phase;      // [Fp]
+  int32_t* gactive;                     // [G]: a frequency of the group is running
+  SolverState* st;                      // tol, maxit, deadline, use_x0
+  double* partials;                     // [blocks][Fp][K]
+  unsigned int* tickets;
+  unsigned int* dev_err;
+  cudaGraphConditionalHandle cond;
+  int has_cond;
+};
+
+__device__ __forceinline__ void sweep_set_cond(const SweepArgs& a, bool cont) {
+  if (a.has_cond) cudaGraphSetConditional(a.cond, cont ? 1u : 0u);
+}
+
+// Per-frequency partial sums of one block: each warp's lanes hold the partials
+// of frequencies g*32 + lane (g = the warp's group); warps with the same group
+// are added in warp order through shared memory, then one value per (block,
+// frequency) goes to `partials`.  The last block adds the partials of all
+// blocks in block order; there thread j < Fp owns frequency j's totals in
+// tot[].  Requires Fp <= blockDim.x.  `sh` holds (warps per block) * 32 * K
+// doubles.
+template <int K>
+__device__ bool sweep_grid_sum(const SweepArgs& a, const double (&v)[K], double* sh, unsigned int* ticket,
+                               double (&tot)[K]) {
+  __shared__ bool s_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) sh[(warp * 32 + lane) * K + k] = v[k];
+  __syncthreads();
+  const int j = threadIdx.x;
+  if (j < a.Fp) {
+    double acc[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = 0.0;
+    for (int w = 0; w < nw; ++w) {
+      const int gw = static_cast<int>((static_cast<int64_t>(blockIdx.x) * nw + w) % a.G);
+      if (gw != j / 32) continue;
+#pragma unroll
+      for (int k = 0; k < K; ++k) acc[k] += sh[(w * 32 + (j & 31)) * K + k];
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) a.partials[(static_cast<size_t>(blockIdx.x) * a.Fp + j) * K + k] = acc[k];
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+#pragma unroll
+  for (int k = 0; k < K; ++k) tot[k] = 0.0;
+  if (j < a.Fp) {
+    for (unsigned int bb = 0; bb < gridDim.x; ++bb) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) tot[k] += ld_cg(&a.partials[(static_cast<size_t>(bb) * a.Fp + j) * K + k]);
+    }
+  }
+  if (threadIdx.x == 0) *ticket = 0u;
+  return true;
+}
+
+// Batched SpMV over the warp's (row, group) units: acc[j] = sum_k A_j[k] x[col][j].
+// Calls epi(i, lane_frequency, acc) for running frequencies.
+template <class Epi>
+__device__ __forceinline__ void sweep_spmv(const SweepArgs& a, const double2* __restrict__ x, Epi& epi) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+  const int64_t units = static_cast<int64_t>(a.A.n) * a.G;
+  // a warp keeps the same group for all its units when nwarps is a multiple
+  // of G (the launcher guarantees it), so its lane frequency is fixed
+  const int g = static_cast<int>(gw % a.G);
+  const int j = g * 32 + lane;
+  const bool grp_on = a.gactive[g] != 0;
+  const bool run = grp_on && j < a.F && a.status[j] == ST_RUNNING;
+  const double wj = a.w[j];
+  const double w2 = wj * wj;
+  for (int64_t u = gw; u < units; u += nwarps) {
+    if (!grp_on) break;
+    const int32_t i = static_cast<int32_t>(u / a.G);
+    const int64_t k0 = __ldg(a.A.rowptr + i), k1 = __ldg(a.A.rowptr + i + 1);
+    double2 acc = make_double2(0.0, 0.0);
+    const bool real_rows = a.A.bzero_blk[i >> 5] != 0;
+    if (real_rows) {
+#pragma unroll 4
+      for (int64_t k = k0; k < k1; ++k) {
+        const int32_t c = __ldg(a.A.colind + k);
+        const double are = fma(-w2, __ldg(a.A.M + k), __ldg(a.A.K + k));
+        const double2 xv = __ldg(x + static_cast<size_t>(c) * a.Fp + j);
+        acc.x = fma(are, xv.x, acc.x);
+        acc.y = fma(are, xv.y, acc.y);
+      }
+    } else {
+#pragma unroll 2
+      for (int64_t k = k0; k < k1; ++k) {
+        const int32_t c = __ldg(a.A.colind + k);
+        const double2 av = make_double2(fma(-w2, __ldg(a.A.M + k), __ldg(a.A.K + k)), wj * __ldg(a.A.B + k));
+        acc = cfma(av, __ldg(x + static_cast<size_t>(c) * a.Fp + j), acc);
+      }
+    }
+    if (run) epi(i, j, acc);
+  }
+}
+
+__global__ void k_sw_configure(SweepArgs a, double tol, int32_t maxit, int32_t use_x0, double deadline_s) {
+  SolverState* st = a.st;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->tol = tol;
+    st->maxit = maxit;
+    st->use_x0 = use_x0;
+    st->deadline_ns = deadline_s > 0.0 ? static_cast<unsigned long long>(deadline_s * 1e9) : 0ull;
+    st->t0 = globaltimer_ns();
+    st->status = ST_RUNNING;
+  }
+  for (int j = threadIdx.x; j < a.Fp; j += blockDim.x) {
+    a.status[j] = j < a.F ? ST_RUNNING : HELM_OK;
+    a.iters[j] = 0;
+    a.phase[j] = PH_RUN;
+    a.relres[j] = 0.0;
+    a.relres_true[j] = 0.0;
+    const double2 one = make_double2(1.0, 0.0);
+    a.rho[j] = one;
+    a.alpha[j] = one;
+    a.omg[j] = one;
+    a.beta[j] = make_double2(0.0, 0.0);
+  }
+  for (int g = threadIdx.x; g < a.G; g += blockDim.x) a.gactive[g] = 1;
+}
+
+// Update the group flags and the loop condition from the per-frequency status
+// (thread 0 of the last block of a reduction kernel, after the statuses are set).
+__device__ void sweep_refresh_groups(const SweepArgs& a) {
+  bool any = false;
+  for (int g = 0; g < a.G; ++g) {
+    bool on = false;
+    for (int l = 0; l < 32; ++l) on |= a.status[g * 32 + l] == ST_RUNNING;
+    a.gactive[g] = on ? 1 : 0;
+    any |= on;
+  }
+  a.st->status = any ? ST_RUNNING : HELM_OK;
+  sweep_set_cond(a, any);
+}
+
+// init: r = b - A_j x (or r = b, x = 0), r^ = r, p = v = 0; ||b||, ||r||, rho
+__global__ void __launch_bounds__(256) k_sw_init(SweepArgs a) {
+  extern __shared__ double sh[];
+  const int use_x0 = a.st->use_x0;
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int g = static_cast<int>(gw % a.G);
+  const int j = g * 32 + lane;
+  double part[4] = {0.0, 0.0, 0.0, 0.0};
+  auto body = [&](int32_t i, int jj, double2 ax) {
+    const size_t idx = static_cast<size_t>(i) * a.Fp + jj;
+    const double2 bi = a.b[a.b_ld ? static_cast<size_t>(i) * a.b_ld + jj : static_cast<size_t>(i)];
+    const double2 ri = csub(bi, ax);
+    a.r[idx] = ri;
+    a.rh[idx] = ri;
+    a.p[idx] = make_double2(0.0, 0.0);
+    a.v[idx] = make_double2(0.0, 0.0);
+    part[0] = cabs2_acc(bi, part[0]);
+    part[1] = cabs2_acc(ri, part[1]);
+    double2 d = cfma_conj(ri, ri, make_double2(part[2], part[3]));
+    part[2] = d.x;
+    part[3] = d.y;
+  };
+  if (use_x0) {
+    sweep_spmv(a, a.x, body);
+  } else {
+    const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    const bool run = j < a.F;
+    for (int64_t u = gw; u < static_cast<int64_t>(a.A.n) * a.G; u += nwarps) {
+      const int32_t i = static_cast<int32_t>(u / a.G);
+      if (run) {
+        a.x[static_cast<size_t>(i) * a.Fp + j] = make_double2(0.0, 0.0);
+        body(i, j, make_double2(0.0, 0.0));
+      }
+    }
+  }
+  double tot[4];
+  if (!sweep_grid_sum<4>(a, part, sh, a.tickets + TK_INIT, tot)) return;
+  for (int jj = threadIdx.x; jj < a.F && jj == (int)threadIdx.x; jj += blockDim.x) {
+    const double bn = sqrt(tot[0]);
+    a.bnorm[jj] = bn;
+    int status = ST_RUNNING;
+    if (!isfinite(bn)) {
+      status = HELM_ERR_NONFINITE;
+    } else if (bn == 0.0) {
+      status = HELM_OK;
+    } else {
+      const double rr = sqrt(tot[1]) / bn;
+      a.relres[jj] = rr;
+      const double2 rho = make_double2(tot[2], tot[3]);
+      if (!isfinite(rr)) status = HELM_ERR_NONFINITE;
+      else if (rr <= a.st->tol) status = HELM_OK;
+      else if (a.st->maxit <= 0) status = HELM_ERR_NOT_CONVERGED;
+      else if (!cfinite(rho)) { status = HELM_ERR_NONFINITE; a.iters[jj] = 1; }
+      else if (czero(rho)) { status = HELM_ERR_BREAKDOWN; a.iters[jj] = 1; }
+      else { a.rho[jj] = rho; a.beta[jj] = rho; }
+    }
+    a.status[jj] = status;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) sweep_refresh_groups(a);
+}
+
+// element-wise kernels walk (row, group) units like the SpMV, 32 frequencies per warp
+#define SWEEP_ELEMENTWISE_BEGIN                                                          \
+  const int lane = threadIdx.x & 31;                                                     \
+  const int64_t gw = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; \
+  const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;            \
+  const int g = static_cast<int>(gw % a.G);                                              \
+  const int j = g * 32 + lane;                                                           \
+  const bool grp_on = a.gactive[g] != 0;                                                 \
+  const bool run = grp_on && j < a.F && a.status[j] == ST_RUNNING;
+
+// K1: p = r + beta (p - omega v)
+__global__ void __launch_bounds__(256) k_sw_p(SweepArgs a) {
+  SWEEP_ELEMENTWISE_BEGIN
+  if (!run) return;
+  const double2 beta = a.beta[j], omg = a.omg[j];
+  for (int64_t u = gw; u < static_cast<int64_t>(a.A.n) * a.G; u += nwarps) {
+    const size_t idx = static_cast<size_t>(u / a.G) * a.Fp + j;
+    a.p[idx] = cfma(beta, cfms(omg, a.v[idx], a.p[idx]), a.r[idx]);
+  }
+}
+
+// K2: v = A_j p, (r^, v) -> alpha
+__global__ void __launch_bounds__(256) k_sw_v(SweepArgs a) {
+  extern __shared__ double sh[];
+  if (a.st->status != ST_RUNNING) return;
+  const int64_t gw = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int g = static_cast<int>(gw % a.G);
+  double part[2] = {0.0, 0.0};
+  auto body = [&](int32_t i, int j, double2 ax) {
+    const size_t idx = static_cast<size_t>(i) * a.Fp + j;
+    a.v[idx] = ax;
+    double2 d = cfma_conj(a.rh[idx], ax, make_double2(part[0], part[1]));
+    part[0] = d.x;
+    part[1] = d.y;
+  };
+  sweep_spmv(a, a.p, body);
+  double tot[2];
+  if (!sweep_grid_sum<2>(a, part, sh, a.tickets + TK_V, tot)) return;
+  for (int j = threadIdx.x; j < a.F && j == (int)threadIdx.x; j += blockDim.x) {
+    if (a.status[j] != ST_RUNNING) continue;
+    a.iters[j] += 1;
+    const double2 rv = make_double2(tot[0], tot[1]);
+    if (!cfinite(rv)) a.status[j] = HELM_ERR_NONFINITE;
+    else if (czero(rv)) a.status[j] = HELM_ERR_BREAKDOWN;
+    else {
+      const double2 al = cdiv(a.rho[j], rv);
+      if (!cfinite(al)) a.status[j] = HELM_ERR_NONFINITE;
+      else a.alpha[j] = al;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) sweep_refresh_groups(a);
+}
+
+// K3: s = r - alpha v, ||s||
+__global__ void __launch_bounds__(256) k_sw_s(SweepArgs a) {
+  extern __shared__ double sh[];
+  if (a.st->status != ST_RUNNING) return;
+  SWEEP_ELEMENTWISE_BEGIN
+  double part[1] = {0.0};
+  if (run) {
+    const double2 al = a.alpha[j];
+    for (int64_t u = gw; u < static_cast<int64_t>(a.A.n) * a.G; u += nwarps) {
+      const size_t idx = static_cast<size_t>(u / a.G) * a.Fp + j;
+      const double2 si = cfms(al, a.v[idx], a.r[idx]);
+      a.s[idx] = si;
+      part[0] = cabs2_acc(si, part[0]);
+    }
+  }
+  double tot[1];
+  if (!sweep_grid_sum<1>(a, part, sh, a.tickets + TK_S, tot)) return;
+  for (int jj = threadIdx.x; jj < a.F && jj == (int)threadIdx.x; jj += blockDim.x) {
+    if (a.status[jj] != ST_RUNNING) continue;
+    const double sn = sqrt(tot[0]);
+    if (!isfinite(sn)) a.status[jj] = HELM_ERR_NONFINITE;
+    else if (sn / a.bnorm[jj] <= a.st->tol) {
+      a.phase[jj] = PH_SCONV;
+      a.relres[jj] = sn / a.bnorm[jj];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) sweep_refresh_groups(a);
+}
+
+// K4: t = A_j s, (t, s), (t, t) -> omega (frequencies stopped at s skip)
+__global__ void __launch_bounds__(256) k_sw_t(SweepArgs a) {
+  extern __shared__ double sh[];
+  if (a.st->status != ST_RUNNING) return;
+  const int64_t gw = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int g = static_cast<int>(gw % a.G);
+  double part[3] = {0.0, 0.0, 0.0};
+  auto body = [&](int32_t i, int j, double2 ax) {
+    if (a.phase[j] != PH_RUN) return;
+    const size_t idx = static_cast<size_t>(i) * a.Fp + j;
+    a.t[idx] = ax;
+    double2 d = cfma_conj(ax, a.s[idx], make_double2(part[0], part[1]));
+    part[0] = d.x;
+    part[1] = d.y;
+    part[2] = cabs2_acc(ax, part[2]);
+  };
+  sweep_spmv(a, a.s, body);
+  double tot[3];
+  if (!sweep_grid_sum<3>(a, part, sh, a.tickets + TK_T, tot)) return;
+  for (int j = threadIdx.x; j < a.F && j == (int)threadIdx.x; j += blockDim.x) {
+    if (a.status[j] != ST_RUNNING || a.phase[j] != PH_RUN) continue;
+    const double2 ts = make_double2(tot[0], tot[1]);
+    const double tt = tot[2];
+    if (!cfinite(ts) || !isfinite(tt)) a.status[j] = HELM_ERR_NONFINITE;
+    else if (tt == 0.0) a.status[j] = HELM_ERR_BREAKDOWN;
+    else {
+      const double2 om = make_double2(ts.x / tt, ts.y / tt);
+      if (!cfinite(om)) a.status[j] = HELM_ERR_NONFINITE;
+      else a.omg[j] = om;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) sweep_refresh_groups(a);
+}
+
+// K5: x += alpha p + omega s, r = s - omega t; per-frequency stop tests
+__global__ void __launch_bounds__(256) k_sw_xr(SweepArgs a) {
+  extern __shared__ double sh[];
+  if (a.st->status != ST_RUNNING) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) sweep_set_cond(a, false);
+    return;
+  }
+  SWEEP_ELEMENTWISE_BEGIN
+  double part[3] = {0.0, 0.0, 0.0};
+  if (run) {
+    const double2 al = a.alpha[j], om = a.omg[j];
+    const bool sconv = a.phase[j] == PH_SCONV;
+    for (int64_t u = gw; u < static_cast<int64_t>(a.A.n) * a.G; u += nwarps) {
+      const size_t idx = static_cast<size_t>(u / a.G) * a.Fp + j;
+      if (sconv) {
+        a.x[idx] = cfma(al, a.p[idx], a.x[idx]);
+      } else {
+        const double2 si = a.s[idx];
+        a.x[idx] = cfma(om, si, cfma(al, a.p[idx], a.x[idx]));
+        const double2 ri = cfms(om, a.t[idx], si);
+        a.r[idx] = ri;
+        double2 d = cfma_conj(a.rh[idx], ri, make_double2(part[0], part[1]));
+        part[0] = d.x;
+        part[1] = d.y;
+        part[2] = cabs2_acc(ri, part[2]);
+      }
+    }
+  }
+  double tot[3];
+  if (!sweep_grid_sum<3>(a, part, sh, a.tickets + TK_XR, tot)) return;
+  const bool late = a.st->deadline_ns != 0ull && (globaltimer_ns() - a.st->t0) > a.st->deadline_ns;
+  for (int jj = threadIdx.x; jj < a.F && jj == (int)threadIdx.x; jj += blockDim.x) {
+    if (a.status[jj] != ST_RUNNING) continue;
+    if (a.phase[jj] == PH_SCONV) {
+      a.status[jj] = HELM_OK;
+      a.phase[jj] = PH_DONE;
+      continue;
+    }
+    const double rr = sqrt(tot[2]) / a.bnorm[jj];
+    a.relres[jj] = rr;
+    const double2 om = a.omg[jj];
+    if (!isfinite(rr)) a.status[jj] = HELM_ERR_NONFINITE;
+    else if (rr <= a.st->tol) a.status[jj] = HELM_OK;
+    else if (czero(om)) a.status[jj] = HELM_ERR_BREAKDOWN;
+    else if (a.iters[jj] >= a.st->maxit) a.status[jj] = HELM_ERR_NOT_CONVERGED;
+    else if (late) a.status[jj] = HELM_ERR_TIMEOUT;
+    else {
+      const double2 rho_new = make_double2(tot[0], tot[1]);
+      const double2 beta = cmul(cdiv(rho_new, a.rho[jj]), cdiv(a.alpha[jj], om));
+      if (!cfinite(rho_new) || !cfinite(beta)) { a.status[jj] = HELM_ERR_NONFINITE; a.iters[jj] += 1; }
+      else if (czero(rho_new)) { a.status[jj] = HELM_ERR_BREAKDOWN; a.iters[jj] += 1; }
+      else { a.rho[jj] = rho_new; a.beta[jj] = beta; }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) sweep_refresh_groups(a);
+}
+
+// tail: true residual per frequency, ||b - A_j x|| / ||b||
+__global__ void __launch_bounds__(256) k_sw_tail(SweepArgs a) {
+  extern __shared__ double sh[];
+  const int64_t gw = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int g = static_cast<int>(gw % a.G);
+  // every frequency is measured: mark them all active for the product
+  double part[1] = {0.0};
+  const int lane = threadIdx.x & 31;
+  const int j = g * 32 + lane;
+  const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+  const double wj = a.w[j], w2 = wj * wj;
+  for (int64_t u = gw; u < static_cast<int64_t>(a.A.n) * a.G; u += nwarps) {
+    const int32_t i = static_cast<int32_t>(u / a.G);
+    const int64_t k0 = __ldg(a.A.rowptr + i), k1 = __ldg(a.A.rowptr + i + 1);
+    double2 acc = make_double2(0.0, 0.0);
+    for (int64_t k = k0; k < k1; ++k) {
+      const int32_t c = __ldg(a.A.colind + k);
+      const double2 av = make_double2(fma(-w2, __ldg(a.A.M + k), __ldg(a.A.K + k)), wj * __ldg(a.A.B + k));
+      acc = cfma(av, a.x[static_cast<size_t>(c) * a.Fp + j], acc);
+    }
+    if (j < a.F)
+      part[0] = cabs2_acc(csub(a.b[a.b_ld ? static_cast<size_t>(i) * a.b_ld + j : static_cast<size_t>(i)], acc),
+                          part[0]);
+  }
+  double tot[1];
+  if (!sweep_grid_sum<1>(a, part, sh, a.tickets + TK_TAIL, tot)) return;
+  for (int jj = threadIdx.x; jj < a.F; jj += blockDim.x)
+    a.relres_true[jj] = a.bnorm[jj] > 0.0 ? sqrt(tot[0]) / a.bnorm[jj] : 0.0;
+}
+
+// X_user[i * ldx + j] <-> x[i * Fp + j]
+__global__ void k_sw_copy(int32_t n, int32_t F, int32_t Fp, const double2* __restrict__ src, int32_t lds,
+                          double2* __restrict__ dst, int32_t ldd) {
+  const int64_t total = static_cast<int64_t>(n) * F;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = q / F, j = q % F;
+    dst[i * ldd + j] = src[i * lds + j];
+  }
+  (void)Fp;
+}
+
+__global__ void k_sw_bzero(int32_t n, const int32_t* __restrict__ rowptr, const double* __restrict__ B,
+                           uint8_t* __restrict__ flags) {
+  const int32_t nblk = (n + 31) / 32;
+  for (int32_t blk = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); blk < nblk;
+       blk += gridDim.x * (blockDim.x / 32)) {
+    const int32_t r0 = blk * 32, r1 = min(r0 + 32, n);
+    bool zero = true;
+    for (int64_t k = rowptr[r0] + (threadIdx.x & 31); k < rowptr[r1]; k += 32)
+      if (B[k] != 0.0) zero = false;
+    zero = __all_sync(0xffffffffu, zero);
+    if ((threadIdx.x & 31) == 0) flags[blk] = zero ? 1 : 0;
+  }
+}
+
+// SpMV-only kernel for the tile-shape autotuner (x = y = internal buffers).
+__global__ void __launch_bounds__(512) k_sw_spmv_probe(SweepArgs a) {
+  auto body = [&](int32_t i, int j, double2 ax) { a.v[static_cast<size_t>(i) * a.Fp + j] = ax; };
+  sweep_spmv(a, a.p, body);
+}
+
+}  // namespace
+
+}  // namespace helm
+
+using namespace helm;
+
+struct helm_sweep_s {
+  int device = 0;
+  int num_sms = 1;
+  int32_t n = 0;
+  int64_t nnz = 0;
+  const int32_t* rowptr = nullptr;
+  const int32_t* colind = nullptr;
+  const double* K = nullptr;
+  const double* M = nullptr;
+  const double* B = nullptr;
+  uint8_t* bzero_blk = nullptr;
+  int32_t Fcap = 0;  // padded frequency capacity of the buffers
+  double2* vec = nullptr;         // 7 vectors [n][Fcap]
+  double2* scal = nullptr;        // 4 [Fcap]
+  double* dscal = nullptr;        // 3 [Fcap] + w [Fcap]
+  int32_t* iscal = nullptr;       // 3 [Fcap] + groups [Fcap / 32]
+  SolverState* state = nullptr;
+  double* partials = nullptr;
+  size_t partials_cap = 0;
+  unsigned int* tickets = nullptr;
+  int warps_per_block = 8;        // autotuned
+  bool tuned = false;
+  std::mutex mu;
+  struct G {
+    int32_t F = -1, b_ld = -1;
+    const void* b = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+  } graph;
+};
+
+namespace {
+
+helm_status sweep_alloc(helm_sweep S, int32_t Fp, size_t blocks) {
+  if (S->Fcap < Fp) {
+    cudaFree(S->vec);
+    cudaFree(S->scal);
+    cudaFree(S->dscal);
+    cudaFree(S->iscal);
+    S->vec = nullptr;
+    S->scal = nullptr;
+    S->dscal = nullptr;
+    S->iscal = nullptr;
+    S->Fcap = 0;
+    const size_t nf = static_cast<size_t>(std::max<int32_t>(S->n, 1)) * Fp;
+    HELM_CUDA_TRY(cudaMalloc(&S->vec, 7 * nf * sizeof(double2)));
+    HELM_CUDA_TRY(cudaMalloc(&S->scal, 4 * static_cast<size_t>(Fp) * sizeof(double2)));
+    HELM_CUDA_TRY(cudaMalloc(&S->dscal, 4 * static_cast<size_t>(Fp) * sizeof(double)));
+    HELM_CUDA_TRY(cudaMalloc(&S->iscal, (3 * static_cast<size_t>(Fp) + Fp / 32) * sizeof(int32_t)));
+    S->Fcap = Fp;
+    if (S->graph.exec) {
+      cudaGraphExecDestroy(S->graph.exec);
+      cudaGraphDestroy(S->graph.graph);
+      S->graph = helm_sweep_s::G();
+    }
+  }
+  const size_t need = blocks * static_cast<size_t>(Fp) * 4;
+  if (S->partials_cap < need) {
+    cudaFree(S->partials);
+    S->partials = nullptr;
+    HELM_CUDA_TRY(cudaMalloc(&S->partials, need * sizeof(double)));
+    S->partials_cap = need;
+  }
+  return HELM_OK;
+}
+
+SweepArgs make_args(helm_sweep S, int32_t F, int32_t Fp, const double2* b, int32_t b_ld) {
+  SweepArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.A = SweepDev{S->n, S->nnz, S->rowptr, S->colind, S->K, S->M, S->B, S->bzero_blk};
+  a.F = F;
+  a.Fp = Fp;
+  a.G = Fp / 32;
+  a.w = S->dscal + 3 * static_cast<size_t>(S->Fcap);
+  a.b = b;
+  a.b_ld = b_ld;
+  const size_t nf = static_cast<size_t>(std::max<int32_t>(S->n, 1)) * Fp;
+  double2* V = S->vec;
+  a.x = V;
+  a.r = V + nf;
+  a.rh = V + 2 * nf;
+  a.p = V + 3 * nf;
+  a.v = V + 4 * nf;
+  a.s = V + 5 * nf;
+  a.t = V + 6 * nf;
+  a.rho = S->scal;
+  a.alpha = S->scal + Fp;
+  a.omg = S->scal + 2 * Fp;
+  a.beta = S->scal + 3 * Fp;
+  a.bnorm = S->dscal;
+  a.relres = S->dscal + Fp;
+  a.relres_true = S->dscal + 2 * Fp;
+  a.status = S->iscal;
+  a.iters = S->iscal + Fp;
+  a.phase = S->iscal + 2 * Fp;
+  a.gactive = S->iscal + 3 * Fp;
+  a.st = S->state;
+  a.partials = S->partials;
+  a.tickets = S->tickets;
+  a.dev_err = S->tickets + TK_COUNT;
+  return a;
+}
+
+struct SweepShape {
+  int threads, grid;
+  size_t smem;  // per-frequency reduction scratch
+};
+
+SweepShape sweep_shape(helm_sweep S, int G) {
+  SweepShape sh;
+  sh.threads = 32 * S->warps_per_block;
+  // each warp keeps one group: the number of warps must be a multiple of G
+  const int warps_per_block = S->warps_per_block;
+  int64_t blocks = static_cast<int64_t>(S->num_sms) * (2048 / sh.threads);
+  int64_t units = static_cast<int64_t>(S->n) * G;
+  int64_t want = (units + warps_per_block - 1) / warps_per_block;
+  if (want < blocks) blocks = want < 1 ? 1 : want;
+  // warps in the grid = blocks * warps_per_block: make it a multiple of G
+  while ((blocks * warps_per_block) % G != 0) ++blocks;
+  sh.grid = static_cast<int>(blocks);
+  sh.smem = static_cast<size_t>(warps_per_block) * 32 * 4 * sizeof(double);
+  return sh;
+}
+
+void enqueue_sweep_body(const SweepArgs& a, const SweepShape& sh, cudaStream_t s) {
+  k_sw_p<<<sh.grid, sh.threads, 0, s>>>(a);
+  k_sw_v<<<sh.grid, sh.threads, sh.smem, s>>>(a);
+  k_sw_s<<<sh.grid, sh.threads, sh.smem, s>>>(a);
+  k_sw_t<<<sh.grid, sh.threads, sh.smem, s>>>(a);
+  k_sw_xr<<<sh.grid, sh.threads, sh.smem, s>>>(a);
+}
+
+helm_status build_sweep_graph(const SweepArgs& base, const SweepShape& sh, cudaGraph_t* gout, cudaGraphExec_t* eout) {
+  cudaStream_t cs = nullptr;
+  HELM_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  helm_status result = HELM_ERR_CUDA;
+  do {
+    if (cudaGraphCreate(&graph, 0) != cudaSuccess) break;
+    cudaGraphConditionalHandle cond;
+    if (cudaGraphConditionalHandleCreate(&cond, graph, 1u, cudaGraphCondAssignDefault) != cudaSuccess) break;
+    SweepArgs a = base;
+    a.cond = cond;
+    a.has_cond = 1;
+    if (cudaStreamBeginCaptureToGraph(cs, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      break;
+    k_sw_init<<<sh.grid, sh.threads, sh.smem, cs>>>(a);
+    cudaStreamCaptureStatus cst;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &deps, nullptr, &ndeps);
+    cudaGraphNode_t init_node = (e == cudaSuccess && ndeps == 1) ? deps[0] : nullptr;
+    cudaGraph_t tmp = nullptr;
+    if (cudaStreamEndCapture(cs, &tmp) != cudaSuccess || e != cudaSuccess || !init_node) break;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    if (cudaGraphAddNode(&wnode, graph, &init_node, nullptr, 1, &cp) != cudaSuccess) break;
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      break;
+    enqueue_sweep_body(a, sh, cs);
+    if (cudaStreamEndCapture(cs, &tmp) != cudaSuccess) break;
+    if (cudaStreamBeginCaptureToGraph(cs, graph, &wnode, nullptr, 1, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      break;
+    k_sw_tail<<<sh.grid, sh.threads, sh.smem, cs>>>(a);
+    if (cudaStreamEndCapture(cs, &tmp) != cudaSuccess) break;
+    if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) break;
+    result = HELM_OK;
+  } while (false);
+  cudaStreamDestroy(cs);
+  if (result != HELM_OK) {
+    (void)cudaGetLastError();
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    return result;
+  }
+  *gout = graph;
+  *eout = exec;
+  return HELM_OK;
+}
+
+// Time the batched SpMV with 4, 8 and 16 warps per block; keep the fastest.
+helm_status autotune(helm_sweep S, int32_t F, int32_t Fp, cudaStream_t s) {
+  const int candidates[3] = {4, 8, 16};  // 128..512 threads: at least kMaxF
+  float best = 1e30f;
+  int best_w = 8;
+  cudaEvent_t e0, e1;
+  HELM_CUDA_TRY(cudaEventCreate(&e0));
+  HELM_CUDA_TRY(cudaEventCreate(&e1));
+  helm_status result = HELM_OK;
+  for (int c : candidates) {
+    S->warps_per_block = c;
+    const SweepShape sh = sweep_shape(S, Fp / 32);
+    result = sweep_alloc(S, Fp, sh.grid);
+    if (result != HELM_OK) break;
+    SweepArgs a = make_args(S, F, Fp, nullptr, 0);
+    // every group active, every frequency running, p = 0 (timing only)
+    k_sw_configure<<<1, 256, 0, s>>>(a, 0.0, 1, 0, 0.0);
+    cudaMemsetAsync(a.p, 0, static_cast<size_t>(S->n) * Fp * sizeof(double2), s);
+    k_sw_spmv_probe<<<sh.grid, sh.threads, 0, s>>>(a);
+    cudaEventRecord(e0, s);
+    for (int rep = 0; rep < 3; ++rep) k_sw_spmv_probe<<<sh.grid, sh.threads, 0, s>>>(a);
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      result = HELM_ERR_CUDA;
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      best_w = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  (void)cudaGetLastError();
+  S->warps_per_block = best_w;
+  S->tuned = true;
+  return result;
+}
+
+}  // namespace
+
+extern "C" {
+
+helm_status helm_sweep_create(helm_sweep* out, int32_t n, int64_t nnz, const int32_t* d_rowptr,
+                              const int32_t* d_colind, const double* d_K, const double* d_M, const double* d_B,
+                              helm_stream_t stream) {
+  if (!out) return HELM_ERR_INVALID;
+  *out = nullptr;
+  if (n < 0 || nnz < 0 || nnz >= (int64_t(1) << 31) || !d_rowptr) return HELM_ERR_INVALID;
+  if (nnz > 0 && (!d_colind || !d_K || !d_M || !d_B)) return HELM_ERR_INVALID;
+  helm_sweep S = new (std::nothrow) helm_sweep_s();
+  if (!S) return HELM_ERR_NOMEM;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  auto fail = [&](helm_status st) {
+    helm_sweep_destroy(S);
+    return st;
+  };
+  if (cudaGetDevice(&S->device) != cudaSuccess) return fail(HELM_ERR_CUDA);
+  S->num_sms = sm_count();
+  S->n = n;
+  S->nnz = nnz;
+  S->rowptr = d_rowptr;
+  S->colind = d_colind;
+  S->K = d_K;
+  S->M = d_M;
+  S->B = d_B;
+  if (cudaMalloc(&S->state, sizeof(SolverState)) != cudaSuccess) return fail(HELM_ERR_NOMEM);
+  if (cudaMalloc(&S->tickets, (TK_COUNT + 2) * sizeof(unsigned int)) != cudaSuccess) return fail(HELM_ERR_NOMEM);
+  if (cudaMemsetAsync(S->tickets, 0, (TK_COUNT + 2) * sizeof(unsigned int), s) != cudaSuccess) return fail(HELM_ERR_CUDA);
+  if (n > 0) {
+    if (cudaMalloc(&S->bzero_blk, (n + 31) / 32) != cudaSuccess) return fail(HELM_ERR_NOMEM);
+    k_sw_bzero<<<vec_grid_for(n / 32 + 1), 256, 0, s>>>(n, d_rowptr, d_B, S->bzero_blk);
+    if (cudaGetLastError() != cudaSuccess) return fail(HELM_ERR_CUDA);
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess) return fail(HELM_ERR_CUDA);
+  *out = S;
+  return HELM_OK;
+}
+
+helm_status helm_sweep_destroy(helm_sweep S) {
+  if (!S) return HELM_OK;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(S->device);
+  cudaDeviceSynchronize();
+  if (S->graph.exec) cudaGraphExecDestroy(S->graph.exec);
+  if (S->graph.graph) cudaGraphDestroy(S->graph.graph);
+  cudaFree(S->bzero_blk);
+  cudaFree(S->vec);
+  cudaFree(S->scal);
+  cudaFree(S->dscal);
+  cudaFree(S->iscal);
+  cudaFree(S->state);
+  cudaFree(S->partials);
+  cudaFree(S->tickets);
+  (void)cudaGetLastError();
+  if (prev >= 0) cudaSetDevice(prev);
+  delete S;
+  return HELM_OK;
+}
+
+helm_status helm_sweep_solve(helm_sweep S, int32_t nfreq, const double* h_omega, const void* d_b, int32_t b_ld,
+                             void* d_X, int32_t ldx, const helm_opts* o, helm_info* h_infos, helm_stream_t stream) {
+  helm_opts opts;
+  if (o) opts = *o;
+  else helm_opts_default(&opts);
+  if (!S || nfreq < 1 || nfreq > kMaxF || !h_omega || (b_ld != 0 && b_ld < nfreq) || ldx < nfreq) return HELM_ERR_INVALID;
+  if (S->n > 0 && (!d_b || !d_X)) return HELM_ERR_INVALID;
+  if (!aligned(d_b, 16) || !aligned(d_X, 16) || !(opts.tol >= 0.0) || opts.maxit < 0) return HELM_ERR_INVALID;
+  if (opts.precision != HELM_PREC_FP64 || opts.method != HELM_BICGSTAB) return HELM_ERR_INVALID;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> lk(S->mu);
+  const int32_t Fp = (nfreq + 31) / 32 * 32;
+  if (!S->tuned) {
+    helm_status st = autotune(S, nfreq, Fp, s);
+    if (st != HELM_OK) return st;
+  }
+  const SweepShape sh = sweep_shape(S, Fp / 32);
+  helm_status st = sweep_alloc(S, Fp, sh.grid);
+  if (st != HELM_OK) return st;
+  // the user's b with its stride becomes an internal [n][Fp] copy only when
+  // its stride differs from Fp; a shared b is read in place
+  const double2* bsrc = static_cast<const double2*>(d_b);
+  int32_t bld = b_ld;
+  double2* bcopy = nullptr;
+  if (b_ld != 0 && b_ld != Fp) {
+    HELM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&bcopy), static_cast<size_t>(S->n) * Fp * sizeof(double2), s));
+    HELM_CUDA_TRY(cudaMemsetAsync(bcopy, 0, static_cast<size_t>(S->n) * Fp * sizeof(double2), s));
+    k_sw_copy<<<vec_grid_for(static_cast<int64_t>(S->n) * nfreq), 256, 0, s>>>(S->n, nfreq, Fp, bsrc, b_ld, bcopy, Fp);
+    bsrc = bcopy;
+    bld = Fp;
+  }
+  // angular frequencies, padded with zeros
+  std::vector<double> w(Fp, 0.0);
+  for (int j = 0; j < nfreq; ++j) w[j] = h_omega[j];
+  SweepArgs a = make_args(S, nfreq, Fp, bsrc, bld);
+  HELM_CUDA_TRY(cudaMemcpyAsync(const_cast<double*>(a.w), w.data(), Fp * sizeof(double), cudaMemcpyHostToDevice, s));
+  if (opts.use_x0) {
+    HELM_CUDA_TRY(cudaMemsetAsync(a.x, 0, static_cast<size_t>(S->n) * Fp * sizeof(double2), s));
+    k_sw_copy<<<vec_grid_for(static_cast<int64_t>(S->n) * nfreq), 256, 0, s>>>(
+        S->n, nfreq, Fp, static_cast<const double2*>(d_X), ldx, a.x, Fp);
+  }
+  // graph for (F, b, stride)
+  if (!(S->graph.exec && S->graph.F == nfreq && S->graph.b == bsrc && S->graph.b_ld == bld)) {
+    if (S->graph.exec) {
+      cudaGraphExecDestroy(S->graph.exec);
+      cudaGraphDestroy(S->graph.graph);
+    }
+    S->graph = helm_sweep_s::G();
+    if (!bcopy) {
+      if (build_sweep_graph(a, sh, &S->graph.graph, &S->graph.exec) == HELM_OK) {
+        S->graph.F = nfreq;
+        S->graph.b = bsrc;
+        S->graph.b_ld = bld;
+      }
+    }
+  }
+  k_sw_configure<<<1, 256, 0, s>>>(a, opts.tol, opts.maxit, opts.use_x0, opts.deadline_s);
+  HELM_CUDA_TRY(cudaGetLastError());
+  if (S->graph.exec && !bcopy) {
+    HELM_CUDA_TRY(cudaGraphLaunch(S->graph.exec, s));
+  } else {
+    SolverState hs;
+    k_sw_init<<<sh.grid, sh.threads, sh.smem, s>>>(a);
+    for (;;) {
+      for (int k = 0; k < 8; ++k) enqueue_sweep_body(a, sh, s);
+      HELM_CUDA_TRY(cudaGetLastError());
+      HELM_CUDA_TRY(cudaMemcpyAsync(&hs, a.st, sizeof(hs), cudaMemcpyDeviceToHost, s));
+      HELM_CUDA_TRY(cudaStreamSynchronize(s));
+      if (hs.status != ST_RUNNING) break;
+    }
+    k_sw_tail<<<sh.grid, sh.threads, sh.smem, s>>>(a);
+  }
+  k_sw_copy<<<vec_grid_for(static_cast<int64_t>(S->n) * nfreq), 256, 0, s>>>(S->n, nfreq, Fp, a.x, Fp,
+                                                                           static_cast<double2*>(d_X), ldx);
+  std::vector<int32_t> status(Fp), iters(Fp);
+  std::vector<double> relres(Fp), relres_true(Fp);
+  HELM_CUDA_TRY(cudaMemcpyAsync(status.data(), a.status, Fp * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  HELM_CUDA_TRY(cudaMemcpyAsync(iters.data(), a.iters, Fp * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  HELM_CUDA_TRY(cudaMemcpyAsync(relres.data(), a.relres, Fp * sizeof(double), cudaMemcpyDeviceToHost, s));
+  HELM_CUDA_TRY(cudaMemcpyAsync(relres_true.data(), a.relres_true, Fp * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (bcopy) cudaFreeAsync(bcopy, s);
+  HELM_CUDA_TRY(cudaStreamSynchronize(s));
+  helm_status worst = HELM_OK;
+  for (int j = 0; j < nfreq; ++j) {
+    helm_status sj = status[j] == ST_RUNNING ? HELM_ERR_CUDA : static_cast<helm_status>(status[j]);
+    if (sj == HELM_OK && !(relres_true[j] <= 1.5 * opts.tol)) sj = HELM_ERR_NOT_CONVERGED;
+    if (h_infos) {
+      h_infos[j].iters = iters[j];
+      h_infos[j].restarts = 0;
+      h_infos[j].relres_recur = relres[j];
+      h_infos[j].relres_true = relres_true[j];
+      h_infos[j].status = sj;
+      h_infos[j].spmv_count = 2 * iters[j];
+    }
+    if (sj != HELM_OK && worst == HELM_OK) worst = sj;
+  }
+  return worst;
+}
+
+}  // extern "C"

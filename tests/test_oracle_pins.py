@@ -370,3 +370,61 @@ def test_helmholtz_values_frequency_form():
         b = g.helmholtz_values(p, F)
         assert np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-300)) <= 1e-15
     assert np.array_equal(oracle.helmholtz_values(p.K, p.Mc, p.Bc, 0.0).real, p.K)
+
+
+# ---------------------------------------------------------------- TFQMR
+
+def test_tfqmr_scaled_identity_one_iteration():
+    rp, ci, v = _csr_diag(np.full(12, 3.0 - 1.0j))
+    b = g.complex_vector(12, 5)
+    x, info = oracle.tfqmr(rp, ci, v, b, tol=1e-12)
+    assert info["status"] == "ok" and info["iters"] == 1
+    assert np.allclose(x, b / (3.0 - 1.0j), rtol=1e-14, atol=0)
+
+
+def test_tfqmr_matches_dense_lu_and_degenerate_cases():
+    for p, vals in _tiny_problems():
+        b = g.complex_vector(p.n, 22) * (~p.dirichlet)
+        xs = oracle.dense_solve(p.rowptr, p.colind, vals, b)
+        x, info = oracle.tfqmr(p.rowptr, p.colind, vals, b, tol=1e-12, maxit=10000)
+        assert info["status"] == "ok" and info["relres_true"] <= 1e-12
+        cond = np.linalg.cond(oracle.densify(p.rowptr, p.colind, vals))
+        assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= 10 * cond * 1e-12
+    p, vals = _tiny_problems()[1]
+    x, info = oracle.tfqmr(p.rowptr, p.colind, vals, np.zeros(p.n, np.complex128))
+    assert info["status"] == "ok" and info["iters"] == 0 and np.all(x == 0)
+    b = g.complex_vector(p.n, 23) * (~p.dirichlet)
+    x, info = oracle.tfqmr(p.rowptr, p.colind, vals, b, tol=1e-30, maxit=1)
+    assert info["status"] == "not_converged" and info["iters"] == 1
+    bad = b.copy()
+    bad[2] = np.nan
+    assert oracle.tfqmr(p.rowptr, p.colind, vals, bad)[1]["status"] == "nonfinite"
+
+
+# ---------------------------------------------------------------- BiCGStab(l)
+
+@pytest.mark.parametrize("ell", [1, 2, 4, 8])
+def test_bicgstabl_matches_dense_lu(ell):
+    for p, vals in _tiny_problems():
+        b = g.complex_vector(p.n, 24) * (~p.dirichlet)
+        xs = oracle.dense_solve(p.rowptr, p.colind, vals, b)
+        x, info = oracle.bicgstabl(p.rowptr, p.colind, vals, b, ell=ell, tol=1e-12, maxit=10000)
+        assert info["status"] == "ok" and info["relres_true"] <= 1.5e-12
+        cond = np.linalg.cond(oracle.densify(p.rowptr, p.colind, vals))
+        assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= 10 * cond * 1e-12
+
+
+def test_bicgstabl_one_is_bicgstab_and_special_cases():
+    # l = 1 is mathematically BiCGStab: same iteration count on small systems
+    for p, vals in _tiny_problems()[1:]:
+        b = g.complex_vector(p.n, 25) * (~p.dirichlet)
+        _, i1 = oracle.bicgstabl(p.rowptr, p.colind, vals, b, ell=1, tol=1e-12)
+        _, ib = oracle.bicgstab(p.rowptr, p.colind, vals, b, tol=1e-12)
+        assert abs(i1["iters"] - ib["iters"]) <= 1
+    rp, ci, v = _csr_diag(np.full(9, 1.5 + 0.5j))
+    b = g.complex_vector(9, 6)
+    x, info = oracle.bicgstabl(rp, ci, v, b, ell=4, tol=1e-12)
+    assert info["status"] == "ok" and info["iters"] == 1 and np.allclose(x, b / (1.5 + 0.5j), rtol=1e-13)
+    p, vals = _tiny_problems()[1]
+    x, info = oracle.bicgstabl(p.rowptr, p.colind, vals, np.zeros(p.n, np.complex128), ell=2)
+    assert info["status"] == "ok" and info["iters"] == 0 and np.all(x == 0)
