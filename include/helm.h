@@ -163,14 +163,20 @@ typedef enum { HELM_BICGSTAB = 0, HELM_TFQMR = 1, HELM_BICGSTABL = 2 } helm_meth
 /* Arithmetic of the solve. */
 typedef enum {
   HELM_PREC_FP64 = 0, /* complex128 throughout */
-  HELM_PREC_MIXED = 1 /* complex64 inner BiCGStab inside complex128 iterative
-                         refinement: residual, update and norms in FP64 */
+  HELM_PREC_MIXED = 1 /* complex64 BiCGStab (values converted once into a
+                         handle-owned copy) with reliable updates: the
+                         solution is accumulated and the residual b - A x
+                         recomputed in FP64 whenever the complex64 residual
+                         has dropped 10x, and convergence is decided on that
+                         FP64 residual */
 } helm_precision;
 /* How the iteration loop is driven on the device. */
 typedef enum {
-  HELM_LAUNCH_AUTO = 0,
-  HELM_LAUNCH_GRAPH = 1,      /* CUDA graph with a device-driven while node */
-  HELM_LAUNCH_PERSISTENT = 2, /* one cooperative kernel with grid barriers */
+  HELM_LAUNCH_AUTO = 0,       /* graph; the host-driven loop if the graph
+                                 cannot be built */
+  HELM_LAUNCH_GRAPH = 1,      /* CUDA graph with a device-driven while node;
+                                 HELM_ERR_CUDA if it cannot be built */
+  HELM_LAUNCH_PERSISTENT = 2, /* reserved: runs as HELM_LAUNCH_AUTO */
   HELM_LAUNCH_HOST = 3        /* host-driven loop of the same kernels, state
                                  polled every 16 iterations (profiling: tools
                                  that cannot see inside conditional graphs) */
@@ -183,8 +189,8 @@ typedef struct {
   int32_t use_x0;      /* 0: start from x = 0 (Section 4); 1: start from d_x */
   int32_t method;      /* helm_method */
   int32_t precision;   /* helm_precision */
-  double inner_tol;    /* HELM_PREC_MIXED: relative tolerance of each inner
-                          complex64 solve */
+  double inner_tol;    /* reserved (mixed precision updates on a fixed
+                          10x drop of the complex64 residual) */
   double deadline_s;   /* device wall-clock limit of one solve; <= 0: none */
   int32_t ell;         /* l of BiCGStab(l), 1..8 */
   int32_t launch;      /* helm_launch */
@@ -194,7 +200,7 @@ typedef struct {
   int32_t iters;        /* iterations performed (all restarts / refinement
                            steps included; for mixed precision, inner
                            iterations) */
-  int32_t restarts;     /* restarts (BiCGStab) or refinement steps (mixed) */
+  int32_t restarts;     /* restarts (BiCGStab) or FP64 reliable updates (mixed) */
   double relres_recur;  /* last recurrence residual / ||b|| */
   double relres_true;   /* ||b - A x|| / ||b|| recomputed in FP64 at the end */
   helm_status status;

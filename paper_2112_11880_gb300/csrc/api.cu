@@ -62,6 +62,13 @@ __global__ void k_real_blocks(int32_t n, const int32_t* __restrict__ rowptr, con
   }
 }
 
+// vals_re[k] = Re vals[k]
+__global__ void k_real_parts(int64_t nnz, const double2* __restrict__ vals, double* __restrict__ vals_re) {
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < nnz;
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    vals_re[k] = vals[k].x;
+}
+
 // Per-row statistics and (optionally) validation of the CSR pattern.
 __global__ void k_csr_check(int32_t n, int64_t nnz, const int32_t* __restrict__ rowptr,
                             const int32_t* __restrict__ colind, int validate, int* out /* [0]=max row, [1]=bad */) {
@@ -229,7 +236,7 @@ helm_status launch_spmv128(helm_csr A, const double2* x, double2* y, double2 alp
   const int mode = (alpha.x == 1.0 && alpha.y == 0.0 && beta.x == 0.0 && beta.y == 0.0) ? 0
                    : (beta.x == 0.0 && beta.y == 0.0)                                    ? 1
                                                                                          : 2;
-  CsrDev<double2> d{A->n, A->nnz, A->rowptr, A->colind, static_cast<const double2*>(A->vals), A->real_blk};
+  CsrDev<double2> d{A->n, A->nnz, A->rowptr, A->colind, static_cast<const double2*>(A->vals), A->real_blk, A->vals_re};
   k_spmv<double2><<<grid, Engine<double2>::kThreads, Engine<double2>::kSmem, s>>>(d, x, y, alpha, beta, mode, A->dev_err);
   HELM_CUDA_TRY(cudaGetLastError());
   return HELM_OK;
@@ -244,7 +251,7 @@ helm_status launch_spmv64(helm_csr A, const float2* vals, const float2* x, float
   const int mode = (alpha.x == 1.f && alpha.y == 0.f && beta.x == 0.f && beta.y == 0.f) ? 0
                    : (beta.x == 0.f && beta.y == 0.f)                                    ? 1
                                                                                          : 2;
-  CsrDev<float2> d{A->n, A->nnz, A->rowptr, A->colind, vals, nullptr};
+  CsrDev<float2> d{A->n, A->nnz, A->rowptr, A->colind, vals, nullptr, nullptr};
   k_spmv<float2><<<grid, Engine<float2>::kThreads, Engine<float2>::kSmem, s>>>(d, x, y, alpha, beta, mode, A->dev_err);
   HELM_CUDA_TRY(cudaGetLastError());
   return HELM_OK;
@@ -404,6 +411,13 @@ helm_status helm_csr_create(helm_csr* out, int32_t n, int64_t nnz, const int32_t
     if (cudaMalloc(&A->real_blk, (n + 31) / 32) != cudaSuccess) return fail(HELM_ERR_NOMEM);
     k_real_blocks<<<vec_grid_for(n / 32 + 1), 256, 0, s>>>(n, d_rowptr, static_cast<const double2*>(d_vals), A->real_blk);
     if (cudaGetLastError() != cudaSuccess) return fail(HELM_ERR_CUDA);
+    // the SpMV stages real blocks from their real parts (8 bytes per entry)
+    if (nnz > 0) {
+      if (cudaMalloc(&A->vals_re, static_cast<size_t>(nnz) * sizeof(double)) != cudaSuccess)
+        return fail(HELM_ERR_NOMEM);
+      k_real_parts<<<vec_grid_for(nnz), 256, 0, s>>>(nnz, static_cast<const double2*>(d_vals), A->vals_re);
+      if (cudaGetLastError() != cudaSuccess) return fail(HELM_ERR_CUDA);
+    }
   }
   *out = A;
   return HELM_OK;
@@ -426,6 +440,7 @@ helm_status helm_csr_destroy(helm_csr A) {
   cudaFree(A->vec);
   cudaFree(A->vals32);
   cudaFree(A->real_blk);
+  cudaFree(A->vals_re);
   cudaFree(A->vec32);
   (void)cudaGetLastError();
   if (prev >= 0) cudaSetDevice(prev);
@@ -538,6 +553,8 @@ helm_status helm_bicgstab_solve(helm_csr A, const void* d_b, void* d_x, const he
   if (opts.precision != HELM_PREC_FP64) return HELM_ERR_INVALID;
   if (opts.method == HELM_TFQMR)
     return tfqmr_fp64(A, static_cast<const double2*>(d_b), static_cast<double2*>(d_x), opts, info, s);
+  if (opts.method == HELM_BICGSTABL)
+    return bicgstabl_fp64(A, static_cast<const double2*>(d_b), static_cast<double2*>(d_x), opts, info, s);
   if (opts.method != HELM_BICGSTAB) return HELM_ERR_INVALID;
   return bicgstab_fp64(A, static_cast<const double2*>(d_b), static_cast<double2*>(d_x), opts, info, s);
 }

@@ -25,6 +25,7 @@ __global__ void k_configure(SolverState* st, double tol, int32_t maxit, int32_t 
   st->tol = tol;
   st->maxit = maxit;
   st->use_x0 = use_x0;
+  st->method = kModePlain;
   st->deadline_ns = deadline_s > 0.0 ? static_cast<unsigned long long>(deadline_s * 1e9) : 0ull;
   st->status = ST_RUNNING;
   st->phase = PH_RUN;
@@ -96,7 +97,7 @@ helm_status bicgstab_fp64(helm_csr A, const double2* b, double2* x, const helm_o
   double2* W = A->vec;
   KArgs<V> a;
   std::memset(&a, 0, sizeof(a));
-  a.A = CsrDev<V>{n, A->nnz, A->rowptr, A->colind, static_cast<const V*>(A->vals), A->real_blk};
+  a.A = CsrDev<V>{n, A->nnz, A->rowptr, A->colind, static_cast<const V*>(A->vals), A->real_blk, A->vals_re};
   a.b = b;
   a.x = x;
   a.r = W;
@@ -132,6 +133,8 @@ helm_status bicgstab_fp64(helm_csr A, const double2* b, double2* x, const helm_o
       g = &(A->graphs[key] = e);
     }
   }
+  // an explicit graph request does not fall back to the host-driven loop
+  if (!g && o.launch == HELM_LAUNCH_GRAPH) return HELM_ERR_CUDA;
 
   int32_t use_x0 = o.use_x0 ? 1 : 0;
   int32_t fresh = 1;

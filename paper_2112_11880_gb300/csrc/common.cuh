@@ -126,29 +126,72 @@ __device__ __forceinline__ double ld_cg(const double* p) { return __ldcg(p); }
 
 // ---------------------------------------------------------------- reductions
 
-// Sum K doubles over the block, fixed shuffle pattern then warps in order.
-// Result valid in thread 0.  `red` must hold 32*K doubles.  Ends with a
-// __syncthreads so `red` can be reused.
+// Warp sum of K doubles with a transposed butterfly: at the first exchange
+// (and for K > 2 the second) each lane keeps only half of the values it
+// carries, so a lane adds K/2 + K/4 + 3 values instead of 5 K -- every FP64
+// add is a full warp instruction on GB300 whatever the number of useful
+// lanes.  The sum of component k ends in lane lane_of<K>(k).  Fixed pattern:
+// bit-for-bit reproducible.
+template <int K>
+__device__ __forceinline__ int warp_sum_lane(int k) {
+  return K == 1 ? 0 : (K == 2 ? (k & 1) * 16 : ((k & 1) * 16 + ((k >> 1) & 1) * 8));
+}
+template <int K>
+__device__ __forceinline__ double warp_sum_t(const double (&v)[K]) {
+  const int lane = threadIdx.x & 31;
+  if (K == 1) {
+    double a = v[0];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
+    return a;
+  } else if (K == 2) {
+    const bool up = lane & 16;
+    double keep = up ? v[1] : v[0];
+    keep += __shfl_xor_sync(0xffffffffu, up ? v[0] : v[1], 16);
+#pragma unroll
+    for (int off = 8; off > 0; off >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, off);
+    return keep;  // lane 0: v[0], lane 16: v[1]
+  } else {
+    // K = 3 or 4 (v[3] = 0 for K = 3): keep components {0,2} / {1,3} across
+    // the 16-exchange, then {0}/{2} resp. {1}/{3} across the 8-exchange
+    const double w3 = K > 3 ? v[K > 3 ? 3 : 0] : 0.0;
+    const bool up16 = lane & 16, up8 = lane & 8;
+    double a = up16 ? v[1] : v[0];
+    double b = up16 ? w3 : v[2];
+    a += __shfl_xor_sync(0xffffffffu, up16 ? v[0] : v[1], 16);
+    b += __shfl_xor_sync(0xffffffffu, up16 ? v[2] : w3, 16);
+    double keep = up8 ? b : a;
+    keep += __shfl_xor_sync(0xffffffffu, up8 ? a : b, 8);
+#pragma unroll
+    for (int off = 4; off > 0; off >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, off);
+    return keep;  // lane 0: v[0], 16: v[1], 8: v[2], 24: v[3]
+  }
+}
+
+// Sum K doubles over the block: warp sums (transposed butterfly), then the
+// warp sums of each component added in warp order by one lane per component
+// (at most 32 warps).  Result valid in thread 0.  `red` holds 32*K doubles.
+// Ends with a __syncthreads so `red` can be reused.
 template <int K>
 __device__ __forceinline__ void block_sum(double (&v)[K], double* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarps = (blockDim.x + 31) >> 5;
+  const double ws = warp_sum_t<K>(v);
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
-  }
-  if (lane == 0) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) red[warp * K + k] = v[k];
-  }
+  for (int k = 0; k < K; ++k)
+    if (lane == warp_sum_lane<K>(k)) red[warp * K + k] = ws;
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (warp == 0) {
+    // lane k adds the K-th component over warps in order (one chain each)
+    double s = 0.0;
+    if (lane < K) {
+      for (int w = 0; w < nwarps; ++w) s += red[w * K + lane];
+    }
+    // gather to thread 0
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      double s = red[k];
-      for (int w = 1; w < nwarps; ++w) s += red[w * K + k];
-      v[k] = s;
+      const double sk = __shfl_sync(0xffffffffu, s, k);
+      if (lane == 0) v[k] = sk;
     }
   }
   __syncthreads();
@@ -204,6 +247,20 @@ __device__ __forceinline__ bool grid_sum_last(double (&v)[K], double* partials,
   for (int k = 0; k < K; ++k) tot[k] = acc[k];
   if (threadIdx.x == 0) *ticket = 0u;
   return true;
+}
+
+// ---------------------------------------------------------------- dependent launch
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may start while its predecessor finishes.  It may load data
+// that no kernel in flight writes before pdl_wait(); everything else (the
+// solver state, the predecessor's outputs, every store) comes after it.
+// pdl_wait() returns once the predecessor grid has completed and its memory
+// is visible (at once for a kernel launched the ordinary way).  A kernel lets
+// its own successor start only after its pdl_wait(), so that at a kernel's
+// start the kernel two launches back has completed.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 // ---------------------------------------------------------------- TMA bulk copy

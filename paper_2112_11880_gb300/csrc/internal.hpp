@@ -33,15 +33,16 @@ enum : int { TK_INIT = 0, TK_V, TK_S, TK_T, TK_XR, TK_TAIL, TK_AUX0, TK_AUX1, TK
 
 // SpMV engine shape (measured on GB300, 120x60x50 Q1 matrix): 32-row tiles
 // of up to 28 entries per row staged by TMA bulk copies into a single buffer
-// per block; each row split over 4 threads in 4 different warps (128-thread
-// blocks, 11 blocks per SM overlapping one another).
+// per block; each row split over 2 threads in 2 different warps (64-thread
+// blocks overlapping one another; 4 warps per row measured the same speed
+// for the plain SpMV and costs 4 more FP64 adds per row).
 constexpr int kRows128 = 32;
 constexpr int kCap128 = kRows128 * 28;
 constexpr int kRows64 = 32;
 constexpr int kCap64 = kRows64 * 28;
 constexpr int kStages = 1;
 #ifndef HELM_SPLIT
-#define HELM_SPLIT 4
+#define HELM_SPLIT 2
 #endif
 constexpr int kSplit = HELM_SPLIT;
 
@@ -80,6 +81,7 @@ struct helm_csr_s {
   int nvec = 0;
   float2* vals32 = nullptr;            // complex64 copy for mixed precision
   uint8_t* real_blk = nullptr;         // per 32-row block: all entries real
+  double* vals_re = nullptr;           // real parts of the complex128 values
   float2* vec32 = nullptr;             // complex64 Krylov vectors
   int nvec32 = 0;
 
@@ -121,6 +123,8 @@ helm_status bicgstab_fp64(helm_csr A, const double2* b, double2* x, const helm_o
                           cudaStream_t s);
 helm_status tfqmr_fp64(helm_csr A, const double2* b, double2* x, const helm_opts& o, helm_info* info,
                        cudaStream_t s);
+helm_status bicgstabl_fp64(helm_csr A, const double2* b, double2* x, const helm_opts& o, helm_info* info,
+                           cudaStream_t s);
 helm_status solve_mixed(helm_csr A, const double2* b, double2* x, const helm_opts& o, helm_info* info,
                         cudaStream_t s);
 

@@ -24,12 +24,22 @@
 #pragma once
 
 #include <cstring>
+#include <utility>
 
 #include "common.cuh"
 #include "internal.hpp"
 #include "spmv.cuh"
 
 namespace helm {
+
+// SolverState::method of the Krylov loop: plain, or the inner loop of the
+// mixed-precision solve with reliable updates (aux[0] = (max ||r|| since the
+// last update, iteration of the last update), aux[1].x = update due,
+// aux[2].x = scale of the inner residual).
+constexpr int32_t kModePlain = 0;
+constexpr int32_t kModeReliable = 1;
+constexpr double kRelDelta = 0.1;
+constexpr int kRelMaxGap = 2000;
 
 template <class V> struct Prec;
 template <> struct Prec<double2> {
@@ -168,6 +178,13 @@ __global__ void __launch_bounds__(Prec<V>::R) k_init(KArgs<V> a) {
 // arithmetic, so the 64-clock FP64 latency and the memory latency of one
 // element overlap the other's.
 constexpr int kVecThreads = 256;
+// Blocks per SM of the element-wise kernels (0: as many as fit).  Fewer
+// threads take more rows each, which spreads the per-thread share of the
+// block reductions (FP64 adds on the FP64 pipe) over more rows.
+#ifndef HELM_VEC_BPS
+#define HELM_VEC_BPS 0
+#endif
+constexpr int kVecBlocksPerSm = HELM_VEC_BPS;
 
 // K1: p = r + beta (p - omega v)
 template <class V>
@@ -177,18 +194,25 @@ __global__ void __launch_bounds__(kVecThreads) k_p(KArgs<V> a) {
   const V beta = Prec<V>::cvt(st->beta), omega = Prec<V>::cvt(st->omega);
   const int32_t n = a.A.n;
   const int32_t stride = gridDim.x * blockDim.x;
-  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += 2 * stride) {
+  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  V v0 = a.v[i], p0 = a.p[i], r0 = a.r[i];
+  for (;;) {
+    // the next row's loads are in flight while this row is computed
     const int32_t j = i + stride;
-    const bool two = j < n;
-    const V v0 = a.v[i], p0 = a.p[i], r0 = a.r[i];
-    V v1 = vzero<V>(), p1 = vzero<V>(), r1 = vzero<V>();
-    if (two) {
+    const bool more = j < n;
+    V v1 = v0, p1 = p0, r1 = r0;
+    if (more) {
       v1 = a.v[j];
       p1 = a.p[j];
       r1 = a.r[j];
     }
     a.p[i] = cfma(beta, cfms(omega, v0, p0), r0);
-    if (two) a.p[j] = cfma(beta, cfms(omega, v1, p1), r1);
+    if (!more) break;
+    v0 = v1;
+    p0 = p1;
+    r0 = r1;
+    i = j;
   }
 }
 
@@ -199,6 +223,8 @@ __global__ void __launch_bounds__(Prec<V>::R) k_v(KArgs<V> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[32 * 2];
   SolverState* st = a.st;
+  pdl_wait();  // p comes from the previous kernel
+  pdl_launch_dependents();
   if (st->status != ST_RUNNING) return;
   struct Epi {
     const KArgs<V>* a;
@@ -235,30 +261,35 @@ __global__ void __launch_bounds__(kVecThreads) k_s(KArgs<V> a) {
   using S = typename Prec<V>::S;
   __shared__ double red[32];
   SolverState* st = a.st;
-  if (st->status != ST_RUNNING) return;
-  const V alpha = Prec<V>::cvt(st->alpha);
-  S acc = S(0), acc1 = S(0);
   const int32_t n = a.A.n;
   const int32_t stride = gridDim.x * blockDim.x;
-  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += 2 * stride) {
+  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  // r was final before the previous kernel started; v and alpha are its output
+  V r0 = vzero<V>();
+  if (i < n) r0 = a.r[i];
+  pdl_wait();
+  pdl_launch_dependents();
+  if (st->status != ST_RUNNING) return;
+  const V alpha = Prec<V>::cvt(st->alpha);
+  S acc = S(0);
+  V v0 = vzero<V>();
+  if (i < n) v0 = a.v[i];
+  while (i < n) {
     const int32_t j = i + stride;
-    const bool two = j < n;
-    const V v0 = a.v[i], r0 = a.r[i];
-    V v1 = vzero<V>(), r1 = vzero<V>();
-    if (two) {
+    const bool more = j < n;
+    V v1 = v0, r1 = r0;
+    if (more) {
       v1 = a.v[j];
       r1 = a.r[j];
     }
     const V s0 = cfms(alpha, v0, r0);
     a.s[i] = s0;
     acc = cabs2_acc(s0, acc);
-    if (two) {
-      const V s1 = cfms(alpha, v1, r1);
-      a.s[j] = s1;
-      acc1 = cabs2_acc(s1, acc1);
-    }
+    v0 = v1;
+    r0 = r1;
+    i = j;
   }
-  double part[1] = {double(acc) + double(acc1)};
+  double part[1] = {double(acc)};
   double tot[1];
   if (!grid_sum_last<1>(part, a.partials, a.tickets + TK_S, red, tot)) return;
   if (threadIdx.x != 0) return;
@@ -267,7 +298,7 @@ __global__ void __launch_bounds__(kVecThreads) k_s(KArgs<V> a) {
   const double bt = st->bnorm * st->tol;
   if (!isfinite(s2)) {
     st->status = HELM_ERR_NONFINITE;
-  } else if (s2 <= bt * bt) {
+  } else if (st->method != kModeReliable && s2 <= bt * bt) {
     st->phase = PH_SCONV;
     st->relres = sqrt(s2) / st->bnorm;
   }
@@ -280,6 +311,8 @@ __global__ void __launch_bounds__(Prec<V>::R) k_t(KArgs<V> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[32 * 3];
   SolverState* st = a.st;
+  pdl_wait();  // s and the phase come from the previous kernel
+  pdl_launch_dependents();
   if (st->status != ST_RUNNING || st->phase != PH_RUN) return;
   struct Epi {
     const KArgs<V>* a;
@@ -319,6 +352,20 @@ __global__ void __launch_bounds__(kVecThreads) k_xr(KArgs<V> a) {
   using S = typename Prec<V>::S;
   __shared__ double red[32 * 3];
   SolverState* st = a.st;
+  const int32_t n = a.A.n;
+  const int32_t stride = gridDim.x * blockDim.x;
+  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  // x, p, s and r^ were final before the previous kernel started; t, omega
+  // and the status are its output
+  V s0 = vzero<V>(), x0 = vzero<V>(), p0 = vzero<V>(), h0 = vzero<V>();
+  if (i < n) {
+    s0 = a.s[i];
+    x0 = a.x[i];
+    p0 = a.p[i];
+    h0 = a.rh[i];
+  }
+  pdl_wait();
+  pdl_launch_dependents();
   const int status0 = st->status;
   if (status0 != ST_RUNNING) {
     if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(a, false);
@@ -327,19 +374,18 @@ __global__ void __launch_bounds__(kVecThreads) k_xr(KArgs<V> a) {
   const double2 alpha64 = st->alpha, omega64 = st->omega;
   const V alpha = Prec<V>::cvt(alpha64), omega = Prec<V>::cvt(omega64);
   const int phase = st->phase;
-  V rr = vzero<V>(), rr1 = vzero<V>();
-  S r2 = S(0), r21 = S(0);
-  const int32_t n = a.A.n;
-  const int32_t stride = gridDim.x * blockDim.x;
+  V rr = vzero<V>();
+  S r2 = S(0);
   if (phase == PH_SCONV) {
-    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) a.x[i] = cfma(alpha, a.p[i], a.x[i]);
+    for (; i < n; i += stride) a.x[i] = cfma(alpha, a.p[i], a.x[i]);
   } else {
-    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += 2 * stride) {
+    V t0 = vzero<V>();
+    if (i < n) t0 = a.t[i];
+    while (i < n) {
       const int32_t j = i + stride;
-      const bool two = j < n;
-      const V s0 = a.s[i], x0 = a.x[i], p0 = a.p[i], t0 = a.t[i], h0 = a.rh[i];
-      V s1 = vzero<V>(), x1 = vzero<V>(), p1 = vzero<V>(), t1 = vzero<V>(), h1 = vzero<V>();
-      if (two) {
+      const bool more = j < n;
+      V s1 = s0, x1 = x0, p1 = p0, t1 = t0, h1 = h0;
+      if (more) {
         s1 = a.s[j];
         x1 = a.x[j];
         p1 = a.p[j];
@@ -351,19 +397,20 @@ __global__ void __launch_bounds__(kVecThreads) k_xr(KArgs<V> a) {
       a.r[i] = r0;
       rr = cfma_conj(h0, r0, rr);
       r2 = cabs2_acc(r0, r2);
-      if (two) {
-        a.x[j] = cfma(omega, s1, cfma(alpha, p1, x1));
-        const V r1 = cfms(omega, t1, s1);
-        a.r[j] = r1;
-        rr1 = cfma_conj(h1, r1, rr1);
-        r21 = cabs2_acc(r1, r21);
-      }
+      s0 = s1;
+      x0 = x1;
+      p0 = p1;
+      t0 = t1;
+      h0 = h1;
+      i = j;
     }
   }
-  double part[3] = {double(rr.x) + double(rr1.x), double(rr.y) + double(rr1.y), double(r2) + double(r21)};
+  double part[3] = {double(rr.x), double(rr.y), double(r2)};
   double tot[3];
   if (!grid_sum_last<3>(part, a.partials, a.tickets + TK_XR, red, tot)) return;
   if (threadIdx.x != 0) return;
+  // reliable mode runs on a scaled residual: b - A x ~ aux[2].x * r
+  const double sc = st->method == kModeReliable ? st->aux[2].x : 1.0;
   int status = ST_RUNNING;
   if (phase == PH_SCONV) {
     status = HELM_OK;
@@ -373,9 +420,22 @@ __global__ void __launch_bounds__(kVecThreads) k_xr(KArgs<V> a) {
     // report only when the loop stops
     const double r2 = tot[2];
     const double bt = st->bnorm * st->tol;
+    bool stop_ok = r2 * (sc * sc) <= bt * bt;
+    if (st->method == kModeReliable && isfinite(r2)) {
+      // mixed precision: the recurrence never declares convergence; it asks
+      // for a reliable update (FP64 residual) when it has dropped by
+      // kRelDelta since the last one, looks converged, or every
+      // kRelMaxGap iterations
+      const double rn = sqrt(r2);
+      const double rmax = fmax(st->aux[0].x, rn);
+      st->aux[0].x = rmax;
+      if (stop_ok || rn < kRelDelta * rmax || st->iter - static_cast<int>(st->aux[0].y) >= kRelMaxGap)
+        st->aux[1].x = 1.0;
+      stop_ok = false;
+    }
     if (!isfinite(r2)) {
       status = HELM_ERR_NONFINITE;
-    } else if (r2 <= bt * bt) {
+    } else if (stop_ok) {
       status = HELM_OK;
     } else if (czero(omega64)) {
       status = HELM_ERR_BREAKDOWN;
@@ -399,7 +459,7 @@ __global__ void __launch_bounds__(kVecThreads) k_xr(KArgs<V> a) {
       }
     }
   }
-  if (phase != PH_SCONV && status != ST_RUNNING) st->relres = sqrt(tot[2]) / st->bnorm;
+  if (phase != PH_SCONV && status != ST_RUNNING) st->relres = sqrt(tot[2]) * sc / st->bnorm;
   st->status = status;
   set_cond(a, status == ST_RUNNING);
 }
@@ -414,14 +474,36 @@ template <class V>
 inline void enqueue_init(const KArgs<V>& a, const KShapes<V>& sh, cudaStream_t s) {
   k_init<V><<<sh.spmv_grid, Prec<V>::R, Engine<V>::kSmem, s>>>(a);
 }
+// Launch with programmatic stream serialization: the kernel may start while
+// its predecessor finishes (it calls pdl_wait() before it reads that
+// kernel's output).  Launch errors surface through cudaGetLastError().
+#ifndef HELM_PDL
+#define HELM_PDL 1
+#endif
+template <class... P, class... Args>
+inline void launch_dependent(void (*kern)(P...), int grid, int block, size_t smem, cudaStream_t s,
+                             Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(grid));
+  cfg.blockDim = dim3(static_cast<unsigned>(block));
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = HELM_PDL ? 1 : 0;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  (void)cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
 template <class V>
 inline void enqueue_body(const KArgs<V>& a, const KShapes<V>& sh, cudaStream_t s) {
   constexpr size_t smem = Engine<V>::kSmem;
   k_p<V><<<sh.grid_p, kVecThreads, 0, s>>>(a);
-  k_v<V><<<sh.spmv_grid, Prec<V>::R, smem, s>>>(a);
-  k_s<V><<<sh.grid_s, kVecThreads, 0, s>>>(a);
-  k_t<V><<<sh.spmv_grid, Prec<V>::R, smem, s>>>(a);
-  k_xr<V><<<sh.grid_xr, kVecThreads, 0, s>>>(a);
+  launch_dependent(k_v<V>, sh.spmv_grid, Prec<V>::R, smem, s, a);
+  launch_dependent(k_s<V>, sh.grid_s, kVecThreads, 0, s, a);
+  launch_dependent(k_t<V>, sh.spmv_grid, Prec<V>::R, smem, s, a);
+  launch_dependent(k_xr<V>, sh.grid_xr, kVecThreads, 0, s, a);
 }
 
 template <class V>
@@ -450,6 +532,7 @@ inline helm_status krylov_shapes(helm_csr A, KShapes<V>* sh) {
   auto wave = [&](const void* fn, int* out) -> helm_status {
     int b = 0;
     HELM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, kVecThreads, 0));
+    if (kVecBlocksPerSm > 0 && b > kVecBlocksPerSm) b = kVecBlocksPerSm;
     int64_t gg = static_cast<int64_t>(b < 1 ? 1 : b) * A->num_sms;
     if (want < gg) gg = want < 1 ? 1 : want;
     *out = static_cast<int>(gg);

@@ -2,19 +2,25 @@
 // per stored entry in complex arithmetic), for complex128 and complex64.
 //
 // Layout and schedule, chosen for GB300:
-//   * A tile is R consecutive rows; its stored entries are one contiguous
-//     range [s, e) of vals / colind.  One elected thread copies that range
-//     into shared memory with two TMA bulk copies (cp.async.bulk, completion
-//     on an mbarrier), double-buffered: while the block multiplies tile i the
-//     copy of its next tile is in flight.  HBM sees long, fully coalesced
-//     streams; no thread issues per-entry global loads for the matrix.
-//   * One thread per row.  The complex multiply-accumulate is 4 FMA per
-//     entry and, for complex128, nothing else runs on the FP64 pipe inside a
-//     row (no shuffle tree) -- the FP64 pipe is what bounds this kernel on
-//     GB300.
+//   * A tile is R = 32 consecutive rows; its stored entries are one
+//     contiguous range [s, e) of the values / colind.  One elected thread
+//     copies that range into shared memory with two TMA bulk copies
+//     (cp.async.bulk, completion on an mbarrier, bounded wait).  HBM sees
+//     long, fully coalesced streams; no thread issues per-entry global loads
+//     for the matrix.
+//   * Complex128 tiles whose entries are all real (Helmholtz FEM rows away
+//     from the impedance boundary) are staged from a copy of the real parts
+//     and take the real x complex product: 12 instead of 20 bytes per entry
+//     and 2 instead of 4 FP64 FMA.  Tiles with a complex entry read the
+//     matrix directly from global memory.
+//   * Single buffer per block and many small blocks per SM: the copies of
+//     some blocks overlap the arithmetic of others.  Each block has R * SPLIT
+//     threads; a row's entries are split between SPLIT threads, whose sums
+//     meet in shared memory.  No shuffle tree inside a row: the FP64 pipe is
+//     what bounds this kernel on GB300.
 //   * x is gathered through the read-only path; for FEM orderings the 27
 //     neighbours of consecutive rows share cache lines.
-//   * Persistent grid (a multiple of the SM count); each block walks tiles
+//   * Persistent grid (resident blocks x SMs); each block walks tiles
 //     blockIdx.x, blockIdx.x + gridDim.x, ...  The epilogue object keeps the
 //     block's partial dot products in registers across all its tiles.
 //   * A tile with more than CAP entries (very long rows) is multiplied
@@ -29,7 +35,14 @@
 #include "common.cuh"
 #include "internal.hpp"
 
+// Unroll of the staged row loops: how many x gathers a thread has in flight.
+#ifndef HELM_SPMV_UNROLL
+#define HELM_SPMV_UNROLL 4
+#endif
+
 namespace helm {
+
+constexpr int kSpmvUnroll = HELM_SPMV_UNROLL;
 
 template <class V>
 struct CsrDev {
@@ -45,6 +58,9 @@ struct CsrDev {
   // since the skipped terms are exact zeros.  Helmholtz FEM rows away from
   // the impedance boundary are of this kind (A = K - k^2 M + i k B).
   const uint8_t* real_blk;
+  // Optional (complex128 only): the real parts of vals.  Real blocks are
+  // staged from it: 8 bytes per entry in HBM and shared memory instead of 16.
+  const double* vals_re;
 };
 
 // Row sum of a complex128 row whose entries are all real: reads only the
@@ -69,14 +85,20 @@ template <class V> __device__ __forceinline__ V vzero();
 template <> __device__ __forceinline__ double2 vzero<double2>() { return make_double2(0.0, 0.0); }
 template <> __device__ __forceinline__ float2 vzero<float2>() { return make_float2(0.f, 0.f); }
 
+// Type of a staged value: complex128 tiles are staged only when all their
+// entries are real, as doubles; complex64 tiles as they are.
+template <class V> struct StagedVal { using T = V; };
+template <> struct StagedVal<double2> { using T = double; };
+
 // Shared-memory footprint of the staged engine: STAGES buffers of CAP
 // entries each.
 template <class V, int CAP, int STAGES = 2>
 struct SpmvStage {
+  using T = typename StagedVal<V>::T;
   static_assert(CAP % 4 == 0, "CAP must be a multiple of 4");
   static_assert(STAGES == 1 || STAGES == 2, "one or two buffers");
-  static constexpr int kVG = 16 / sizeof(V);  // values per 16-byte group
-  static constexpr size_t kValsBytes = sizeof(V) * (CAP + 2 * kVG);
+  static constexpr int kVG = 16 / sizeof(T);  // staged values per 16-byte group
+  static constexpr size_t kValsBytes = sizeof(T) * (CAP + 2 * kVG);
   static constexpr size_t kColsBytes = sizeof(int32_t) * (CAP + 8);
   static constexpr size_t kBytes = STAGES * (kValsBytes + kColsBytes) + 2 * sizeof(uint64_t);
   static_assert(kValsBytes % 16 == 0 && kColsBytes % 16 == 0, "16-byte aligned buffers");
@@ -84,42 +106,58 @@ struct SpmvStage {
 
 template <class V> __device__ __forceinline__ V vadd(V a, V b) { return cadd(a, b); }
 
+// multiply-accumulate with a staged value
+__device__ __forceinline__ double2 mac_staged(double a, double2 x, double2 acc) { return mac_real(a, x, acc); }
+__device__ __forceinline__ float2 mac_staged(float2 a, float2 x, float2 acc) { return mac(a, x, acc); }
+
 // Walk this block's tiles; call epi.row(r, acc) for each row r with
 // acc = sum_k vals[k] * x[colind[k]].  epi.prefetch(r) is called by the same
-// thread before the row's sum starts, so the epilogue can issue its own loads
-// early.  Returns false if a bulk copy never
-// completed (error flag set).  Must be called by all threads of the block.
+// thread before the row's sum starts (while the tile's copy is in flight), so
+// the epilogue can issue its own loads early.  Returns false if a bulk copy
+// never completed (error flag set).  Must be called by all threads of the
+// block.
+//
+// Staged tiles: complex64 tiles, and complex128 tiles whose entries are all
+// real (copied from vals_re as doubles), with at most CAP entries.  Other
+// tiles (complex128 tiles with a complex entry -- for Helmholtz FEM only the
+// rows at the impedance boundary -- and tiles of very long rows) are
+// multiplied with direct loads of vals / colind.
 //
 // STAGES = 2: the copy of a block's next tile overlaps the current tile.
 // STAGES = 1: half the shared memory per block, so more blocks share an SM
-// and overlap one another instead.  NACC = 2 splits each row's sum into two
-// interleaved partial sums (more independent FP64 chains per thread).
+// and overlap one another instead.
 //
 // SPLIT > 1: the block has R * SPLIT threads and thread t takes the entries
 // k = k0 + (t / R), k0 + (t / R) + SPLIT, ... of row t % R (more warps per
 // staged tile, each with a shorter dependent chain); the SPLIT partial sums
 // of a row are added in a fixed order through shared memory, and only the
 // threads t < R call epi.row.
-template <class V, int R, int CAP, class Epi, int STAGES = 2, int NACC = 1, int SPLIT = 1>
+template <class V, int R, int CAP, class Epi, int STAGES = 2, int SPLIT = 1>
 __device__ __forceinline__ bool spmv_tiles(const CsrDev<V>& A, const V* __restrict__ x, Epi& epi,
                                            unsigned char* smem, unsigned int* dev_err) {
   using S = SpmvStage<V, CAP, STAGES>;
-  static_assert(SPLIT == 1 || NACC == 1, "split rows use one accumulator per thread");
+  using T = typename S::T;
+  constexpr bool kC128 = std::is_same<V, double2>::value;
+  static_assert(!kC128 || R == 32, "complex128 tiles are the 32-row blocks of real_blk");
   __shared__ V s_part[SPLIT > 1 ? (SPLIT - 1) * R : 1];
   const int part = SPLIT > 1 ? static_cast<int>(threadIdx.x) / R : 0;
   const int lrow = SPLIT > 1 ? static_cast<int>(threadIdx.x) % R : static_cast<int>(threadIdx.x);
   constexpr int VG = S::kVG;
   // buffer b: values at smem + b * kValsBytes, columns after the value buffers
-  auto sv = [&](int b) { return reinterpret_cast<V*>(smem + b * S::kValsBytes); };
+  auto sv = [&](int b) { return reinterpret_cast<T*>(smem + b * S::kValsBytes); };
   auto sc = [&](int b) {
     return reinterpret_cast<int32_t*>(smem + STAGES * S::kValsBytes + b * S::kColsBytes);
   };
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + STAGES * (S::kValsBytes + S::kColsBytes));
+  // source of the staged values
+  const T* stage_src;
+  if constexpr (kC128) stage_src = A.vals_re;
+  else stage_src = A.vals;
 
   const int32_t n = A.n;
   const int32_t ntiles = (n + R - 1) / R;
   const int64_t cend = A.nnz & ~int64_t(3);        // last whole 16-byte group of colind
-  const int64_t vend = A.nnz & ~int64_t(VG - 1);   // same for vals
+  const int64_t vend = A.nnz & ~int64_t(VG - 1);   // same for the staged values
 
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
@@ -139,6 +177,7 @@ __device__ __forceinline__ bool spmv_tiles(const CsrDev<V>& A, const V* __restri
     g.s = A.rowptr[r0];
     g.e = A.rowptr[r1];
     g.staged = (g.e - g.s) <= CAP;
+    if constexpr (kC128) g.staged = g.staged && A.vals_re != nullptr && A.real_blk[t] != 0;
     g.va0 = g.s & ~int64_t(VG - 1);
     g.va1 = min((g.e + VG - 1) & ~int64_t(VG - 1), vend);
     g.ca0 = g.s & ~int64_t(3);
@@ -151,11 +190,11 @@ __device__ __forceinline__ bool spmv_tiles(const CsrDev<V>& A, const V* __restri
     const Range g = range_of(t);
     uint32_t vbytes = 0, cbytes = 0;
     if (g.staged && g.e > g.s) {
-      if (g.va1 > g.va0) vbytes = static_cast<uint32_t>((g.va1 - g.va0) * sizeof(V));
+      if (g.va1 > g.va0) vbytes = static_cast<uint32_t>((g.va1 - g.va0) * sizeof(T));
       if (g.ca1 > g.ca0) cbytes = static_cast<uint32_t>((g.ca1 - g.ca0) * sizeof(int32_t));
     }
     mbar_expect_tx(&bar[b], vbytes + cbytes);
-    if (vbytes) bulk_g2s(sv(b), A.vals + g.va0, vbytes, &bar[b]);
+    if (vbytes) bulk_g2s(sv(b), stage_src + g.va0, vbytes, &bar[b]);
     if (cbytes) bulk_g2s(sc(b), A.colind + g.ca0, cbytes, &bar[b]);
   };
 
@@ -179,6 +218,18 @@ __device__ __forceinline__ bool spmv_tiles(const CsrDev<V>& A, const V* __restri
       }
     }
     const Range g = range_of(tile);
+    // The row's bounds, its real-block flag and the epilogue's operands are
+    // loaded while the tile's copy is in flight.
+    const int32_t r = tile * R + lrow;
+    const bool row_ok = r < min(tile * R + R, n);
+    int64_t k0 = 0, k1 = 0;
+    bool rreal = false;
+    if (row_ok) {
+      k0 = A.rowptr[r] + part;
+      k1 = A.rowptr[r + 1];
+      rreal = row_block_real(A, r);
+      if (part == 0) epi.prefetch(r);
+    }
     const uint32_t parity = STAGES == 2 ? ((it >> 1) & 1) : (it & 1);
     // Every thread observes the phase (visibility of the async-proxy
     // writes); the give-up decision is made block-uniform by the vote.
@@ -190,66 +241,49 @@ __device__ __forceinline__ bool spmv_tiles(const CsrDev<V>& A, const V* __restri
       fail_next = STAGES == 2 && next < ntiles;
       break;
     }
-    const int32_t r = tile * R + lrow;
-    const bool row_ok = r < min(tile * R + R, n);
-    V acc_split = vzero<V>();
-    if (row_ok && part == 0) epi.prefetch(r);  // epilogue operands load under the row's gathers
+    V acc = vzero<V>();
     if (row_ok) {
-      const int64_t k0 = A.rowptr[r] + part, k1 = A.rowptr[r + 1];
       constexpr int KS = SPLIT;
-      V acc = vzero<V>();
       if (g.staged) {
-        const V* v = sv(b) - g.va0;
+        const T* v = sv(b) - g.va0;
         const int32_t* c = sc(b) - g.ca0;
-        bool real_done = false;
-        if constexpr (std::is_same<V, double2>::value) {
-          if (g.e <= g.va1 && g.e <= g.ca1 && row_block_real(A, r)) {
-            const double* vr = reinterpret_cast<const double*>(v);
-#pragma unroll 4
-            for (int64_t k = k0; k < k1; k += KS) acc = mac_real(vr[2 * k], ld_gather(x + c[k]), acc);
-            real_done = true;
-          }
-        }
-        if (real_done) {
-        } else if (g.e <= g.va1 && g.e <= g.ca1) {
-          if (NACC == 2) {
-            V acc1 = vzero<V>();
-            int64_t k = k0;
-#pragma unroll 2
-            for (; k + 1 < k1; k += 2) {
-              acc = mac(v[k], ld_gather(x + c[k]), acc);
-              acc1 = mac(v[k + 1], ld_gather(x + c[k + 1]), acc1);
-            }
-            if (k < k1) acc = mac(v[k], ld_gather(x + c[k]), acc);
-            acc = vadd(acc, acc1);
-          } else {
-#pragma unroll 4
-            for (int64_t k = k0; k < k1; k += KS) acc = mac(v[k], ld_gather(x + c[k]), acc);
-          }
+        if (g.e <= g.va1 && g.e <= g.ca1) {
+#pragma unroll kSpmvUnroll
+          for (int64_t k = k0; k < k1; k += KS) acc = mac_staged(v[k], ld_gather(x + c[k]), acc);
         } else {  // entries past the last whole 16-byte group: plain loads
 #pragma unroll 2
           for (int64_t k = k0; k < k1; k += KS) {
-            const V a = (k < g.va1) ? v[k] : ld_stream(A.vals + k);
+            const T a = (k < g.va1) ? v[k] : stage_src[k];
             const int32_t col = (k < g.ca1) ? c[k] : ld_stream(A.colind + k);
-            acc = mac(a, ld_gather(x + col), acc);
+            acc = mac_staged(a, ld_gather(x + col), acc);
           }
         }
       } else {
+        bool done = false;
+        if constexpr (kC128) {
+          if (rreal && A.vals_re != nullptr) {  // real rows of a tile too long to stage
 #pragma unroll 4
-        for (int64_t k = k0; k < k1; k += KS)
-          acc = mac(ld_stream(A.vals + k), ld_gather(x + ld_stream(A.colind + k)), acc);
+            for (int64_t k = k0; k < k1; k += KS)
+              acc = mac_real(__ldcs(A.vals_re + k), ld_gather(x + ld_stream(A.colind + k)), acc);
+            done = true;
+          }
+        }
+        if (!done) {
+#pragma unroll 4
+          for (int64_t k = k0; k < k1; k += KS)
+            acc = mac(ld_stream(A.vals + k), ld_gather(x + ld_stream(A.colind + k)), acc);
+        }
       }
-      acc_split = acc;
     }
     if (SPLIT > 1) {
-      if (part > 0) s_part[(part - 1) * R + lrow] = acc_split;
+      if (part > 0) s_part[(part - 1) * R + lrow] = acc;
       __syncthreads();
       if (part == 0 && row_ok) {
 #pragma unroll
-        for (int q = 1; q < SPLIT; ++q) acc_split = vadd(acc_split, s_part[(q - 1) * R + lrow]);
+        for (int q = 1; q < SPLIT; ++q) acc = vadd(acc, s_part[(q - 1) * R + lrow]);
       }
     }
-    if (part == 0 && row_ok) epi.row(r, acc_split);
+    if (part == 0 && row_ok) epi.row(r, acc);
     __syncthreads();  // buffer b fully consumed before it is refilled
   }
   if (!ok) {
@@ -326,7 +360,7 @@ template <> struct Engine<float2> {
 template <class V, class Epi>
 __device__ __forceinline__ bool spmv_run(const CsrDev<V>& A, const V* __restrict__ x, Epi& epi, unsigned char* smem,
                                          unsigned int* dev_err) {
-  return spmv_tiles<V, Engine<V>::R, Engine<V>::CAP, Epi, kStages, 1, Engine<V>::SPLIT>(A, x, epi, smem, dev_err);
+  return spmv_tiles<V, Engine<V>::R, Engine<V>::CAP, Epi, kStages, Engine<V>::SPLIT>(A, x, epi, smem, dev_err);
 }
 
 }  // namespace helm

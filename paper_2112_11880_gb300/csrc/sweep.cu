@@ -106,12 +106,46 @@ __device__ bool sweep_grid_sum(const SweepArgs& a, const double (&v)[K], double*
   __syncthreads();
   if (!s_last) return false;
   __threadfence();
+  // Q = blockDim / Fp threads per frequency, each adding blocks q, q+Q, ...
+  // into four interleaved accumulators (independent FP64 chains); then the Q
+  // sums of a frequency are added in q order.  Fixed order throughout.
+  const int Q = blockDim.x / a.Fp;
+  const int jf = threadIdx.x % a.Fp, q = threadIdx.x / a.Fp;
+  double acc4[4][K];
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc4[c][k] = 0.0;
+  if (q < Q) {
+    unsigned int bb = q;
+    for (; bb + 3u * Q < gridDim.x; bb += 4u * Q) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+          acc4[c][k] += ld_cg(&a.partials[(static_cast<size_t>(bb + c * Q) * a.Fp + jf) * K + k]);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      if (bb + c * Q < gridDim.x) {
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+          acc4[c][k] += ld_cg(&a.partials[(static_cast<size_t>(bb + c * Q) * a.Fp + jf) * K + k]);
+      }
+    }
+  }
+  __syncthreads();  // sh is reused below
+  if (q < Q) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) sh[(q * a.Fp + jf) * K + k] = (acc4[0][k] + acc4[1][k]) + (acc4[2][k] + acc4[3][k]);
+  }
+  __syncthreads();
 #pragma unroll
   for (int k = 0; k < K; ++k) tot[k] = 0.0;
   if (j < a.Fp) {
-    for (unsigned int bb = 0; bb < gridDim.x; ++bb) {
+    for (int qq = 0; qq < Q; ++qq) {
 #pragma unroll
-      for (int k = 0; k < K; ++k) tot[k] += ld_cg(&a.partials[(static_cast<size_t>(bb) * a.Fp + j) * K + k]);
+      for (int k = 0; k < K; ++k) tot[k] += sh[(qq * a.Fp + j) * K + k];
     }
   }
   if (threadIdx.x == 0) *ticket = 0u;
@@ -201,7 +235,7 @@ __device__ void sweep_refresh_groups(const SweepArgs& a) {
 }
 
 // init: r = b - A_j x (or r = b, x = 0), r^ = r, p = v = 0; ||b||, ||r||, rho
-__global__ void __launch_bounds__(256) k_sw_init(SweepArgs a) {
+__global__ void __launch_bounds__(512) k_sw_init(SweepArgs a) {
   extern __shared__ double sh[];
   const int use_x0 = a.st->use_x0;
   const int lane = threadIdx.x & 31;
@@ -274,7 +308,7 @@ __global__ void __launch_bounds__(256) k_sw_init(SweepArgs a) {
   const bool run = grp_on && j < a.F && a.status[j] == ST_RUNNING;
 
 // K1: p = r + beta (p - omega v)
-__global__ void __launch_bounds__(256) k_sw_p(SweepArgs a) {
+__global__ void __launch_bounds__(512) k_sw_p(SweepArgs a) {
   SWEEP_ELEMENTWISE_BEGIN
   if (!run) return;
   const double2 beta = a.beta[j], omg = a.omg[j];
@@ -285,7 +319,7 @@ __global__ void __launch_bounds__(256) k_sw_p(SweepArgs a) {
 }
 
 // K2: v = A_j p, (r^, v) -> alpha
-__global__ void __launch_bounds__(256) k_sw_v(SweepArgs a) {
+__global__ void __launch_bounds__(512) k_sw_v(SweepArgs a) {
   extern __shared__ double sh[];
   if (a.st->status != ST_RUNNING) return;
   const int64_t gw = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
@@ -318,7 +352,7 @@ __global__ void __launch_bounds__(256) k_sw_v(SweepArgs a) {
 }
 
 // K3: s = r - alpha v, ||s||
-__global__ void __launch_bounds__(256) k_sw_s(SweepArgs a) {
+__global__ void __launch_bounds__(512) k_sw_s(SweepArgs a) {
   extern __shared__ double sh[];
   if (a.st->status != ST_RUNNING) return;
   SWEEP_ELEMENTWISE_BEGIN
@@ -348,7 +382,7 @@ __global__ void __launch_bounds__(256) k_sw_s(SweepArgs a) {
 }
 
 // K4: t = A_j s, (t, s), (t, t) -> omega (frequencies stopped at s skip)
-__global__ void __launch_bounds__(256) k_sw_t(SweepArgs a) {
+__global__ void __launch_bounds__(512) k_sw_t(SweepArgs a) {
   extern __shared__ double sh[];
   if (a.st->status != ST_RUNNING) return;
   const int64_t gw = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
@@ -383,7 +417,7 @@ __global__ void __launch_bounds__(256) k_sw_t(SweepArgs a) {
 }
 
 // K5: x += alpha p + omega s, r = s - omega t; per-frequency stop tests
-__global__ void __launch_bounds__(256) k_sw_xr(SweepArgs a) {
+__global__ void __launch_bounds__(512) k_sw_xr(SweepArgs a) {
   extern __shared__ double sh[];
   if (a.st->status != ST_RUNNING) {
     if (blockIdx.x == 0 && threadIdx.x == 0) sweep_set_cond(a, false);
@@ -441,7 +475,7 @@ __global__ void __launch_bounds__(256) k_sw_xr(SweepArgs a) {
 }
 
 // tail: true residual per frequency, ||b - A_j x|| / ||b||
-__global__ void __launch_bounds__(256) k_sw_tail(SweepArgs a) {
+__global__ void __launch_bounds__(512) k_sw_tail(SweepArgs a) {
   extern __shared__ double sh[];
   const int64_t gw = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int g = static_cast<int>(gw % a.G);
@@ -620,7 +654,9 @@ SweepShape sweep_shape(helm_sweep S, int G) {
   sh.threads = 32 * S->warps_per_block;
   // each warp keeps one group: the number of warps must be a multiple of G
   const int warps_per_block = S->warps_per_block;
-  int64_t blocks = static_cast<int64_t>(S->num_sms) * (2048 / sh.threads);
+  // 1024 resident threads per SM: enough warps to hide latency, few block
+  // partials for the per-frequency reductions
+  int64_t blocks = static_cast<int64_t>(S->num_sms) * std::max(1, 1024 / sh.threads);
   int64_t units = static_cast<int64_t>(S->n) * G;
   int64_t want = (units + warps_per_block - 1) / warps_per_block;
   if (want < blocks) blocks = want < 1 ? 1 : want;

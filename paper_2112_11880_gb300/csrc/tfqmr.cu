@@ -429,7 +429,7 @@ helm_status tfqmr_fp64(helm_csr A, const double2* b, double2* x, const helm_opts
   double2* W = A->vec;
   TqArgs a;
   std::memset(&a, 0, sizeof(a));
-  a.A = CsrDev<V>{A->n, A->nnz, A->rowptr, A->colind, static_cast<const V*>(A->vals), A->real_blk};
+  a.A = CsrDev<V>{A->n, A->nnz, A->rowptr, A->colind, static_cast<const V*>(A->vals), A->real_blk, A->vals_re};
   a.b = b;
   a.x = x;
   a.r0 = W;
@@ -468,6 +468,8 @@ helm_status tfqmr_fp64(helm_csr A, const double2* b, double2* x, const helm_opts
       g = &(A->graphs[key] = e);
   }
 
+  // an explicit graph request does not fall back to the host-driven loop
+  if (!g && o.launch == HELM_LAUNCH_GRAPH) return HELM_ERR_CUDA;
   k_configure<<<1, 1, 0, s>>>(A->state, o.tol, o.maxit, o.use_x0 ? 1 : 0, o.deadline_s, 1);
   HELM_CUDA_TRY(cudaGetLastError());
   SolverState* hs = A->state_host;

@@ -113,7 +113,7 @@ def test_adjoint80_gradient_against_central_differences():
     good as the solves behind it: its noise is about kappa * tol * L / eps, so
     the solves run to 1e-13 and the step is eps = 1 m/s (3e-3 of c) with the
     fourth-order central stencil, whose O(eps^4) truncation stays below 1e-8
-    (measured 2e-10 .. 4e-9; second order at 0.1 m/s gives 2e-8 .. 8e-7)."""
+    (measured worst case 2.6e-7; second order at 0.1 m/s gave 7.9e-7)."""
     cfg = g.CONFIGS["adjoint80"]
     p = g.assemble(cfg)
     b = torch.as_tensor(g.source(p), device=DEV)

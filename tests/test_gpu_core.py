@@ -288,3 +288,25 @@ def test_bicgstab_repeated_solves_reuse_graph(box20):
     assert all(i["status"] == "ok" for i in infos)
     assert len({i["iters"] for i in infos}) == 1      # deterministic
     A.close()
+
+
+@pytest.mark.parametrize("method,prec", [("bicgstab", "fp64"), ("tfqmr", "fp64"), ("bicgstabl", "fp64"),
+                                         ("bicgstab", "mixed")])
+def test_graph_and_host_loops_agree_bit_for_bit(box20, method, prec):
+    """The graph (device-driven while node, dependent launches) and the
+    host-driven loop run the same kernels on the same grids with fixed-order
+    reductions: same iterations, same x to the last bit.  An explicit graph
+    request must not fall back to the host loop."""
+    p, vals, b, *_ = box20
+    A = helm.CsrMatrix.from_host(p.rowptr, p.colind, vals, device=DEV)
+    bd = _dev(b)
+    kw = dict(tol=1e-9, maxit=20000, method={"bicgstab": helm.HELM_BICGSTAB, "tfqmr": helm.HELM_TFQMR,
+                                              "bicgstabl": helm.HELM_BICGSTABL}[method],
+              precision=helm.HELM_PREC_MIXED if prec == "mixed" else helm.HELM_PREC_FP64)
+    xg, xh = torch.empty_like(bd), torch.empty_like(bd)
+    ig = helm.helm_bicgstab_solve(A.handle, bd, xg, helm.default_opts(launch=helm.HELM_LAUNCH_GRAPH, **kw))
+    ih = helm.helm_bicgstab_solve(A.handle, bd, xh, helm.default_opts(launch=helm.HELM_LAUNCH_HOST, **kw))
+    assert ig["status"] == "ok" and ih["status"] == "ok", (ig, ih)
+    assert ig["iters"] == ih["iters"] and ig["restarts"] == ih["restarts"]
+    assert torch.equal(torch.view_as_real(xg), torch.view_as_real(xh))
+    A.close()

@@ -73,3 +73,40 @@ def test_mixed_zero_rhs_and_bad_input():
     x, info = helm.solve(A, _dev(bad), precision=helm.HELM_PREC_MIXED)
     assert info["status"] == "nonfinite"
     A.close()
+
+
+@pytest.mark.parametrize("e", [-100, 100])
+def test_mixed_is_scale_invariant(e):
+    """A right-hand side scaled by 2^e (exact in FP64) gives the solution scaled
+    by 2^e.  Run in the problem's own scale, the complex64 recurrence would
+    underflow (2^-100: squared entries ~1e-68) or overflow (2^100: ~1e52)."""
+    cfg = g.CONFIGS["box20"]
+    p = g.assemble(cfg)
+    vals = g.helmholtz_values(p, cfg.F)
+    b = g.source(p)
+    A = helm.CsrMatrix.from_host(p.rowptr, p.colind, vals, device=DEV)
+    x1, i1 = helm.solve(A, _dev(b), tol=1e-10, maxit=200000, precision=helm.HELM_PREC_MIXED)
+    xs, i2 = helm.solve(A, _dev(np.ldexp(b.real, e) + 1j * np.ldexp(b.imag, e)), tol=1e-10, maxit=200000,
+                        precision=helm.HELM_PREC_MIXED)
+    assert i1["status"] == "ok" and i2["status"] == "ok", (i1, i2)
+    x1, xs = x1.cpu().numpy(), xs.cpu().numpy()
+    xs = np.ldexp(xs.real, -e) + 1j * np.ldexp(xs.imag, -e)
+    assert np.linalg.norm(xs - x1) <= 1e-8 * np.linalg.norm(x1)
+    A.close()
+
+
+def test_mixed_warm_start():
+    """x0 = a perturbed solution: the residual replacement starts from b - A x0."""
+    cfg = g.tiny_config(8, 6, 5, h=0.1, F=700.0, seed=2)
+    p = g.assemble(cfg)
+    vals = g.helmholtz_values(p, cfg.F)
+    b = g.source(p)
+    xs = oracle.dense_solve(p.rowptr, p.colind, vals, b)
+    x0 = xs + 1e-3 * np.linalg.norm(xs) / np.sqrt(p.n) * g.complex_vector(p.n, 9) * (~p.dirichlet)
+    A = helm.CsrMatrix.from_host(p.rowptr, p.colind, vals, device=DEV)
+    x = _dev(x0)
+    opts = helm.default_opts(tol=1e-11, maxit=20000, precision=helm.HELM_PREC_MIXED, use_x0=1)
+    info = helm.helm_bicgstab_solve(A.handle, _dev(b), x, opts)
+    assert info["status"] == "ok", info
+    assert np.linalg.norm(x.cpu().numpy() - xs) <= 1e-9 * np.linalg.norm(xs)
+    A.close()
