@@ -49,7 +49,7 @@ def load_peaks():
 
 def kernel_source_sha() -> str:
     h = hashlib.sha256()
-    for f in ("spmv.cuh", "common.cuh", "api.cu"):
+    for f in ("spmv.cuh", "common.cuh", "api.cu", "internal.hpp"):
         with open(os.path.join(ROOT, "paper_2112_11880_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -505,7 +505,7 @@ def main():
     ap.add_argument("--ref-step-iters", type=int, default=60)
     ap.add_argument("--ref-iters-per-solve", type=int, default=int(os.environ.get("HELM_ITERS_PER_SOLVE", "0")) or 0)
     ap.add_argument("--mixed-maxit", type=int, default=200000)
-    ap.add_argument("--inner-tol", type=float, default=1e-4)
+    ap.add_argument("--inner-tol", type=float, default=1e-3)
     ap.add_argument("--mode", default="bench", choices=["bench", "spmv", "extensions"],
                     help="spmv: only the complex128 SpMV loop on the same matrix (profiling target)")
     ap.add_argument("--reps", type=int, default=20)

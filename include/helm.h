@@ -163,12 +163,12 @@ typedef enum { HELM_BICGSTAB = 0, HELM_TFQMR = 1, HELM_BICGSTABL = 2 } helm_meth
 /* Arithmetic of the solve. */
 typedef enum {
   HELM_PREC_FP64 = 0, /* complex128 throughout */
-  HELM_PREC_MIXED = 1 /* complex64 BiCGStab (values converted once into a
-                         handle-owned copy) with reliable updates: the
-                         solution is accumulated and the residual b - A x
-                         recomputed in FP64 whenever the complex64 residual
-                         has dropped 10x, and convergence is decided on that
-                         FP64 residual */
+  HELM_PREC_MIXED = 1 /* iterative refinement: complex64 BiCGStab inner
+                         solves (values converted once into a handle-owned
+                         copy), each ended when its residual has dropped by
+                         opts.inner_tol; the solution is accumulated and the
+                         residual b - A x recomputed in FP64 after each, and
+                         convergence is decided on that FP64 residual */
 } helm_precision;
 /* How the iteration loop is driven on the device. */
 typedef enum {
@@ -189,8 +189,10 @@ typedef struct {
   int32_t use_x0;      /* 0: start from x = 0 (Section 4); 1: start from d_x */
   int32_t method;      /* helm_method */
   int32_t precision;   /* helm_precision */
-  double inner_tol;    /* reserved (mixed precision updates on a fixed
-                          10x drop of the complex64 residual) */
+  double inner_tol;    /* mixed precision: an inner solve ends when its
+                          residual has dropped by this factor (0 or >= 1:
+                          only when it looks below tol), or after 20000
+                          iterations */
   double deadline_s;   /* device wall-clock limit of one solve; <= 0: none */
   int32_t ell;         /* l of BiCGStab(l), 1..8 */
   int32_t launch;      /* helm_launch */
@@ -200,14 +202,14 @@ typedef struct {
   int32_t iters;        /* iterations performed (all restarts / refinement
                            steps included; for mixed precision, inner
                            iterations) */
-  int32_t restarts;     /* restarts (BiCGStab) or FP64 reliable updates (mixed) */
+  int32_t restarts;     /* restarts (BiCGStab) or FP64 refinement steps (mixed) */
   double relres_recur;  /* last recurrence residual / ||b|| */
   double relres_true;   /* ||b - A x|| / ||b|| recomputed in FP64 at the end */
   helm_status status;
   int32_t spmv_count;   /* applications of A (all precisions) */
 } helm_info;
 
-/* Defaults: tol 1e-8, maxit 20000, use_x0 0, BiCGStab, FP64, inner_tol 1e-5,
+/* Defaults: tol 1e-8, maxit 20000, use_x0 0, BiCGStab, FP64, inner_tol 1e-3,
  * no deadline, ell 2, launch auto. */
 void helm_opts_default(helm_opts* o);
 

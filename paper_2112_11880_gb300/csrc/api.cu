@@ -334,7 +334,7 @@ void helm_opts_default(helm_opts* o) {
   o->use_x0 = 0;
   o->method = HELM_BICGSTAB;
   o->precision = HELM_PREC_FP64;
-  o->inner_tol = 1e-5;
+  o->inner_tol = 1e-3;
   o->deadline_s = 0.0;
   o->ell = 2;
   o->launch = HELM_LAUNCH_AUTO;

@@ -110,7 +110,9 @@ helm_status bicgstab_fp64(helm_csr A, const double2* b, double2* x, const helm_o
   a.partials = A->partials;
   a.tickets = A->tickets;
   a.dev_err = A->dev_err;
-  TailFp64 tail{sh.spmv_grid};
+  TailFp64 tail{0};
+  HELM_TRY(persistent_grid({reinterpret_cast<const void*>(&k_tail)}, R, kSmem, A->num_sms,
+                           (static_cast<int64_t>(n) + Engine<V>::R - 1) / Engine<V>::R, &tail.grid));
 
   // Graph for this (b, x), built once and reused.
   GraphEntry* g = nullptr;

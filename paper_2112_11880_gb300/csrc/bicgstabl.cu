@@ -455,12 +455,10 @@ helm_status bicgstabl_fp64(helm_csr A, const double2* b, double2* x, const helm_
     HELM_CUDA_TRY(set_smem_attr(fn, kSmem));
   BlShapes sh;
   {
-    int per_sm = 0;
-    HELM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bl_au, RT, kSmem));
-    per_sm = per_sm < 1 ? 1 : per_sm;
-    const int ntiles = (A->n + Engine<V>::R - 1) / Engine<V>::R;
-    sh.spmv_grid = per_sm * A->num_sms;
-    if (ntiles < sh.spmv_grid) sh.spmv_grid = ntiles < 1 ? 1 : ntiles;
+    HELM_TRY(persistent_grid({reinterpret_cast<const void*>(&k_bl_init), reinterpret_cast<const void*>(&k_bl_au),
+                              reinterpret_cast<const void*>(&k_bl_ar), reinterpret_cast<const void*>(&k_bl_tail)},
+                             RT, kSmem, A->num_sms, (static_cast<int64_t>(A->n) + Engine<V>::R - 1) / Engine<V>::R,
+                             &sh.spmv_grid));
     sh.vec_grid = A->vec_grid;
     // the Gram kernel keeps 2 (l+1)(l+2)/2 accumulators per thread: few
     // blocks, and its partials (blocks x 45 x 2 doubles + coefficients) must

@@ -202,9 +202,10 @@ __device__ __forceinline__ void block_sum(double (&v)[K], double* red) {
 // every thread of the last block; `tot` then holds the totals in thread 0.
 // The counter is reset by the last block, so a kernel can use it again in its
 // next launch.
-template <int K>
+template <int K, int B = 4>
 __device__ __forceinline__ bool grid_sum_last(double (&v)[K], double* partials,
                                               unsigned int* ticket, double* red, double (&tot)[K]) {
+  static_assert(B % 4 == 0, "B is a multiple of the four accumulators");
   __shared__ bool s_last;
   block_sum<K>(v, red);
   if (threadIdx.x == 0) {
@@ -217,7 +218,7 @@ __device__ __forceinline__ bool grid_sum_last(double (&v)[K], double* partials,
   __syncthreads();
   if (!s_last) return false;
   __threadfence();
-  // Thread j sums partials j + T (4 m + q) into accumulator q, then adds the
+  // Thread j sums partials j + T m into accumulator m mod 4, then adds the
   // four accumulators in order: a fixed order for every addition (four
   // independent FP64 chains hide the DADD latency); the block tree follows.
   double acc[K], acc4[4][K];
@@ -225,19 +226,26 @@ __device__ __forceinline__ bool grid_sum_last(double (&v)[K], double* partials,
   for (int q = 0; q < 4; ++q)
 #pragma unroll
     for (int k = 0; k < K; ++k) acc4[q][k] = 0.0;
+  // B partials are loaded before they are added (one L2 round trip per B);
+  // partial j + T m goes to accumulator m mod 4 whatever B is.
   const unsigned int T = blockDim.x;
   unsigned int b = threadIdx.x;
-  for (; b + 3 * T < gridDim.x; b += 4 * T) {
+  for (; b + (B - 1) * T < gridDim.x; b += B * T) {
+    double w[B][K];
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
+    for (int q = 0; q < B; ++q)
 #pragma unroll
-      for (int k = 0; k < K; ++k) acc4[q][k] += ld_cg(&partials[(size_t)(b + q * T) * K + k]);
+      for (int k = 0; k < K; ++k) w[q][k] = ld_cg(&partials[(size_t)(b + q * T) * K + k]);
+#pragma unroll
+    for (int q = 0; q < B; ++q)
+#pragma unroll
+      for (int k = 0; k < K; ++k) acc4[q & 3][k] += w[q][k];
   }
 #pragma unroll
-  for (int q = 0; q < 3; ++q) {
+  for (int q = 0; q < B - 1; ++q) {
     if (b + q * T < gridDim.x) {
 #pragma unroll
-      for (int k = 0; k < K; ++k) acc4[q][k] += ld_cg(&partials[(size_t)(b + q * T) * K + k]);
+      for (int k = 0; k < K; ++k) acc4[q & 3][k] += ld_cg(&partials[(size_t)(b + q * T) * K + k]);
     }
   }
 #pragma unroll

@@ -18,6 +18,7 @@ namespace helm {
 struct SolverState {
   double2 rho, alpha, omega, beta;
   double2 aux[4];          // method-specific scalars
+  double2 gamma;           // mixed precision: step length of the last refinement step
   double bnorm, tol, relres, relres_true;
   double tau, theta, eta;  // TFQMR
   int32_t iter, maxit, status, phase;
@@ -90,6 +91,12 @@ struct helm_csr_s {
 };
 
 namespace helm {
+
+#define HELM_TRY(expr)                   \
+  do {                                   \
+    const helm_status _s = (expr);       \
+    if (_s != HELM_OK) return _s;        \
+  } while (0)
 
 #define HELM_CUDA_TRY(expr)                          \
   do {                                               \

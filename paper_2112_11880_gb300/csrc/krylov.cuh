@@ -24,6 +24,7 @@
 #pragma once
 
 #include <cstring>
+#include <initializer_list>
 #include <utility>
 
 #include "common.cuh"
@@ -33,13 +34,13 @@
 namespace helm {
 
 // SolverState::method of the Krylov loop: plain, or the inner loop of the
-// mixed-precision solve with reliable updates (aux[0] = (max ||r|| since the
-// last update, iteration of the last update), aux[1].x = update due,
-// aux[2].x = scale of the inner residual).
+// mixed-precision solve (aux[0] = (||r|| when the process began, in its
+// scale; iteration it began), aux[1].x = refinement step due, aux[2].x =
+// scale of the inner residual, aux[3] = (steps in a row without a 2x gain,
+// inner_tol)).
 constexpr int32_t kModePlain = 0;
-constexpr int32_t kModeReliable = 1;
-constexpr double kRelDelta = 0.1;
-constexpr int kRelMaxGap = 2000;
+constexpr int32_t kModeRefine = 1;
+constexpr int kInnerMax = 20000;  // inner iterations per refinement step at most
 
 template <class V> struct Prec;
 template <> struct Prec<double2> {
@@ -178,18 +179,14 @@ __global__ void __launch_bounds__(Prec<V>::R) k_init(KArgs<V> a) {
 // arithmetic, so the 64-clock FP64 latency and the memory latency of one
 // element overlap the other's.
 constexpr int kVecThreads = 256;
-// Blocks per SM of the element-wise kernels (0: as many as fit).  Fewer
-// threads take more rows each, which spreads the per-thread share of the
-// block reductions (FP64 adds on the FP64 pipe) over more rows.
-#ifndef HELM_VEC_BPS
-#define HELM_VEC_BPS 0
-#endif
-constexpr int kVecBlocksPerSm = HELM_VEC_BPS;
 
 // K1: p = r + beta (p - omega v)
 template <class V>
 __global__ void __launch_bounds__(kVecThreads) k_p(KArgs<V> a) {
   const SolverState* st = a.st;
+  // K2 may start staging the matrix at once (it waits for p itself); K1 is
+  // launched the ordinary way, after the previous iteration has completed
+  pdl_launch_dependents();
   if (st->status != ST_RUNNING) return;
   const V beta = Prec<V>::cvt(st->beta), omega = Prec<V>::cvt(st->omega);
   const int32_t n = a.A.n;
@@ -223,9 +220,6 @@ __global__ void __launch_bounds__(Prec<V>::R) k_v(KArgs<V> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[32 * 2];
   SolverState* st = a.st;
-  pdl_wait();  // p comes from the previous kernel
-  pdl_launch_dependents();
-  if (st->status != ST_RUNNING) return;
   struct Epi {
     const KArgs<V>* a;
     V part;
@@ -236,10 +230,20 @@ __global__ void __launch_bounds__(Prec<V>::R) k_v(KArgs<V> a) {
       part = cfma_conj(rh, ax, part);
     }
   } epi{&a, vzero<V>(), vzero<V>()};
-  spmv_run<V>(a.A, a.p, epi, smem, a.dev_err);
+  // the first tile's copy is in flight while p (the previous kernel's
+  // output) is waited for
+  bool go = false;
+  spmv_run<V>(a.A, a.p, epi, smem, a.dev_err, [&]() {
+    pdl_wait();
+    pdl_launch_dependents();
+    go = st->status == ST_RUNNING;
+    return go;
+  });
+  if (!go) return;
   double part[2] = {double(epi.part.x), double(epi.part.y)};
   double tot[2];
-  if (!grid_sum_last<2>(part, a.partials, a.tickets + TK_V, red, tot)) return;
+  // many blocks of few threads: eight partials per round trip in the last block
+  if (!grid_sum_last<2, 8>(part, a.partials, a.tickets + TK_V, red, tot)) return;
   if (threadIdx.x != 0) return;
   st->iter += 1;
   st->spmv_count += 1;
@@ -298,7 +302,7 @@ __global__ void __launch_bounds__(kVecThreads) k_s(KArgs<V> a) {
   const double bt = st->bnorm * st->tol;
   if (!isfinite(s2)) {
     st->status = HELM_ERR_NONFINITE;
-  } else if (st->method != kModeReliable && s2 <= bt * bt) {
+  } else if (st->method != kModeRefine && s2 <= bt * bt) {
     st->phase = PH_SCONV;
     st->relres = sqrt(s2) / st->bnorm;
   }
@@ -311,9 +315,6 @@ __global__ void __launch_bounds__(Prec<V>::R) k_t(KArgs<V> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[32 * 3];
   SolverState* st = a.st;
-  pdl_wait();  // s and the phase come from the previous kernel
-  pdl_launch_dependents();
-  if (st->status != ST_RUNNING || st->phase != PH_RUN) return;
   struct Epi {
     const KArgs<V>* a;
     V ts;
@@ -326,10 +327,19 @@ __global__ void __launch_bounds__(Prec<V>::R) k_t(KArgs<V> a) {
       tt = cabs2_acc(ax, tt);
     }
   } epi{&a, vzero<V>(), S(0), vzero<V>()};
-  spmv_run<V>(a.A, a.s, epi, smem, a.dev_err);
+  // the first tile's copy is in flight while s and the phase (the previous
+  // kernel's output) are waited for
+  bool go = false;
+  spmv_run<V>(a.A, a.s, epi, smem, a.dev_err, [&]() {
+    pdl_wait();
+    pdl_launch_dependents();
+    go = st->status == ST_RUNNING && st->phase == PH_RUN;
+    return go;
+  });
+  if (!go) return;
   double part[3] = {double(epi.ts.x), double(epi.ts.y), double(epi.tt)};
   double tot[3];
-  if (!grid_sum_last<3>(part, a.partials, a.tickets + TK_T, red, tot)) return;
+  if (!grid_sum_last<3, 8>(part, a.partials, a.tickets + TK_T, red, tot)) return;
   if (threadIdx.x != 0) return;
   st->spmv_count += 1;
   const double2 ts = make_double2(tot[0], tot[1]);
@@ -410,7 +420,7 @@ __global__ void __launch_bounds__(kVecThreads) k_xr(KArgs<V> a) {
   if (!grid_sum_last<3>(part, a.partials, a.tickets + TK_XR, red, tot)) return;
   if (threadIdx.x != 0) return;
   // reliable mode runs on a scaled residual: b - A x ~ aux[2].x * r
-  const double sc = st->method == kModeReliable ? st->aux[2].x : 1.0;
+  const double sc = st->method == kModeRefine ? st->aux[2].x : 1.0;
   int status = ST_RUNNING;
   if (phase == PH_SCONV) {
     status = HELM_OK;
@@ -421,16 +431,17 @@ __global__ void __launch_bounds__(kVecThreads) k_xr(KArgs<V> a) {
     const double r2 = tot[2];
     const double bt = st->bnorm * st->tol;
     bool stop_ok = r2 * (sc * sc) <= bt * bt;
-    if (st->method == kModeReliable && isfinite(r2)) {
+    if (st->method == kModeRefine && isfinite(r2)) {
       // mixed precision: the recurrence never declares convergence; it asks
-      // for a reliable update (FP64 residual) when it has dropped by
-      // kRelDelta since the last one, looks converged, or every
-      // kRelMaxGap iterations
+      // for a refinement step (FP64 residual, fresh process) when it has
+      // dropped by inner_tol since the process began, looks converged, or
+      // after kInnerMax iterations (complex64 BiCGStab can stagnate on
+      // strongly indefinite systems; the step's minimal-residual length
+      // keeps a poor inner iterate from increasing the FP64 residual)
       const double rn = sqrt(r2);
-      const double rmax = fmax(st->aux[0].x, rn);
-      st->aux[0].x = rmax;
-      if (stop_ok || rn < kRelDelta * rmax || st->iter - static_cast<int>(st->aux[0].y) >= kRelMaxGap)
-        st->aux[1].x = 1.0;
+      const double cyc = st->aux[3].y;
+      const bool dropped = cyc > 0.0 && cyc < 1.0 && rn <= cyc * st->aux[0].x;
+      if (stop_ok || dropped || st->iter - static_cast<int>(st->aux[0].y) >= kInnerMax) st->aux[1].x = 1.0;
       stop_ok = false;
     }
     if (!isfinite(r2)) {
@@ -466,13 +477,33 @@ __global__ void __launch_bounds__(kVecThreads) k_xr(KArgs<V> a) {
 
 template <class V>
 struct KShapes {
-  int spmv_grid, vec_grid;
+  int spmv_grid;                // K2 and K4
+  int init_grid;                // the init kernel
+  int vec_grid;
   int grid_p, grid_s, grid_xr;  // one wave of each element-wise kernel
 };
 
+// Persistent grid shared by `fns`: the blocks that fit on every SM at once
+// for each of them (so that none runs a second wave, which would leave most
+// of the GPU idle while it finishes), times the SMs, at most `units`.
+inline helm_status persistent_grid(std::initializer_list<const void*> fns, int threads, size_t smem,
+                                   int num_sms, int64_t units, int* grid) {
+  int per_sm = 1 << 30;
+  for (const void* fn : fns) {
+    int b = 0;
+    HELM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, threads, smem));
+    per_sm = b < per_sm ? b : per_sm;
+  }
+  if (per_sm < 1) per_sm = 1;
+  int64_t g = static_cast<int64_t>(per_sm) * num_sms;
+  if (units < g) g = units < 1 ? 1 : units;
+  *grid = static_cast<int>(g);
+  return HELM_OK;
+}
+
 template <class V>
 inline void enqueue_init(const KArgs<V>& a, const KShapes<V>& sh, cudaStream_t s) {
-  k_init<V><<<sh.spmv_grid, Prec<V>::R, Engine<V>::kSmem, s>>>(a);
+  k_init<V><<<sh.init_grid, Prec<V>::R, Engine<V>::kSmem, s>>>(a);
 }
 // Launch with programmatic stream serialization: the kernel may start while
 // its predecessor finishes (it calls pdl_wait() before it reads that
@@ -515,24 +546,20 @@ inline helm_status prepare_krylov_kernels() {
   return HELM_OK;
 }
 
-// Grid of the staged SpMV kernels of the solver: resident blocks per SM x SMs
-// (the same for every SpMV-shaped kernel of the solver: they share the
-// engine's shared-memory footprint).
+// Grids of the solver's kernels: one wave each.
 template <class V>
 inline helm_status krylov_shapes(helm_csr A, KShapes<V>* sh) {
   constexpr size_t smem = Engine<V>::kSmem;
-  int per_sm = 0;
-  HELM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_v<V>, Prec<V>::R, smem));
-  per_sm = per_sm < 1 ? 1 : per_sm;
-  const int ntiles = (A->n + Engine<V>::R - 1) / Engine<V>::R;
-  int g = per_sm * A->num_sms;
-  sh->spmv_grid = ntiles < g ? (ntiles < 1 ? 1 : ntiles) : g;
+  const int64_t ntiles = (static_cast<int64_t>(A->n) + Engine<V>::R - 1) / Engine<V>::R;
+  HELM_TRY(persistent_grid({reinterpret_cast<const void*>(&k_v<V>), reinterpret_cast<const void*>(&k_t<V>)},
+                                       Prec<V>::R, smem, A->num_sms, ntiles, &sh->spmv_grid));
+  HELM_TRY(persistent_grid({reinterpret_cast<const void*>(&k_init<V>)}, Prec<V>::R, smem, A->num_sms, ntiles,
+                                       &sh->init_grid));
   sh->vec_grid = A->vec_grid;
   const int64_t want = (static_cast<int64_t>(A->n) + 2 * kVecThreads - 1) / (2 * kVecThreads);
   auto wave = [&](const void* fn, int* out) -> helm_status {
     int b = 0;
     HELM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, kVecThreads, 0));
-    if (kVecBlocksPerSm > 0 && b > kVecBlocksPerSm) b = kVecBlocksPerSm;
     int64_t gg = static_cast<int64_t>(b < 1 ? 1 : b) * A->num_sms;
     if (want < gg) gg = want < 1 ? 1 : want;
     *out = static_cast<int>(gg);

@@ -1,7 +1,5 @@
-// Mixed-precision solve: one complex64 BiCGStab whose residual is replaced by
-// the FP64 true residual b - A x at "reliable updates" (Sleijpen & van der
-// Vorst 1996; the defect-correction form of iterative refinement that keeps
-// the Krylov recurrence running instead of restarting it at every step).
+// Mixed-precision solve: iterative refinement (defect correction) in FP64
+// around a complex64 BiCGStab, the whole solve in one CUDA graph.
 //
 // The paper's library covers single and double precision (Section 1); here
 // single precision does the bulk of the work and FP64 decides accuracy:
@@ -9,21 +7,29 @@
 //                  handle, 12 bytes per entry instead of 20), vectors
 //                  complex64; products and per-thread sums FP32, block and
 //                  grid sums and every recurrence scalar FP64.  The inner
-//                  vectors carry the residual divided by sigma (unit RMS
-//                  entries at the last update); x32 collects the solution
-//                  increment since the last update in the same scale.
-//   update (FP64): when the recurrence residual has dropped 10x below its
-//                  maximum since the last update (or looks converged, or every
-//                  2000 iterations):  x += sigma x32, x32 = 0;  r64 = b - A x
-//                  in FP64;  stop if ||r64|| / ||b|| <= tol;  new sigma;
-//                  r = complex64(r64 / sigma), p and v rescaled, rho and beta
-//                  moved to the replaced residual -- or, when the recurrence
-//                  had drifted from r64 by more than a tenth of ||r64||, a
-//                  fresh process (r^ = r, p = v = 0) as in restarted
-//                  iterative refinement.
-// The convergence test is always the FP64 true residual.  The whole solve is
-// one graph: init (+ first replacement) -> while(5 FP32 kernels + 3 update
-// kernels) -> tail; the update kernels return at once when no update is due.
+//                  system is A32 d = r / sigma with sigma = ||r|| / sqrt(n)
+//                  (unit RMS entries: in the problem's own scale, b ~ h^3,
+//                  the squared terms of the inner dots would fall below the
+//                  smallest normal float long before FP64 convergence).
+//   step (FP64):   when the inner recurrence residual has dropped by
+//                  inner_tol since the inner solve began, looks below the
+//                  outer tolerance, or after kInnerMax inner iterations:
+//                  w = A (sigma d), gamma = (w, r) / (w, w) (the step that
+//                  minimises ||r - gamma w||, so a poor inner solve cannot
+//                  increase the residual), x += gamma sigma d;
+//                  r = b - A x in FP64;  stop if ||r|| / ||b|| <= tol (or,
+//                  not converged, after three steps in a row without
+//                  halving ||r||);  else a fresh inner solve on the new r
+//                  (r^ = r, p = v = d = 0).
+// The inner operator is A rounded to complex64, so one step gains at most
+// about 1 / (kappa eps_float): an inner_tol near that bound wastes the fewest
+// inner iterations.  Keeping one inner process across steps (replacing its
+// residual only, Sleijpen & van der Vorst 1996) was tried first; on the
+// strongly indefinite 200x100x80 cavity its complex64 recurrence stagnated
+// (and diverged when combined with restarts), while restarted refinement
+// converges.  The convergence test is always the FP64 true residual.
+// Graph: init (+ first inner start) -> while(5 FP32 kernels + 5 step
+// kernels) -> tail; the step kernels return at once when no step is due.
 #include <cmath>
 #include <cstring>
 
@@ -33,12 +39,6 @@ namespace helm {
 
 namespace {
 
-// restart the complex64 Krylov process when ||r64 - sigma r|| > kRelRestart ||r64||
-#ifndef HELM_REL_RESTART
-#define HELM_REL_RESTART 0.1
-#endif
-constexpr double kRelRestart = HELM_REL_RESTART;
-
 constexpr int R128 = Engine<double2>::kThreads;  // threads per SpMV block
 constexpr size_t kSmem128 = Engine<double2>::kSmem;
 
@@ -47,6 +47,7 @@ struct RuArgs {
   const double2* b;
   double2* x;         // FP64 solution (the caller's)
   double2* r64;       // FP64 residual
+  double2* d64;       // FP64 copy of the scaled inner solution
   float2 *x32, *r32, *rh32, *p32, *v32;
   SolverState* st;    // the inner loop's state
   double* partials;
@@ -61,7 +62,7 @@ __device__ __forceinline__ void ru_cond(const RuArgs& a, bool cont) {
 }
 
 // One row of the init: r64 and its partial sums ||b||^2, ||r||^2; zero x32,
-// p, v (r and r^ are written by the first replacement, once the scale is known).
+// p, v (r and r^ are written by the first inner start, once the scale is known).
 struct MxRow {
   const RuArgs* a;
   double part[2];
@@ -79,7 +80,7 @@ struct MxRow {
   __device__ __forceinline__ void row(int32_t i, double2 ax) { put(i, bi, csub(bi, ax)); }
 };
 
-// init: r64 = b - A x (or b, x = 0); asks for the first replacement, which
+// init: r64 = b - A x (or b, x = 0); asks for the first inner start, which
 // starts the complex64 recurrence
 __global__ void __launch_bounds__(R128) k_mx_init(RuArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -118,63 +119,98 @@ __global__ void __launch_bounds__(R128) k_mx_init(RuArgs a) {
   } else if (st->maxit <= 0) {
     status = HELM_ERR_NOT_CONVERGED;
   }
-  st->method = kModeReliable;
-  st->aux[0] = make_double2(rn, 0.0);   // ||r64||, iteration of the last update
-  st->aux[1] = make_double2(1.0, 0.0);  // replacement due
+  st->method = kModeRefine;
+  st->aux[0] = make_double2(rn, 0.0);   // ||r64||, iteration of the last step
+  st->aux[1] = make_double2(1.0, 0.0);  // inner start due
   st->aux[2] = make_double2(0.0, 0.0);  // no inner scale yet
   st->status = status;
 }
 
-// update 1: x += scale * complex128(x32); x32 = 0
-__global__ void __launch_bounds__(256) k_mx_fold(RuArgs a, int always) {
+// aux[3].y = the reduction of the inner residual that ends an inner solve
+// (opts.inner_tol)
+__global__ void k_mx_configure(SolverState* st, double inner_tol) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) st->aux[3] = make_double2(0.0, inner_tol);
+}
+
+// step 1a: d64 = sigma complex128(d); d = 0
+__global__ void __launch_bounds__(256) k_mx_lift(RuArgs a, int always) {
   const SolverState* st = a.st;
   if (!always && st->aux[1].x == 0.0) return;
   const double sc = st->aux[2].x;
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.A.n; i += gridDim.x * blockDim.x) {
     const float2 d = a.x32[i];
-    double2 xi = a.x[i];
-    xi.x = fma(sc, static_cast<double>(d.x), xi.x);
-    xi.y = fma(sc, static_cast<double>(d.y), xi.y);
-    a.x[i] = xi;
+    a.d64[i] = make_double2(sc * static_cast<double>(d.x), sc * static_cast<double>(d.y));
     a.x32[i] = make_float2(0.f, 0.f);
   }
 }
 
-// update 2: r64 = b - A x (FP64), the convergence test, and the gap between
-// it and the complex64 recurrence, ||r64 - sigma r||.  A gap above
-// kRelRestart ||r64|| means the recurrence no longer tracks the residual (its
-// rounding has grown with the iterates): the Krylov process restarts from r64.
+// step 1b: w = A d64 (FP64) and gamma = (w, r64) / (w, w), the step length
+// that minimises ||r64 - gamma w||: x += gamma d64 never increases the FP64
+// residual, whatever the inner solve returned (gamma = 1 for an exact one).
+__global__ void __launch_bounds__(R128) k_mx_mr(RuArgs a, int always) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[32 * 3];
+  SolverState* st = a.st;
+  if (!always && st->aux[1].x == 0.0) return;
+  struct Epi {
+    const RuArgs* a;
+    double2 wr;
+    double ww;
+    double2 ri;
+    __device__ __forceinline__ void prefetch(int32_t i) { ri = a->r64[i]; }
+    __device__ __forceinline__ void row(int32_t i, double2 w) {
+      wr = cfma_conj(w, ri, wr);
+      ww = cabs2_acc(w, ww);
+    }
+  } epi{&a, make_double2(0.0, 0.0), 0.0, make_double2(0.0, 0.0)};
+  spmv_run<double2>(a.A, a.d64, epi, smem, a.dev_err);
+  double part[3] = {epi.wr.x, epi.wr.y, epi.ww};
+  double tot[3];
+  if (!grid_sum_last<3, 8>(part, a.partials, a.tickets + TK_AUX2, red, tot)) return;
+  if (threadIdx.x != 0) return;
+  st->spmv_count += 1;
+  double2 gamma = make_double2(0.0, 0.0);
+  if (tot[2] > 0.0 && isfinite(tot[2])) {
+    const double inv = 1.0 / tot[2];
+    gamma = make_double2(tot[0] * inv, tot[1] * inv);
+    if (!cfinite(gamma)) gamma = make_double2(0.0, 0.0);
+  }
+  st->gamma = gamma;
+}
+
+// step 1c: x += gamma d64
+__global__ void __launch_bounds__(256) k_mx_xupd(RuArgs a, int always) {
+  const SolverState* st = a.st;
+  if (!always && st->aux[1].x == 0.0) return;
+  const double2 gamma = st->gamma;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.A.n; i += gridDim.x * blockDim.x)
+    a.x[i] = cfma(gamma, a.d64[i], a.x[i]);
+}
+
+// step 2: r64 = b - A x (FP64), the convergence test
 __global__ void __launch_bounds__(R128) k_mx_residual(RuArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ double red[32 * 2];
+  __shared__ double red[32];
   SolverState* st = a.st;
   if (st->aux[1].x == 0.0) return;
   struct Epi {
     const RuArgs* a;
-    double part[2];
-    double sigma;
+    double part;
     double2 bi;
-    float2 ri32;
-    __device__ __forceinline__ void prefetch(int32_t i) {
-      bi = a->b[i];
-      ri32 = a->r32[i];
-    }
+    __device__ __forceinline__ void prefetch(int32_t i) { bi = a->b[i]; }
     __device__ __forceinline__ void row(int32_t i, double2 ax) {
       const double2 ri = csub(bi, ax);
       a->r64[i] = ri;
-      part[0] = cabs2_acc(ri, part[0]);
-      const double2 d = make_double2(fma(-sigma, static_cast<double>(ri32.x), ri.x),
-                                     fma(-sigma, static_cast<double>(ri32.y), ri.y));
-      part[1] = cabs2_acc(d, part[1]);
+      part = cabs2_acc(ri, part);
     }
-  } epi{&a, {0.0, 0.0}, st->aux[2].x, make_double2(0.0, 0.0), make_float2(0.f, 0.f)};
+  } epi{&a, 0.0, make_double2(0.0, 0.0)};
   spmv_run<double2>(a.A, a.x, epi, smem, a.dev_err);
-  double part[2] = {epi.part[0], epi.part[1]};
-  double tot[2];
-  if (!grid_sum_last<2>(part, a.partials, a.tickets + TK_AUX0, red, tot)) return;
+  double part[1] = {epi.part};
+  double tot[1];
+  if (!grid_sum_last<1>(part, a.partials, a.tickets + TK_AUX0, red, tot)) return;
   if (threadIdx.x != 0) return;
   st->spmv_count += 1;
-  st->restarts += 1;  // reliable updates performed
+  st->restarts += 1;  // refinement steps
   const double rn = sqrt(tot[0]);
   st->relres_true = rn / st->bnorm;
   if (!isfinite(rn)) st->status = HELM_ERR_NONFINITE;
@@ -182,18 +218,19 @@ __global__ void __launch_bounds__(R128) k_mx_residual(RuArgs a) {
     st->status = HELM_OK;
     st->relres = st->relres_true;
   }
+  // refinement must contract: three steps in a row without halving the
+  // residual end the solve (the inner operator, A rounded to complex64, is
+  // then too far from A for this system)
+  const double prev = st->aux[0].x * st->aux[2].x;  // ||r64|| before the step
+  st->aux[3].x = rn > 0.5 * prev ? st->aux[3].x + 1.0 : 0.0;
+  if (st->status == ST_RUNNING && st->aux[3].x >= 3.0) st->status = HELM_ERR_NOT_CONVERGED;
   st->aux[0] = make_double2(rn, static_cast<double>(st->iter));
-  st->aux[1].y = tot[1] > (kRelRestart * kRelRestart) * tot[0] ? 1.0 : 0.0;  // restart
 }
 
-// update 3: the recurrence moves to the replaced residual.  The complex64
-// vectors are kept at unit RMS entries, sigma = ||r64|| / sqrt(n): with the
-// problem's own scale (entries of b ~ h^3) the squared terms of the inner dots
-// fall below the smallest normal float long before FP64 convergence.
-//   r = complex64(r64 / sigma);  p, v *= sigma_old / sigma  (r^ = r the first
-//   time);  rho = (r^, r);  beta moved to the replaced residual.
-// Also the deadline and the loop condition of the iteration.
-__global__ void __launch_bounds__(256) k_mx_replace(RuArgs a) {
+// step 3: a fresh inner solve on r64: sigma = ||r64|| / sqrt(n),
+// r = r^ = complex64(r64 / sigma), p = v = 0, rho = (r^, r); the deadline and
+// the loop condition of the iteration.
+__global__ void __launch_bounds__(256) k_mx_restart(RuArgs a) {
   __shared__ double red[32 * 2];
   SolverState* st = a.st;
   const bool due = st->aux[1].x != 0.0;
@@ -206,30 +243,19 @@ __global__ void __launch_bounds__(256) k_mx_replace(RuArgs a) {
     return;
   }
   const int32_t n = a.A.n;
-  const double s_old = st->aux[2].x;
-  // a fresh Krylov process at the start and after a restart: r^ = r, p = v = 0
-  const bool first = s_old == 0.0 || st->aux[1].y != 0.0;
   const double s_new = st->aux[0].x / sqrt(static_cast<double>(n));
   const double inv = 1.0 / s_new;
-  const float c = first ? 0.f : static_cast<float>(s_old * inv);
   double2 rr = make_double2(0.0, 0.0);
   if (st->status == ST_RUNNING) {
+    const float2 z = make_float2(0.f, 0.f);
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
       const double2 ri = a.r64[i];
       const float2 r32 = make_float2(static_cast<float>(ri.x * inv), static_cast<float>(ri.y * inv));
       a.r32[i] = r32;
-      float2 h = r32;
-      if (first) {
-        a.rh32[i] = r32;
-        a.p32[i] = make_float2(0.f, 0.f);
-        a.v32[i] = make_float2(0.f, 0.f);
-      } else {
-        h = a.rh32[i];
-        const float2 pi = a.p32[i], vi = a.v32[i];
-        a.p32[i] = make_float2(c * pi.x, c * pi.y);
-        a.v32[i] = make_float2(c * vi.x, c * vi.y);
-      }
-      rr = cfma_conj(make_double2(h.x, h.y), make_double2(r32.x, r32.y), rr);
+      a.rh32[i] = r32;
+      a.p32[i] = z;
+      a.v32[i] = z;
+      rr = cfma_conj(make_double2(r32.x, r32.y), make_double2(r32.x, r32.y), rr);
     }
   }
   double part[2] = {rr.x, rr.y};
@@ -238,20 +264,13 @@ __global__ void __launch_bounds__(256) k_mx_replace(RuArgs a) {
   if (threadIdx.x != 0) return;
   st->aux[1] = make_double2(0.0, 0.0);
   if (st->status == ST_RUNNING) {
-    const double2 rho_true = make_double2(tot[0], tot[1]);
-    if (!cfinite(rho_true)) {
+    const double2 rho = make_double2(tot[0], tot[1]);
+    if (!cfinite(rho)) {
       st->status = HELM_ERR_NONFINITE;
-    } else if (czero(rho_true)) {
+    } else if (czero(rho)) {
       st->status = HELM_ERR_BREAKDOWN;
     } else {
-      // a fresh process's first p update gives p = r whatever beta is;
-      // otherwise, with every vector scaled by c,
-      // beta = beta rho_true / (c rho_recurrence)
-      if (!first) {
-        const double cd = static_cast<double>(c);
-        st->beta = cdiv_fast(cmul(st->beta, rho_true), make_double2(cd * st->rho.x, cd * st->rho.y));
-      }
-      st->rho = rho_true;
+      st->rho = rho;  // the first p update gives p = r whatever beta is
       st->aux[2].x = s_new;
       st->aux[0].x = st->aux[0].x * inv;  // ||r|| in the inner scale
     }
@@ -297,16 +316,21 @@ struct MxShapes {
 
 void mx_init(const RuArgs& a, const MxShapes& sh, cudaStream_t s) {
   k_mx_init<<<sh.grid128, R128, kSmem128, s>>>(a);
-  k_mx_replace<<<sh.vec_grid, 256, 0, s>>>(a);
+  k_mx_restart<<<sh.vec_grid, 256, 0, s>>>(a);
+}
+void mx_fold(const RuArgs& a, const MxShapes& sh, int always, cudaStream_t s) {
+  k_mx_lift<<<sh.vec_grid, 256, 0, s>>>(a, always);
+  k_mx_mr<<<sh.grid128, R128, kSmem128, s>>>(a, always);
+  k_mx_xupd<<<sh.vec_grid, 256, 0, s>>>(a, always);
 }
 void mx_body(const RuArgs& a, const KArgs<float2>& k, const MxShapes& sh, cudaStream_t s) {
   enqueue_body(k, sh.k, s);
-  k_mx_fold<<<sh.vec_grid, 256, 0, s>>>(a, 0);
+  mx_fold(a, sh, 0, s);
   k_mx_residual<<<sh.grid128, R128, kSmem128, s>>>(a);
-  k_mx_replace<<<sh.vec_grid, 256, 0, s>>>(a);
+  k_mx_restart<<<sh.vec_grid, 256, 0, s>>>(a);
 }
 void mx_tail(const RuArgs& a, const MxShapes& sh, cudaStream_t s) {
-  k_mx_fold<<<sh.vec_grid, 256, 0, s>>>(a, 1);
+  mx_fold(a, sh, 1, s);
   k_mx_tail<<<sh.grid128, R128, kSmem128, s>>>(a);
 }
 
@@ -320,20 +344,16 @@ helm_status solve_mixed(helm_csr A, const double2* b, double2* x, const helm_opt
   if (st == HELM_OK) st = prepare_krylov_kernels<float2>();
   if (st != HELM_OK) return st;
   for (const void* fn : {reinterpret_cast<const void*>(&k_mx_init), reinterpret_cast<const void*>(&k_mx_residual),
-                         reinterpret_cast<const void*>(&k_mx_tail)})
+                         reinterpret_cast<const void*>(&k_mx_mr), reinterpret_cast<const void*>(&k_mx_tail)})
     HELM_CUDA_TRY(set_smem_attr(fn, kSmem128));
   MxShapes sh;
   st = krylov_shapes<float2>(A, &sh.k);
   if (st != HELM_OK) return st;
-  {
-    int per_sm = 0;
-    HELM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mx_residual, R128, kSmem128));
-    per_sm = per_sm < 1 ? 1 : per_sm;
-    const int ntiles = (A->n + Engine<double2>::R - 1) / Engine<double2>::R;
-    sh.grid128 = per_sm * A->num_sms;
-    if (ntiles < sh.grid128) sh.grid128 = ntiles < 1 ? 1 : ntiles;
-    sh.vec_grid = A->vec_grid;
-  }
+  HELM_TRY(persistent_grid({reinterpret_cast<const void*>(&k_mx_init), reinterpret_cast<const void*>(&k_mx_residual),
+                            reinterpret_cast<const void*>(&k_mx_mr), reinterpret_cast<const void*>(&k_mx_tail)},
+                           R128, kSmem128, A->num_sms,
+                           (static_cast<int64_t>(A->n) + Engine<double2>::R - 1) / Engine<double2>::R, &sh.grid128));
+  sh.vec_grid = A->vec_grid;
   const int32_t n = A->n;
   const size_t N = static_cast<size_t>(n);
   float2* W = A->vec32;
@@ -360,6 +380,7 @@ helm_status solve_mixed(helm_csr A, const double2* b, double2* x, const helm_opt
   a.b = b;
   a.x = x;
   a.r64 = A->vec;
+  a.d64 = A->vec + N;
   a.x32 = k.x;
   a.r32 = k.r;
   a.rh32 = k.rh;
@@ -402,6 +423,7 @@ helm_status solve_mixed(helm_csr A, const double2* b, double2* x, const helm_opt
   // an explicit graph request does not fall back to the host-driven loop
   if (!g && o.launch == HELM_LAUNCH_GRAPH) return HELM_ERR_CUDA;
   k_configure<<<1, 1, 0, s>>>(A->state, o.tol, o.maxit, o.use_x0 ? 1 : 0, o.deadline_s, 1);
+  k_mx_configure<<<1, 1, 0, s>>>(A->state, o.inner_tol);
   HELM_CUDA_TRY(cudaGetLastError());
   SolverState* hs = A->state_host;
   if (g) {

@@ -132,9 +132,19 @@ __device__ __forceinline__ float2 mac_staged(float2 a, float2 x, float2 acc) { r
 // staged tile, each with a shorter dependent chain); the SPLIT partial sums
 // of a row are added in a fixed order through shared memory, and only the
 // threads t < R call epi.row.
-template <class V, int R, int CAP, class Epi, int STAGES = 2, int SPLIT = 1>
+// gate(): called by every thread once, after the block's first tile copy is
+// issued and before anything else is read (a kernel's wait for its
+// predecessor goes there, so the matrix copy overlaps the predecessor's
+// tail).  It must return the same value in every thread of the block; on
+// false the engine lets the copy land and returns without touching x or
+// calling the epilogue.
+struct NoGate {
+  __device__ __forceinline__ bool operator()() const { return true; }
+};
+
+template <class V, int R, int CAP, class Epi, int STAGES = 2, int SPLIT = 1, class Gate = NoGate>
 __device__ __forceinline__ bool spmv_tiles(const CsrDev<V>& A, const V* __restrict__ x, Epi& epi,
-                                           unsigned char* smem, unsigned int* dev_err) {
+                                           unsigned char* smem, unsigned int* dev_err, Gate gate = Gate()) {
   using S = SpmvStage<V, CAP, STAGES>;
   using T = typename S::T;
   constexpr bool kC128 = std::is_same<V, double2>::value;
@@ -202,7 +212,11 @@ __device__ __forceinline__ bool spmv_tiles(const CsrDev<V>& A, const V* __restri
   int fail_it = 0;
   bool fail_next = false;
   int32_t tile = blockIdx.x;
-  if (STAGES == 2 && threadIdx.x == 0 && tile < ntiles) issue(tile, 0);
+  if (threadIdx.x == 0 && tile < ntiles) issue(tile, 0);  // the first copy
+  if (!gate()) {
+    if (tile < ntiles) (void)mbar_wait_bounded(&bar[0], 0, 100000000ull);
+    return true;
+  }
   for (int it = 0; tile < ntiles; tile += gridDim.x, ++it) {
     const int b = STAGES == 2 ? (it & 1) : 0;
     const int32_t next = tile + gridDim.x;
@@ -212,7 +226,7 @@ __device__ __forceinline__ bool spmv_tiles(const CsrDev<V>& A, const V* __restri
           fence_proxy_async();  // buffer b^1 was last read through the generic proxy
           issue(next, b ^ 1);
         }
-      } else {
+      } else if (it > 0) {
         fence_proxy_async();  // the single buffer was last read through the generic proxy
         issue(tile, 0);
       }
@@ -357,10 +371,11 @@ template <> struct Engine<float2> {
   static constexpr int kThreads = R * SPLIT;
   static constexpr size_t kSmem = SpmvStage<float2, CAP, kStages>::kBytes;
 };
-template <class V, class Epi>
+template <class V, class Epi, class Gate = NoGate>
 __device__ __forceinline__ bool spmv_run(const CsrDev<V>& A, const V* __restrict__ x, Epi& epi, unsigned char* smem,
-                                         unsigned int* dev_err) {
-  return spmv_tiles<V, Engine<V>::R, Engine<V>::CAP, Epi, kStages, Engine<V>::SPLIT>(A, x, epi, smem, dev_err);
+                                         unsigned int* dev_err, Gate gate = Gate()) {
+  return spmv_tiles<V, Engine<V>::R, Engine<V>::CAP, Epi, kStages, Engine<V>::SPLIT, Gate>(A, x, epi, smem, dev_err,
+                                                                                           gate);
 }
 
 }  // namespace helm

@@ -654,16 +654,33 @@ SweepShape sweep_shape(helm_sweep S, int G) {
   sh.threads = 32 * S->warps_per_block;
   // each warp keeps one group: the number of warps must be a multiple of G
   const int warps_per_block = S->warps_per_block;
-  // 1024 resident threads per SM: enough warps to hide latency, few block
-  // partials for the per-frequency reductions
-  int64_t blocks = static_cast<int64_t>(S->num_sms) * std::max(1, 1024 / sh.threads);
+  sh.smem = static_cast<size_t>(warps_per_block) * 32 * 4 * sizeof(double);
+  // up to 1024 resident threads per SM (enough warps to hide latency, few
+  // block partials for the per-frequency reductions), and no more blocks
+  // than every sweep kernel fits on an SM at once: one wave
+  int per_sm = std::max(1, 1024 / sh.threads);
+  for (const void* fn : {reinterpret_cast<const void*>(&k_sw_init), reinterpret_cast<const void*>(&k_sw_p),
+                         reinterpret_cast<const void*>(&k_sw_v), reinterpret_cast<const void*>(&k_sw_s),
+                         reinterpret_cast<const void*>(&k_sw_t), reinterpret_cast<const void*>(&k_sw_xr),
+                         reinterpret_cast<const void*>(&k_sw_tail)}) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, sh.threads, sh.smem) == cudaSuccess && b >= 1)
+      per_sm = std::min(per_sm, b);
+  }
+  (void)cudaGetLastError();
+  int64_t blocks = static_cast<int64_t>(S->num_sms) * per_sm;
   int64_t units = static_cast<int64_t>(S->n) * G;
   int64_t want = (units + warps_per_block - 1) / warps_per_block;
   if (want < blocks) blocks = want < 1 ? 1 : want;
   // warps in the grid = blocks * warps_per_block: make it a multiple of G
-  while ((blocks * warps_per_block) % G != 0) ++blocks;
+  // (rounding down keeps one wave; up only when that leaves no block)
+  const int64_t b0 = blocks;
+  while (blocks > 1 && (blocks * warps_per_block) % G != 0) --blocks;
+  if ((blocks * warps_per_block) % G != 0) {
+    blocks = b0;
+    while ((blocks * warps_per_block) % G != 0) ++blocks;
+  }
   sh.grid = static_cast<int>(blocks);
-  sh.smem = static_cast<size_t>(warps_per_block) * 32 * 4 * sizeof(double);
   return sh;
 }
 

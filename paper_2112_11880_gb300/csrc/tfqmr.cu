@@ -416,15 +416,12 @@ helm_status tfqmr_fp64(helm_csr A, const double2* b, double2* x, const helm_opts
                          reinterpret_cast<const void*>(&k_tq_check), reinterpret_cast<const void*>(&k_tq_tail)})
     HELM_CUDA_TRY(set_smem_attr(fn, kSmem));
   TqShapes sh;
-  {
-    int per_sm = 0;
-    HELM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tq_spmv_u, RT, kSmem));
-    per_sm = per_sm < 1 ? 1 : per_sm;
-    const int ntiles = (A->n + Engine<V>::R - 1) / Engine<V>::R;
-    sh.spmv_grid = per_sm * A->num_sms;
-    if (ntiles < sh.spmv_grid) sh.spmv_grid = ntiles < 1 ? 1 : ntiles;
-    sh.vec_grid = A->vec_grid;
-  }
+  HELM_TRY(persistent_grid({reinterpret_cast<const void*>(&k_tq_init_a), reinterpret_cast<const void*>(&k_tq_init_b),
+                            reinterpret_cast<const void*>(&k_tq_spmv_un), reinterpret_cast<const void*>(&k_tq_spmv_u),
+                            reinterpret_cast<const void*>(&k_tq_check), reinterpret_cast<const void*>(&k_tq_tail)},
+                           RT, kSmem, A->num_sms, (static_cast<int64_t>(A->n) + Engine<V>::R - 1) / Engine<V>::R,
+                           &sh.spmv_grid));
+  sh.vec_grid = A->vec_grid;
   const size_t N = static_cast<size_t>(A->n);
   double2* W = A->vec;
   TqArgs a;
