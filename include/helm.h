@@ -182,6 +182,20 @@ typedef enum {
                                  that cannot see inside conditional graphs) */
 } helm_launch;
 
+/* Preconditioner.  Section 4 names its solvers P-BiCGSTAB, P-TFQMR and
+ * P-BiCGSTAB(l) without saying which preconditioner they use. */
+typedef enum {
+  HELM_PRECOND_NONE = 0,
+  HELM_PRECOND_JACOBI = 1 /* right Jacobi: the method runs on A D^-1 y = b,
+                             D = diag(A) (a row without a stored nonzero
+                             diagonal takes 1), and x = D^-1 y at the end.
+                             The scaled matrix is a handle-owned copy made at
+                             the first such solve (20 bytes per entry).  The
+                             residual reported and tested is that of A x = b
+                             itself.  FP64 only (HELM_ERR_INVALID with
+                             HELM_PREC_MIXED) */
+} helm_precond;
+
 typedef struct {
   double tol;          /* target ||b - A x|| / ||b|| (Section 4 uses 1e-9) */
   int32_t maxit;       /* iteration cap (Section 4 uses 1000); each BiCGStab
@@ -191,11 +205,12 @@ typedef struct {
   int32_t precision;   /* helm_precision */
   double inner_tol;    /* mixed precision: an inner solve ends when its
                           residual has dropped by this factor (0 or >= 1:
-                          only when it looks below tol), or after 20000
+                          only when it looks below tol), or after 50000
                           iterations */
   double deadline_s;   /* device wall-clock limit of one solve; <= 0: none */
   int32_t ell;         /* l of BiCGStab(l), 1..8 */
   int32_t launch;      /* helm_launch */
+  int32_t precond;     /* helm_precond */
 } helm_opts;
 
 typedef struct {
@@ -210,7 +225,7 @@ typedef struct {
 } helm_info;
 
 /* Defaults: tol 1e-8, maxit 20000, use_x0 0, BiCGStab, FP64, inner_tol 1e-3,
- * no deadline, ell 2, launch auto. */
+ * no deadline, ell 2, launch auto, no preconditioner. */
 void helm_opts_default(helm_opts* o);
 
 /*

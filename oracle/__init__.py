@@ -141,6 +141,35 @@ def _krylov(fname, rowptr, colind, vals, b, tol, maxit, x0, ell=None):
 # numpy-level definitions
 # ---------------------------------------------------------------------------
 
+def jacobi_scale(rowptr, colind, vals):
+    """Right Jacobi preconditioning written out (the paper's P- solvers, Section 4,
+    with the diagonal as the preconditioner): D = diag(A), a row without a stored
+    nonzero diagonal taking 1; returns (values of A D^-1, d, 1/d).  Solving
+    (A D^-1) y = b and setting x = D^-1 y solves A x = b."""
+    rowptr = np.asarray(rowptr)
+    colind = np.asarray(colind)
+    vals = np.asarray(vals, dtype=np.complex128)
+    n = len(rowptr) - 1
+    d = np.ones(n, dtype=np.complex128)
+    for i in range(n):
+        for k in range(rowptr[i], rowptr[i + 1]):
+            if colind[k] == i:
+                if vals[k] != 0 and np.isfinite(vals[k]):
+                    d[i] = vals[k]
+                break
+    dinv = 1.0 / d
+    return vals * dinv[colind], d, dinv
+
+
+def jacobi_solve(method, rowptr, colind, vals, b, **kw):
+    """x = D^-1 y with y from `method` (bicgstab, tfqmr, bicgstabl) on A D^-1."""
+    vs, d, dinv = jacobi_scale(rowptr, colind, vals)
+    x0 = kw.pop("x0", None)
+    y0 = None if x0 is None else d * np.asarray(x0, dtype=np.complex128)
+    y, info = method(rowptr, colind, vs, b, x0=y0, **kw)
+    return dinv * y, info
+
+
 def helmholtz_values(K, Mc, Bc, w: float) -> np.ndarray:
     """A(w) = K - w^2 M_c + i w B_c entry by entry (the frequency-dependent
     system of the Helmholtz problem of Section 1 with the impedance term)."""

@@ -43,12 +43,15 @@ HELM_LAUNCH_AUTO = 0
 HELM_LAUNCH_GRAPH = 1
 HELM_LAUNCH_PERSISTENT = 2
 HELM_LAUNCH_HOST = 3
+HELM_PRECOND_NONE = 0
+HELM_PRECOND_JACOBI = 1
 
 
 class helm_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int32), ("use_x0", ctypes.c_int32),
                 ("method", ctypes.c_int32), ("precision", ctypes.c_int32), ("inner_tol", ctypes.c_double),
-                ("deadline_s", ctypes.c_double), ("ell", ctypes.c_int32), ("launch", ctypes.c_int32)]
+                ("deadline_s", ctypes.c_double), ("ell", ctypes.c_int32), ("launch", ctypes.c_int32),
+                ("precond", ctypes.c_int32)]
 
 
 class helm_info(ctypes.Structure):

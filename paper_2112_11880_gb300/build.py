@@ -39,20 +39,34 @@ def _deps():
         + glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB) or os.environ.get("HELM_NVCC_EXTRA"):
+STAMP = os.path.join(OUT_DIR, "build_flags.txt")
+
+
+def _extra_flags(extra_flags=None):
+    return list(extra_flags or []) + os.environ.get("HELM_NVCC_EXTRA", "").split()
+
+
+def up_to_date(extra_flags=None) -> bool:
+    """The library exists, is newer than every source, and was built with the
+    same extra flags (a build with experiment flags is never reused by a
+    default build, nor the other way round)."""
+    if not os.path.exists(LIB) or not os.path.exists(STAMP):
         return False
+    with open(STAMP) as f:
+        if f.read() != " ".join(_extra_flags(extra_flags)):
+            return False
     t = os.path.getmtime(LIB)
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
-    if not force and up_to_date():
+    if not force and up_to_date(extra_flags):
         return LIB
     os.makedirs(os.path.join(OUT_DIR, "obj"), exist_ok=True)
     cc = nvcc()
     # HELM_NVCC_EXTRA: extra nvcc flags (engine-shape experiments, e.g. -DHELM_SPLIT=2)
-    flags = FLAGS + list(extra_flags or []) + os.environ.get("HELM_NVCC_EXTRA", "").split()
+    extra = _extra_flags(extra_flags)
+    flags = FLAGS + extra
 
     def compile_one(src):
         obj = os.path.join(OUT_DIR, "obj", os.path.basename(src) + ".o")
@@ -72,6 +86,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as f:
+        f.write(" ".join(extra))
     return LIB
 
 

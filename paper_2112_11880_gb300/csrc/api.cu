@@ -47,7 +47,8 @@ __global__ void __launch_bounds__(Engine<V>::kThreads) k_spmv(CsrDev<V> A, const
 }
 
 // real_blk[b] = 1 when every entry of rows [32 b, 32 b + 32) is real.
-__global__ void k_real_blocks(int32_t n, const int32_t* __restrict__ rowptr, const double2* __restrict__ vals,
+template <class V>
+__global__ void k_real_blocks(int32_t n, const int32_t* __restrict__ rowptr, const V* __restrict__ vals,
                               uint8_t* __restrict__ real_blk) {
   const int32_t nblk = (n + 31) / 32;
   for (int32_t blk = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); blk < nblk;
@@ -56,17 +57,49 @@ __global__ void k_real_blocks(int32_t n, const int32_t* __restrict__ rowptr, con
     const int64_t k0 = rowptr[r0], k1 = rowptr[r1];
     bool real = true;
     for (int64_t k = k0 + (threadIdx.x & 31); k < k1; k += 32)
-      if (reinterpret_cast<const double*>(vals)[2 * k + 1] != 0.0) real = false;
+      if (vals[k].y != 0) real = false;
     real = __all_sync(0xffffffffu, real);
     if ((threadIdx.x & 31) == 0) real_blk[blk] = real ? 1 : 0;
   }
 }
 
 // vals_re[k] = Re vals[k]
-__global__ void k_real_parts(int64_t nnz, const double2* __restrict__ vals, double* __restrict__ vals_re) {
+template <class V, class R>
+__global__ void k_real_parts(int64_t nnz, const V* __restrict__ vals, R* __restrict__ vals_re) {
   for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < nnz;
        k += static_cast<int64_t>(gridDim.x) * blockDim.x)
     vals_re[k] = vals[k].x;
+}
+
+// Right Jacobi: d_i = a_ii (1 when row i stores no nonzero diagonal),
+// dinv_i = 1 / d_i.
+__global__ void k_jac_diag(int32_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+                           const double2* __restrict__ vals, double2* __restrict__ d, double2* __restrict__ dinv) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double2 di = make_double2(1.0, 0.0);
+    for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+      if (colind[k] == i) {
+        if (!czero(vals[k]) && cfinite(vals[k])) di = vals[k];
+        break;
+      }
+    }
+    d[i] = di;
+    dinv[i] = cdiv(make_double2(1.0, 0.0), di);
+  }
+}
+// A D^-1: entry k of row i is a_ik dinv_colind[k]
+__global__ void k_jac_scale(int64_t nnz, const int32_t* __restrict__ colind, const double2* __restrict__ vals,
+                            const double2* __restrict__ dinv, double2* __restrict__ out, double* __restrict__ out_re) {
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < nnz;
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const double2 v = cmul(vals[k], dinv[colind[k]]);
+    out[k] = v;
+    out_re[k] = v.x;
+  }
+}
+// x_i <- s_i x_i
+__global__ void k_jac_apply(int32_t n, const double2* __restrict__ sc, double2* __restrict__ x) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = cmul(sc[i], x[i]);
 }
 
 // Per-row statistics and (optionally) validation of the CSR pattern.
@@ -251,7 +284,7 @@ helm_status launch_spmv64(helm_csr A, const float2* vals, const float2* x, float
   const int mode = (alpha.x == 1.f && alpha.y == 0.f && beta.x == 0.f && beta.y == 0.f) ? 0
                    : (beta.x == 0.f && beta.y == 0.f)                                    ? 1
                                                                                          : 2;
-  CsrDev<float2> d{A->n, A->nnz, A->rowptr, A->colind, vals, nullptr, nullptr};
+  CsrDev<float2> d{A->n, A->nnz, A->rowptr, A->colind, vals, A->real_blk, A->vals32_re};
   k_spmv<float2><<<grid, Engine<float2>::kThreads, Engine<float2>::kSmem, s>>>(d, x, y, alpha, beta, mode, A->dev_err);
   HELM_CUDA_TRY(cudaGetLastError());
   return HELM_OK;
@@ -296,9 +329,12 @@ helm_status ensure_vectors32(helm_csr A, int nvec) {
 
 helm_status ensure_vals32(helm_csr A, cudaStream_t s) {
   if (A->vals32) return HELM_OK;
-  HELM_CUDA_TRY(cudaMalloc(&A->vals32, sizeof(float2) * static_cast<size_t>(std::max<int64_t>(A->nnz, 1))));
+  const size_t NNZ = static_cast<size_t>(std::max<int64_t>(A->nnz, 1));
+  HELM_CUDA_TRY(cudaMalloc(&A->vals32_re, sizeof(float) * NNZ));
+  HELM_CUDA_TRY(cudaMalloc(&A->vals32, sizeof(float2) * NNZ));
   if (A->nnz) {
     k_c128_to_c64<<<vec_grid_for(A->nnz), 256, 0, s>>>(A->nnz, static_cast<const double2*>(A->vals), A->vals32);
+    k_real_parts<<<vec_grid_for(A->nnz), 256, 0, s>>>(A->nnz, static_cast<const float2*>(A->vals32), A->vals32_re);
     HELM_CUDA_TRY(cudaGetLastError());
   }
   return HELM_OK;
@@ -309,6 +345,39 @@ helm_status ensure_vals32(helm_csr A, cudaStream_t s) {
 using namespace helm;
 
 // ---------------------------------------------------------------- C ABI
+
+namespace helm {
+helm_status ensure_jacobi(helm_csr A, cudaStream_t s) {
+  if (A->jac_vals) return HELM_OK;
+  const int32_t n = A->n;
+  const size_t N = static_cast<size_t>(n > 0 ? n : 1), NNZ = static_cast<size_t>(A->nnz > 0 ? A->nnz : 1);
+  HELM_CUDA_TRY(cudaMalloc(&A->jac_d, N * sizeof(double2)));
+  HELM_CUDA_TRY(cudaMalloc(&A->jac_dinv, N * sizeof(double2)));
+  HELM_CUDA_TRY(cudaMalloc(&A->jac_real_blk, (N + 31) / 32));
+  HELM_CUDA_TRY(cudaMalloc(&A->jac_vals_re, NNZ * sizeof(double)));
+  HELM_CUDA_TRY(cudaMalloc(&A->jac_vals, NNZ * sizeof(double2)));
+  const double2* vals = static_cast<const double2*>(A->vals);
+  k_jac_diag<<<vec_grid_for(n), 256, 0, s>>>(n, A->rowptr, A->colind, vals, A->jac_d, A->jac_dinv);
+  k_jac_scale<<<vec_grid_for(A->nnz), 256, 0, s>>>(A->nnz, A->colind, vals, A->jac_dinv, A->jac_vals, A->jac_vals_re);
+  if (n > 0) k_real_blocks<<<vec_grid_for(n / 32 + 1), 256, 0, s>>>(n, A->rowptr, static_cast<const double2*>(A->jac_vals), A->jac_real_blk);
+  HELM_CUDA_TRY(cudaGetLastError());
+  return HELM_OK;
+}
+}  // namespace helm
+
+static helm_status solve_dispatch(helm_csr A, const double2* b, double2* x, const helm_opts& opts, helm_info* info,
+                                  cudaStream_t s) {
+  if (opts.precision == HELM_PREC_MIXED) {
+    if (opts.method != HELM_BICGSTAB) return HELM_ERR_INVALID;
+    return solve_mixed(A, b, x, opts, info, s);
+  }
+  if (opts.precision != HELM_PREC_FP64) return HELM_ERR_INVALID;
+  if (opts.method == HELM_TFQMR) return tfqmr_fp64(A, b, x, opts, info, s);
+  if (opts.method == HELM_BICGSTABL) return bicgstabl_fp64(A, b, x, opts, info, s);
+  if (opts.method != HELM_BICGSTAB) return HELM_ERR_INVALID;
+  return bicgstab_fp64(A, b, x, opts, info, s);
+}
+
 
 extern "C" {
 
@@ -338,6 +407,7 @@ void helm_opts_default(helm_opts* o) {
   o->deadline_s = 0.0;
   o->ell = 2;
   o->launch = HELM_LAUNCH_AUTO;
+  o->precond = HELM_PRECOND_NONE;
 }
 
 helm_status helm_csr_create(helm_csr* out, int32_t n, int64_t nnz, const int32_t* d_rowptr,
@@ -406,16 +476,25 @@ helm_status helm_csr_create(helm_csr* out, int32_t n, int64_t nnz, const int32_t
   A->vec_grid = vec_grid_for(n);
   helm_status st = dt == HELM_C128 ? spmv_grid<double2>(n, &A->spmv_grid) : spmv_grid<float2>(n, &A->spmv_grid);
   if (st != HELM_OK) return fail(st);
-  if (dt == HELM_C128 && n > 0) {
-    // rows blocks with only real entries take the cheaper product
+  if (n > 0) {
+    // row blocks with only real entries take the cheaper product, staged
+    // from their real parts (8 or 4 bytes per entry)
     if (cudaMalloc(&A->real_blk, (n + 31) / 32) != cudaSuccess) return fail(HELM_ERR_NOMEM);
-    k_real_blocks<<<vec_grid_for(n / 32 + 1), 256, 0, s>>>(n, d_rowptr, static_cast<const double2*>(d_vals), A->real_blk);
+    if (dt == HELM_C128)
+      k_real_blocks<<<vec_grid_for(n / 32 + 1), 256, 0, s>>>(n, d_rowptr, static_cast<const double2*>(d_vals), A->real_blk);
+    else
+      k_real_blocks<<<vec_grid_for(n / 32 + 1), 256, 0, s>>>(n, d_rowptr, static_cast<const float2*>(d_vals), A->real_blk);
     if (cudaGetLastError() != cudaSuccess) return fail(HELM_ERR_CUDA);
-    // the SpMV stages real blocks from their real parts (8 bytes per entry)
     if (nnz > 0) {
-      if (cudaMalloc(&A->vals_re, static_cast<size_t>(nnz) * sizeof(double)) != cudaSuccess)
-        return fail(HELM_ERR_NOMEM);
-      k_real_parts<<<vec_grid_for(nnz), 256, 0, s>>>(nnz, static_cast<const double2*>(d_vals), A->vals_re);
+      if (dt == HELM_C128) {
+        if (cudaMalloc(&A->vals_re, static_cast<size_t>(nnz) * sizeof(double)) != cudaSuccess)
+          return fail(HELM_ERR_NOMEM);
+        k_real_parts<<<vec_grid_for(nnz), 256, 0, s>>>(nnz, static_cast<const double2*>(d_vals), A->vals_re);
+      } else {
+        if (cudaMalloc(&A->vals32_re, static_cast<size_t>(nnz) * sizeof(float)) != cudaSuccess)
+          return fail(HELM_ERR_NOMEM);
+        k_real_parts<<<vec_grid_for(nnz), 256, 0, s>>>(nnz, static_cast<const float2*>(d_vals), A->vals32_re);
+      }
       if (cudaGetLastError() != cudaSuccess) return fail(HELM_ERR_CUDA);
     }
   }
@@ -441,6 +520,12 @@ helm_status helm_csr_destroy(helm_csr A) {
   cudaFree(A->vals32);
   cudaFree(A->real_blk);
   cudaFree(A->vals_re);
+  cudaFree(A->vals32_re);
+  cudaFree(A->jac_vals);
+  cudaFree(A->jac_vals_re);
+  cudaFree(A->jac_real_blk);
+  cudaFree(A->jac_d);
+  cudaFree(A->jac_dinv);
   cudaFree(A->vec32);
   (void)cudaGetLastError();
   if (prev >= 0) cudaSetDevice(prev);
@@ -545,18 +630,24 @@ helm_status helm_bicgstab_solve(helm_csr A, const void* d_b, void* d_x, const he
   if (!aligned(d_b, 16) || !aligned(d_x, 16) || d_b == d_x) return HELM_ERR_INVALID;
   if (!(opts.tol >= 0.0) || opts.maxit < 0) return HELM_ERR_INVALID;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (opts.precond != HELM_PRECOND_NONE && opts.precond != HELM_PRECOND_JACOBI) return HELM_ERR_INVALID;
+  if (opts.precond == HELM_PRECOND_JACOBI && opts.precision != HELM_PREC_FP64) return HELM_ERR_INVALID;
   std::lock_guard<std::mutex> lk(A->mu);
-  if (opts.precision == HELM_PREC_MIXED) {
-    if (opts.method != HELM_BICGSTAB) return HELM_ERR_INVALID;
-    return solve_mixed(A, static_cast<const double2*>(d_b), static_cast<double2*>(d_x), opts, info, s);
+  const double2* b = static_cast<const double2*>(d_b);
+  double2* x = static_cast<double2*>(d_x);
+  if (opts.precond != HELM_PRECOND_JACOBI) return solve_dispatch(A, b, x, opts, info, s);
+  // right Jacobi: solve (A D^-1) y = b with y0 = D x0, then x = D^-1 y
+  helm_status st = ensure_jacobi(A, s);
+  if (st != HELM_OK) return st;
+  if (opts.use_x0 && A->n > 0) k_jac_apply<<<vec_grid_for(A->n), 256, 0, s>>>(A->n, A->jac_d, x);
+  HELM_CUDA_TRY(cudaGetLastError());
+  st = solve_dispatch(A, b, x, opts, info, s);
+  if (A->n > 0) {
+    k_jac_apply<<<vec_grid_for(A->n), 256, 0, s>>>(A->n, A->jac_dinv, x);
+    if (cudaGetLastError() != cudaSuccess && st == HELM_OK) st = HELM_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess && st == HELM_OK) st = HELM_ERR_CUDA;
   }
-  if (opts.precision != HELM_PREC_FP64) return HELM_ERR_INVALID;
-  if (opts.method == HELM_TFQMR)
-    return tfqmr_fp64(A, static_cast<const double2*>(d_b), static_cast<double2*>(d_x), opts, info, s);
-  if (opts.method == HELM_BICGSTABL)
-    return bicgstabl_fp64(A, static_cast<const double2*>(d_b), static_cast<double2*>(d_x), opts, info, s);
-  if (opts.method != HELM_BICGSTAB) return HELM_ERR_INVALID;
-  return bicgstab_fp64(A, static_cast<const double2*>(d_b), static_cast<double2*>(d_x), opts, info, s);
+  return st;
 }
 
 }  // extern "C"

@@ -97,7 +97,7 @@ helm_status bicgstab_fp64(helm_csr A, const double2* b, double2* x, const helm_o
   double2* W = A->vec;
   KArgs<V> a;
   std::memset(&a, 0, sizeof(a));
-  a.A = CsrDev<V>{n, A->nnz, A->rowptr, A->colind, static_cast<const V*>(A->vals), A->real_blk, A->vals_re};
+  a.A = csr_for(A, o);
   a.b = b;
   a.x = x;
   a.r = W;
@@ -117,7 +117,7 @@ helm_status bicgstab_fp64(helm_csr A, const double2* b, double2* x, const helm_o
   // Graph for this (b, x), built once and reused.
   GraphEntry* g = nullptr;
   const bool use_graph = o.launch != HELM_LAUNCH_HOST;
-  auto key = std::make_pair(static_cast<const void*>(b), static_cast<const void*>(x));
+  auto key = graph_key(b, x, 0, o);
   auto it = A->graphs.find(key);
   if (!use_graph) {
   } else if (it != A->graphs.end()) {

@@ -471,7 +471,7 @@ helm_status bicgstabl_fp64(helm_csr A, const double2* b, double2* x, const helm_
   double2* W = A->vec;
   BlArgs a;
   std::memset(&a, 0, sizeof(a));
-  a.A = CsrDev<V>{A->n, A->nnz, A->rowptr, A->colind, static_cast<const V*>(A->vals), A->real_blk, A->vals_re};
+  a.A = csr_for(A, o);
   a.b = b;
   a.x = x;
   a.rt = W;
@@ -486,8 +486,7 @@ helm_status bicgstabl_fp64(helm_csr A, const double2* b, double2* x, const helm_
   a.dev_err = A->dev_err;
 
   GraphEntry* g = nullptr;
-  auto key = std::make_pair(static_cast<const void*>(reinterpret_cast<const char*>(b) + 4 + ell),
-                            static_cast<const void*>(x));
+  auto key = graph_key(b, x, 4 + ell, o);
   auto it = A->graphs.find(key);
   if (o.launch == HELM_LAUNCH_HOST) {
   } else if (it != A->graphs.end()) {

@@ -41,7 +41,10 @@ constexpr int kRows128 = 32;
 constexpr int kCap128 = kRows128 * 28;
 constexpr int kRows64 = 32;
 constexpr int kCap64 = kRows64 * 28;
-constexpr int kStages = 1;
+#ifndef HELM_STAGES
+#define HELM_STAGES 1
+#endif
+constexpr int kStages = HELM_STAGES;
 #ifndef HELM_SPLIT
 #define HELM_SPLIT 2
 #endif
@@ -83,6 +86,14 @@ struct helm_csr_s {
   float2* vals32 = nullptr;            // complex64 copy for mixed precision
   uint8_t* real_blk = nullptr;         // per 32-row block: all entries real
   double* vals_re = nullptr;           // real parts of the complex128 values
+  float* vals32_re = nullptr;          // real parts of the complex64 values (own or vals32)
+  // right Jacobi (built at the first preconditioned solve): A D^-1 as
+  // values, real parts and real-block flags; D and D^-1
+  double2* jac_vals = nullptr;
+  double* jac_vals_re = nullptr;
+  uint8_t* jac_real_blk = nullptr;
+  double2* jac_d = nullptr;
+  double2* jac_dinv = nullptr;
   float2* vec32 = nullptr;             // complex64 Krylov vectors
   int nvec32 = 0;
 
@@ -126,6 +137,15 @@ helm_status launch_spmv64(helm_csr A, const float2* vals, const float2* x, float
                           float2 beta, cudaStream_t s);
 
 // Solver entry points implemented in the solver translation units.
+// Graph-cache key of a solve: (b, x) tagged with the method and the
+// preconditioner, so that each variant keeps its own graph.
+inline std::pair<const void*, const void*> graph_key(const void* b, const void* x, int tag, const helm_opts& o) {
+  return std::make_pair(static_cast<const void*>(static_cast<const char*>(b) + tag +
+                                                 (o.precond == HELM_PRECOND_JACOBI ? 16 : 0)),
+                        x);
+}
+
+helm_status ensure_jacobi(helm_csr A, cudaStream_t s);
 helm_status bicgstab_fp64(helm_csr A, const double2* b, double2* x, const helm_opts& o, helm_info* info,
                           cudaStream_t s);
 helm_status tfqmr_fp64(helm_csr A, const double2* b, double2* x, const helm_opts& o, helm_info* info,

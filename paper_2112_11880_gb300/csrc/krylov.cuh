@@ -33,6 +33,14 @@
 
 namespace helm {
 
+// The complex128 matrix a solve runs on: A, or A D^-1 under right Jacobi.
+inline CsrDev<double2> csr_for(helm_csr A, const helm_opts& o) {
+  if (o.precond == HELM_PRECOND_JACOBI)
+    return CsrDev<double2>{A->n, A->nnz, A->rowptr, A->colind, A->jac_vals, A->jac_real_blk, A->jac_vals_re};
+  return CsrDev<double2>{A->n, A->nnz, A->rowptr, A->colind, static_cast<const double2*>(A->vals), A->real_blk,
+                         A->vals_re};
+}
+
 // SolverState::method of the Krylov loop: plain, or the inner loop of the
 // mixed-precision solve (aux[0] = (||r|| when the process began, in its
 // scale; iteration it began), aux[1].x = refinement step due, aux[2].x =
@@ -40,7 +48,7 @@ namespace helm {
 // inner_tol)).
 constexpr int32_t kModePlain = 0;
 constexpr int32_t kModeRefine = 1;
-constexpr int kInnerMax = 20000;  // inner iterations per refinement step at most
+constexpr int kInnerMax = 50000;  // inner iterations per refinement step at most
 
 template <class V> struct Prec;
 template <> struct Prec<double2> {

@@ -218,12 +218,12 @@ __global__ void __launch_bounds__(R128) k_mx_residual(RuArgs a) {
     st->status = HELM_OK;
     st->relres = st->relres_true;
   }
-  // refinement must contract: three steps in a row without halving the
+  // refinement must contract: five steps in a row without halving the
   // residual end the solve (the inner operator, A rounded to complex64, is
   // then too far from A for this system)
   const double prev = st->aux[0].x * st->aux[2].x;  // ||r64|| before the step
   st->aux[3].x = rn > 0.5 * prev ? st->aux[3].x + 1.0 : 0.0;
-  if (st->status == ST_RUNNING && st->aux[3].x >= 3.0) st->status = HELM_ERR_NOT_CONVERGED;
+  if (st->status == ST_RUNNING && st->aux[3].x >= 5.0) st->status = HELM_ERR_NOT_CONVERGED;
   st->aux[0] = make_double2(rn, static_cast<double>(st->iter));
 }
 
@@ -360,7 +360,7 @@ helm_status solve_mixed(helm_csr A, const double2* b, double2* x, const helm_opt
 
   KArgs<float2> k;
   std::memset(&k, 0, sizeof(k));
-  k.A = CsrDev<float2>{n, A->nnz, A->rowptr, A->colind, A->vals32, nullptr, nullptr};
+  k.A = CsrDev<float2>{n, A->nnz, A->rowptr, A->colind, A->vals32, A->real_blk, A->vals32_re};
   k.r = W;
   k.rh = W + N;
   k.p = W + 2 * N;
@@ -393,8 +393,7 @@ helm_status solve_mixed(helm_csr A, const double2* b, double2* x, const helm_opt
 
   // graph per (b, x), tagged as mixed in the cache key
   GraphEntry* g = nullptr;
-  auto key = std::make_pair(static_cast<const void*>(reinterpret_cast<const char*>(b) + 2),
-                            static_cast<const void*>(x));
+  auto key = graph_key(b, x, 2, o);
   auto it = A->graphs.find(key);
   if (o.launch == HELM_LAUNCH_HOST) {
   } else if (it != A->graphs.end()) {

@@ -44,6 +44,11 @@ namespace helm {
 
 constexpr int kSpmvUnroll = HELM_SPMV_UNROLL;
 
+// Real type of a complex type.
+template <class V> struct RealOf;
+template <> struct RealOf<double2> { using T = double; };
+template <> struct RealOf<float2> { using T = float; };
+
 template <class V>
 struct CsrDev {
   int32_t n;
@@ -51,16 +56,17 @@ struct CsrDev {
   const int32_t* rowptr;
   const int32_t* colind;
   const V* vals;
-  // Optional (complex128 only): real_blk[r >> 5] != 0 when every stored
+  // Optional: real_blk[r >> 5] != 0 when every stored
   // entry of rows [32 (r >> 5), 32 (r >> 5) + 32) has a zero imaginary part.
   // Those rows take the real x complex product (2 FMA per entry instead of
   // 4); for finite x the result is bit-identical to the complex product,
   // since the skipped terms are exact zeros.  Helmholtz FEM rows away from
   // the impedance boundary are of this kind (A = K - k^2 M + i k B).
   const uint8_t* real_blk;
-  // Optional (complex128 only): the real parts of vals.  Real blocks are
-  // staged from it: 8 bytes per entry in HBM and shared memory instead of 16.
-  const double* vals_re;
+  // Optional: the real parts of vals.  Real blocks are staged from it: 8
+  // (complex128) or 4 (complex64) bytes per entry in HBM and shared memory
+  // instead of 16 or 8.  Without it (or real_blk) no tile is staged.
+  const typename RealOf<V>::T* vals_re;
 };
 
 // Row sum of a complex128 row whose entries are all real: reads only the
@@ -70,13 +76,14 @@ __device__ __forceinline__ double2 mac_real(double a, double2 x, double2 acc) {
   acc.y = fma(a, x.y, acc.y);
   return acc;
 }
+__device__ __forceinline__ float2 mac_real(float a, float2 x, float2 acc) {
+  acc.x = fmaf(a, x.x, acc.x);
+  acc.y = fmaf(a, x.y, acc.y);
+  return acc;
+}
 template <class V>
 __device__ __forceinline__ bool row_block_real(const CsrDev<V>& A, int64_t r) {
-  return false;
-}
-template <>
-__device__ __forceinline__ bool row_block_real<double2>(const CsrDev<double2>& A, int64_t r) {
-  return A.real_blk != nullptr && A.real_blk[r >> 5] != 0;
+  return A.real_blk != nullptr && A.vals_re != nullptr && A.real_blk[r >> 5] != 0;
 }
 
 __device__ __forceinline__ double2 mac(double2 a, double2 x, double2 acc) { return cfma(a, x, acc); }
@@ -85,10 +92,9 @@ template <class V> __device__ __forceinline__ V vzero();
 template <> __device__ __forceinline__ double2 vzero<double2>() { return make_double2(0.0, 0.0); }
 template <> __device__ __forceinline__ float2 vzero<float2>() { return make_float2(0.f, 0.f); }
 
-// Type of a staged value: complex128 tiles are staged only when all their
-// entries are real, as doubles; complex64 tiles as they are.
-template <class V> struct StagedVal { using T = V; };
-template <> struct StagedVal<double2> { using T = double; };
+// Type of a staged value: tiles are staged only when all their entries are
+// real, as their real parts.
+template <class V> struct StagedVal { using T = typename RealOf<V>::T; };
 
 // Shared-memory footprint of the staged engine: STAGES buffers of CAP
 // entries each.
@@ -106,9 +112,9 @@ struct SpmvStage {
 
 template <class V> __device__ __forceinline__ V vadd(V a, V b) { return cadd(a, b); }
 
-// multiply-accumulate with a staged value
+// multiply-accumulate with a staged (real) value
 __device__ __forceinline__ double2 mac_staged(double a, double2 x, double2 acc) { return mac_real(a, x, acc); }
-__device__ __forceinline__ float2 mac_staged(float2 a, float2 x, float2 acc) { return mac(a, x, acc); }
+__device__ __forceinline__ float2 mac_staged(float a, float2 x, float2 acc) { return mac_real(a, x, acc); }
 
 // Walk this block's tiles; call epi.row(r, acc) for each row r with
 // acc = sum_k vals[k] * x[colind[k]].  epi.prefetch(r) is called by the same
@@ -117,10 +123,9 @@ __device__ __forceinline__ float2 mac_staged(float2 a, float2 x, float2 acc) { r
 // never completed (error flag set).  Must be called by all threads of the
 // block.
 //
-// Staged tiles: complex64 tiles, and complex128 tiles whose entries are all
-// real (copied from vals_re as doubles), with at most CAP entries.  Other
-// tiles (complex128 tiles with a complex entry -- for Helmholtz FEM only the
-// rows at the impedance boundary -- and tiles of very long rows) are
+// Staged tiles: tiles whose entries are all real (copied from vals_re), with
+// at most CAP entries.  Other tiles (a complex entry -- for Helmholtz FEM
+// only the rows at the impedance boundary -- or very long rows) are
 // multiplied with direct loads of vals / colind.
 //
 // STAGES = 2: the copy of a block's next tile overlaps the current tile.
@@ -147,8 +152,7 @@ __device__ __forceinline__ bool spmv_tiles(const CsrDev<V>& A, const V* __restri
                                            unsigned char* smem, unsigned int* dev_err, Gate gate = Gate()) {
   using S = SpmvStage<V, CAP, STAGES>;
   using T = typename S::T;
-  constexpr bool kC128 = std::is_same<V, double2>::value;
-  static_assert(!kC128 || R == 32, "complex128 tiles are the 32-row blocks of real_blk");
+  static_assert(R == 32, "tiles are the 32-row blocks of real_blk");
   __shared__ V s_part[SPLIT > 1 ? (SPLIT - 1) * R : 1];
   const int part = SPLIT > 1 ? static_cast<int>(threadIdx.x) / R : 0;
   const int lrow = SPLIT > 1 ? static_cast<int>(threadIdx.x) % R : static_cast<int>(threadIdx.x);
@@ -159,10 +163,7 @@ __device__ __forceinline__ bool spmv_tiles(const CsrDev<V>& A, const V* __restri
     return reinterpret_cast<int32_t*>(smem + STAGES * S::kValsBytes + b * S::kColsBytes);
   };
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + STAGES * (S::kValsBytes + S::kColsBytes));
-  // source of the staged values
-  const T* stage_src;
-  if constexpr (kC128) stage_src = A.vals_re;
-  else stage_src = A.vals;
+  const T* stage_src = A.vals_re;  // source of the staged values
 
   const int32_t n = A.n;
   const int32_t ntiles = (n + R - 1) / R;
@@ -186,8 +187,7 @@ __device__ __forceinline__ bool spmv_tiles(const CsrDev<V>& A, const V* __restri
     const int32_t r1 = min(r0 + R, n);
     g.s = A.rowptr[r0];
     g.e = A.rowptr[r1];
-    g.staged = (g.e - g.s) <= CAP;
-    if constexpr (kC128) g.staged = g.staged && A.vals_re != nullptr && A.real_blk[t] != 0;
+    g.staged = (g.e - g.s) <= CAP && A.vals_re != nullptr && A.real_blk != nullptr && A.real_blk[t] != 0;
     g.va0 = g.s & ~int64_t(VG - 1);
     g.va1 = min((g.e + VG - 1) & ~int64_t(VG - 1), vend);
     g.ca0 = g.s & ~int64_t(3);
@@ -274,13 +274,11 @@ __device__ __forceinline__ bool spmv_tiles(const CsrDev<V>& A, const V* __restri
         }
       } else {
         bool done = false;
-        if constexpr (kC128) {
-          if (rreal && A.vals_re != nullptr) {  // real rows of a tile too long to stage
+        if (rreal) {  // real rows of a tile too long to stage
 #pragma unroll 4
-            for (int64_t k = k0; k < k1; k += KS)
-              acc = mac_real(__ldcs(A.vals_re + k), ld_gather(x + ld_stream(A.colind + k)), acc);
-            done = true;
-          }
+          for (int64_t k = k0; k < k1; k += KS)
+            acc = mac_real(__ldcs(A.vals_re + k), ld_gather(x + ld_stream(A.colind + k)), acc);
+          done = true;
         }
         if (!done) {
 #pragma unroll 4
@@ -312,51 +310,6 @@ __device__ __forceinline__ bool spmv_tiles(const CsrDev<V>& A, const V* __restri
     }
   }
   return ok;
-}
-
-// Direct-load engine: LANES threads per row (1, 2, 4, 8, 16 or 32), no shared
-// memory, so occupancy is limited only by registers.  Entries are read
-// through L1 (consecutive k of a lane group share sectors); the lane sums
-// are combined with a fixed xor-shuffle tree (log2 LANES FP64 adds).  The
-// warp walks rows in uniform steps so every shuffle has all 32 lanes.
-template <class V, int LANES, class Epi>
-__device__ __forceinline__ void spmv_lanes(const CsrDev<V>& A, const V* __restrict__ x, Epi& epi) {
-  static_assert(LANES >= 1 && LANES <= 32 && (LANES & (LANES - 1)) == 0, "power of two");
-  constexpr int RPW = 32 / LANES;  // rows per warp step
-  const int lane = threadIdx.x & 31;
-  const int sub = lane % LANES;
-  const int64_t warp = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
-  for (int64_t base = warp * RPW; base < A.n; base += nwarps * RPW) {
-    const int64_t r = base + lane / LANES;
-    const bool valid = r < A.n;
-    V acc = vzero<V>();
-    if (valid && sub == 0) epi.prefetch(static_cast<int32_t>(r));
-    if (valid) {
-      const int64_t k0 = A.rowptr[r], k1 = A.rowptr[r + 1];
-      bool real_done = false;
-      if constexpr (std::is_same<V, double2>::value) {
-        if (row_block_real(A, r)) {
-          const double* vr = reinterpret_cast<const double*>(A.vals);
-#pragma unroll 4
-          for (int64_t k = k0 + sub; k < k1; k += LANES)
-            acc = mac_real(__ldg(vr + 2 * k), ld_gather(x + __ldg(A.colind + k)), acc);
-          real_done = true;
-        }
-      }
-      if (!real_done) {
-#pragma unroll 4
-        for (int64_t k = k0 + sub; k < k1; k += LANES)
-          acc = mac(__ldg(A.vals + k), ld_gather(x + __ldg(A.colind + k)), acc);
-      }
-    }
-#pragma unroll
-    for (int off = LANES / 2; off > 0; off >>= 1) {
-      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
-      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
-    }
-    if (valid && sub == 0) epi.row(static_cast<int32_t>(r), acc);
-  }
 }
 
 // The engine configuration every SpMV-shaped kernel of the library uses.

@@ -426,7 +426,7 @@ helm_status tfqmr_fp64(helm_csr A, const double2* b, double2* x, const helm_opts
   double2* W = A->vec;
   TqArgs a;
   std::memset(&a, 0, sizeof(a));
-  a.A = CsrDev<V>{A->n, A->nnz, A->rowptr, A->colind, static_cast<const V*>(A->vals), A->real_blk, A->vals_re};
+  a.A = csr_for(A, o);
   a.b = b;
   a.x = x;
   a.r0 = W;
@@ -444,8 +444,7 @@ helm_status tfqmr_fp64(helm_csr A, const double2* b, double2* x, const helm_opts
 
   // graph cache: key (b, x) tagged by the method (low bit of b set for TFQMR)
   GraphEntry* g = nullptr;
-  auto key = std::make_pair(static_cast<const void*>(reinterpret_cast<const char*>(b) + 1),
-                            static_cast<const void*>(x));
+  auto key = graph_key(b, x, 1, o);
   auto it = A->graphs.find(key);
   if (o.launch == HELM_LAUNCH_HOST) {
   } else if (it != A->graphs.end()) {

@@ -428,3 +428,42 @@ def test_bicgstabl_one_is_bicgstab_and_special_cases():
     p, vals = _tiny_problems()[1]
     x, info = oracle.bicgstabl(p.rowptr, p.colind, vals, np.zeros(p.n, np.complex128), ell=2)
     assert info["status"] == "ok" and info["iters"] == 0 and np.all(x == 0)
+
+
+# ---------------------------------------------------------------- right Jacobi
+
+def test_jacobi_scale_is_column_scaling_by_the_diagonal():
+    """A D^-1 equals the dense product with diag(1/a_ii); its diagonal is 1; a
+    row without a stored diagonal keeps scale 1 (pins against dense algebra)."""
+    for p, vals in _tiny_problems():
+        vs, d, dinv = oracle.jacobi_scale(p.rowptr, p.colind, vals)
+        A = oracle.densify(p.rowptr, p.colind, vals)
+        assert np.array_equal(d, np.diag(A))
+        As = oracle.densify(p.rowptr, p.colind, vs)
+        assert np.allclose(As, A @ np.diag(1.0 / np.diag(A)), rtol=0, atol=4 * EPS * np.abs(As).max())
+        assert np.allclose(np.diag(As), 1.0, rtol=0, atol=4 * EPS)
+    # row 1 stores no diagonal
+    rowptr = np.array([0, 2, 4, 6], np.int32)
+    colind = np.array([0, 2, 0, 2, 1, 2], np.int32)
+    vals = np.array([2.0, 1.0, 1.0, 3.0, 4.0, 5.0 + 1j], np.complex128)
+    vs, d, dinv = oracle.jacobi_scale(rowptr, colind, vals)
+    assert np.array_equal(d, [2.0, 1.0, 5.0 + 1j])
+    b = np.array([1.0, 2.0, 3.0 - 1j])
+    x, info = oracle.jacobi_solve(oracle.bicgstab, rowptr, colind, vals, b, tol=1e-14, maxit=100)
+    assert info["status"] == "ok"
+    assert np.allclose(x, np.linalg.solve(oracle.densify(rowptr, colind, vals), b), rtol=1e-12)
+
+
+@pytest.mark.parametrize("method", ["bicgstab", "tfqmr", "bicgstabl"])
+def test_jacobi_solve_matches_dense_lu(method):
+    fn = getattr(oracle, method)
+    for p, vals in _tiny_problems():
+        b = g.complex_vector(p.n, 26) * (~p.dirichlet)
+        xs = oracle.dense_solve(p.rowptr, p.colind, vals, b)
+        x, info = oracle.jacobi_solve(fn, p.rowptr, p.colind, vals, b, tol=1e-12, maxit=10000)
+        assert info["status"] == "ok"
+        # the true residual it reports is that of A D^-1 y = b, i.e. of A x = b
+        r = np.linalg.norm(b - oracle.spmv(p.rowptr, p.colind, vals, x)) / np.linalg.norm(b)
+        assert r <= 2e-12
+        cond = np.linalg.cond(oracle.densify(p.rowptr, p.colind, vals))
+        assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= 10 * cond * 1e-12
