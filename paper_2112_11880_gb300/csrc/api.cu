@@ -445,6 +445,9 @@ helm_status helm_csr_create(helm_csr* out, int32_t n, int64_t nnz, const int32_t
   if (cudaMemsetAsync(A->tickets, 0, (TK_COUNT + 2) * sizeof(unsigned int), s) != cudaSuccess)
     return fail(HELM_ERR_CUDA);
   A->dev_err = A->tickets + TK_COUNT;
+  if (cudaMalloc(&A->gtickets, 2 * kGroupTickets * sizeof(unsigned int)) != cudaSuccess) return fail(HELM_ERR_NOMEM);
+  if (cudaMemsetAsync(A->gtickets, 0, 2 * kGroupTickets * sizeof(unsigned int), s) != cudaSuccess)
+    return fail(HELM_ERR_CUDA);
   // two solver states: [0] the Krylov loop, [1] an outer loop (refinement)
   if (cudaMalloc(&A->state, 2 * sizeof(SolverState)) != cudaSuccess) return fail(HELM_ERR_NOMEM);
   if (cudaMemsetAsync(A->state, 0, 2 * sizeof(SolverState), s) != cudaSuccess) return fail(HELM_ERR_CUDA);
@@ -514,6 +517,7 @@ helm_status helm_csr_destroy(helm_csr A) {
   }
   cudaFree(A->partials);
   cudaFree(A->tickets);
+  cudaFree(A->gtickets);
   cudaFree(A->state);
   if (A->state_host) cudaFreeHost(A->state_host);
   cudaFree(A->vec);

@@ -109,6 +109,7 @@ helm_status bicgstab_fp64(helm_csr A, const double2* b, double2* x, const helm_o
   a.st = A->state;
   a.partials = A->partials;
   a.tickets = A->tickets;
+  a.gtickets = A->gtickets;
   a.dev_err = A->dev_err;
   TailFp64 tail{0};
   HELM_TRY(persistent_grid({reinterpret_cast<const void*>(&k_tail)}, R, kSmem, A->num_sms,

@@ -257,6 +257,61 @@ __device__ __forceinline__ bool grid_sum_last(double (&v)[K], double* partials,
   return true;
 }
 
+// Two-level form for grids of many small blocks: blocks form groups of
+// blockDim.x consecutive blocks; the last block of a group to arrive adds the
+// group's partials (one per thread) and stores the group sum after the block
+// partials; the last group to finish adds the group sums.  Each level adds in
+// a fixed order (thread j takes member j, then the fixed block tree), so the
+// result does not depend on arrival order.  gticket holds one counter per
+// group (at most 256 groups); partials holds gridDim.x * K + groups * K
+// doubles.  The total is valid in thread 0 of the returning block.
+template <int K>
+__device__ __forceinline__ bool grid_sum_last2(double (&v)[K], double* partials, unsigned int* ticket,
+                                               unsigned int* gticket, double* red, double (&tot)[K]) {
+  __shared__ bool s_go;
+  block_sum<K>(v, red);
+  const unsigned int T = blockDim.x;
+  const unsigned int g = blockIdx.x / T, ng = (gridDim.x + T - 1) / T;
+  const unsigned int g0 = g * T, gn = min(T, gridDim.x - g0);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) partials[(size_t)blockIdx.x * K + k] = v[k];
+    __threadfence();
+    s_go = atomicAdd(&gticket[g], 1u) == gn - 1;
+  }
+  __syncthreads();
+  if (!s_go) return false;
+  __threadfence();
+  double acc[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) acc[k] = 0.0;
+  for (unsigned int j = threadIdx.x; j < gn; j += T)
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] += ld_cg(&partials[(size_t)(g0 + j) * K + k]);
+  block_sum<K>(acc, red);
+  double* gpart = partials + (size_t)gridDim.x * K;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) gpart[(size_t)g * K + k] = acc[k];
+    gticket[g] = 0u;
+    __threadfence();
+    s_go = atomicAdd(ticket, 1u) == ng - 1;
+  }
+  __syncthreads();
+  if (!s_go) return false;
+  __threadfence();
+#pragma unroll
+  for (int k = 0; k < K; ++k) acc[k] = 0.0;
+  for (unsigned int j = threadIdx.x; j < ng; j += T)
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] += ld_cg(&gpart[(size_t)j * K + k]);
+  block_sum<K>(acc, red);
+#pragma unroll
+  for (int k = 0; k < K; ++k) tot[k] = acc[k];
+  if (threadIdx.x == 0) *ticket = 0u;
+  return true;
+}
+
 // ---------------------------------------------------------------- dependent launch
 // Programmatic dependent launch: a kernel launched with programmatic stream
 // serialization may start while its predecessor finishes.  It may load data

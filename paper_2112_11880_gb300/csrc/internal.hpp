@@ -31,6 +31,8 @@ enum : int32_t { PH_RUN = 0, PH_SCONV = 1, PH_DONE = 2 };
 
 // Tickets (arrival counters for last-block reductions), one per kernel kind.
 enum : int { TK_INIT = 0, TK_V, TK_S, TK_T, TK_XR, TK_TAIL, TK_AUX0, TK_AUX1, TK_AUX2, TK_AUX3, TK_COUNT };
+// Group counters per two-level reduction (groups of blockDim blocks).
+constexpr int kGroupTickets = 256;
 
 // SpMV engine shape (measured on GB300, 120x60x50 Q1 matrix): 32-row tiles
 // of up to 28 entries per row staged by TMA bulk copies into a single buffer
@@ -78,6 +80,7 @@ struct helm_csr_s {
   // workspace (owned)
   double* partials = nullptr;          // max(grid) * 8 doubles
   unsigned int* tickets = nullptr;     // TK_COUNT counters
+  unsigned int* gtickets = nullptr;    // 2 x kGroupTickets group counters (K2, K4)
   unsigned int* dev_err = nullptr;     // device error flags
   helm::SolverState* state = nullptr;  // device
   helm::SolverState* state_host = nullptr;  // pinned host mirror

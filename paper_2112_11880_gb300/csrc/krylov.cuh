@@ -73,6 +73,7 @@ struct KArgs {
   SolverState* st;
   double* partials;
   unsigned int* tickets;
+  unsigned int* gtickets;  // group counters of the two-level sums of K2 and K4
   unsigned int* dev_err;
   cudaGraphConditionalHandle cond;
   int has_cond;
@@ -250,8 +251,8 @@ __global__ void __launch_bounds__(Prec<V>::R) k_v(KArgs<V> a) {
   if (!go) return;
   double part[2] = {double(epi.part.x), double(epi.part.y)};
   double tot[2];
-  // many blocks of few threads: eight partials per round trip in the last block
-  if (!grid_sum_last<2, 8>(part, a.partials, a.tickets + TK_V, red, tot)) return;
+  // many blocks of few threads: the two-level sum keeps the last block short
+  if (!grid_sum_last2<2>(part, a.partials, a.tickets + TK_V, a.gtickets, red, tot)) return;
   if (threadIdx.x != 0) return;
   st->iter += 1;
   st->spmv_count += 1;
@@ -347,7 +348,7 @@ __global__ void __launch_bounds__(Prec<V>::R) k_t(KArgs<V> a) {
   if (!go) return;
   double part[3] = {double(epi.ts.x), double(epi.ts.y), double(epi.tt)};
   double tot[3];
-  if (!grid_sum_last<3, 8>(part, a.partials, a.tickets + TK_T, red, tot)) return;
+  if (!grid_sum_last2<3>(part, a.partials, a.tickets + TK_T, a.gtickets + kGroupTickets, red, tot)) return;
   if (threadIdx.x != 0) return;
   st->spmv_count += 1;
   const double2 ts = make_double2(tot[0], tot[1]);
@@ -638,6 +639,13 @@ helm_status build_while_graph(Init init, Body body, Tail tail, GraphEntry* out) 
 }
 
 // BiCGStab graph  init -> while(K1..K5) -> tail  for fixed vectors.
+// Iterations per pass of the while node's body: a finished solve lets the
+// remaining kernels of the pass return at once.
+#ifndef HELM_BODY_UNROLL
+#define HELM_BODY_UNROLL 1
+#endif
+constexpr int kBodyUnroll = HELM_BODY_UNROLL;
+
 template <class V, class Tail>
 helm_status build_krylov_graph(const KArgs<V>& base, const KShapes<V>& sh, Tail tail, GraphEntry* out) {
   auto with = [&](cudaGraphConditionalHandle cond) {
@@ -647,7 +655,9 @@ helm_status build_krylov_graph(const KArgs<V>& base, const KShapes<V>& sh, Tail 
     return a;
   };
   return build_while_graph([&](cudaGraphConditionalHandle c, cudaStream_t s) { enqueue_init(with(c), sh, s); },
-                           [&](cudaGraphConditionalHandle c, cudaStream_t s) { enqueue_body(with(c), sh, s); },
+                           [&](cudaGraphConditionalHandle c, cudaStream_t s) {
+                             for (int u = 0; u < kBodyUnroll; ++u) enqueue_body(with(c), sh, s);
+                           },
                            [&](cudaGraphConditionalHandle c, cudaStream_t s) { tail(with(c), s); }, out);
 }
 

@@ -372,6 +372,7 @@ helm_status solve_mixed(helm_csr A, const double2* b, double2* x, const helm_opt
   k.st = A->state;
   k.partials = A->partials;
   k.tickets = A->tickets;
+  k.gtickets = A->gtickets;
   k.dev_err = A->dev_err;
 
   RuArgs a;
