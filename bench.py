@@ -510,6 +510,17 @@ def run_extensions(args):
                      "relres_true": info["relres_true"]}
     res["speedup"] = round(res["plain"]["s"] / res["jacobi"]["s"], 3)
     out[WORKLOAD + "_jacobi"] = res
+    # (5) the paper's solver comparison (Tables 9-10): BiCGStab, TFQMR and
+    # BiCGStab(l) on the same system; one iteration = 2 (TFQMR) or 2 l
+    # (BiCGStab(l)) products with A
+    res = {}
+    for name, method, ell in (("bicgstab", helm.HELM_BICGSTAB, 2), ("tfqmr", helm.HELM_TFQMR, 2),
+                              ("bicgstab_l2", helm.HELM_BICGSTABL, 2), ("bicgstab_l8", helm.HELM_BICGSTABL, 8)):
+        o = helm.default_opts(tol=cfg.tol, maxit=100000, method=method, ell=ell)
+        info, dt = timed(lambda: helm.helm_bicgstab_solve(A.handle, b, x, o))
+        res[name] = {"s": round(dt, 4), "iters": info["iters"], "spmv": info["spmv_count"], "status": info["status"],
+                     "relres_true": info["relres_true"]}
+    out[WORKLOAD + "_methods"] = res
     A.close()
     print(json.dumps(out), flush=True)
 
