@@ -198,15 +198,20 @@ int tfqmr(const Csr& A, const cplx* b, cplx* x, double tol, int32_t maxit, int u
     for (int32_t i = 0; i < n; ++i) tmp[i] = b[i] - tmp[i];
     return dznrm2(n, tmp.data()) / bnorm;
   };
-  // w = u = r0 = b - A x ; v = A u ; d = 0
-  A.apply(x, tmp.data());
-  for (int32_t i = 0; i < n; ++i) { r0[i] = b[i] - tmp[i]; w[i] = r0[i]; u[i] = r0[i]; d[i] = 0.0; }
-  A.apply(u.data(), v.data());
-  for (int32_t i = 0; i < n; ++i) Au[i] = v[i];
-  double tau = dznrm2(n, r0.data());
-  double theta = 0.0;
-  cplx eta(0.0, 0.0), alpha(0.0, 0.0);
-  cplx rho = zdotc(n, r0.data(), r0.data());
+  // (re)start from the current x: w = u = r0 = b - A x ; v = A u ; d = 0
+  double tau = 0.0, theta = 0.0;
+  cplx eta(0.0, 0.0), alpha(0.0, 0.0), rho(0.0, 0.0);
+  auto start = [&]() {
+    A.apply(x, tmp.data());
+    for (int32_t i = 0; i < n; ++i) { r0[i] = b[i] - tmp[i]; w[i] = r0[i]; u[i] = r0[i]; d[i] = 0.0; }
+    A.apply(u.data(), v.data());
+    for (int32_t i = 0; i < n; ++i) Au[i] = v[i];
+    tau = dznrm2(n, r0.data());
+    theta = 0.0;
+    eta = cplx(0.0, 0.0);
+    rho = zdotc(n, r0.data(), r0.data());
+  };
+  start();
   double relres = tau / bnorm;
   *relres_true_out = relres;
   if (!std::isfinite(relres)) return ST_NONFINITE;
@@ -241,6 +246,12 @@ int tfqmr(const Csr& A, const cplx* b, cplx* x, double tol, int32_t maxit, int u
       const double rt = true_relres();
       *relres_true_out = rt;
       if (rt <= tol) { status = ST_OK; break; }
+      // the bound is below tol but the true residual is not: the recurrence
+      // has drifted from b - A x, so start again from the current x
+      if (!std::isfinite(rt)) { status = ST_NONFINITE; break; }
+      start();
+      m = -1;
+      continue;
     }
     if (even) {
       for (int32_t i = 0; i < n; ++i) u[i] = u_next[i];

@@ -26,7 +26,7 @@ struct SolverState {
   unsigned long long t0, deadline_ns;
 };
 
-enum : int32_t { ST_RUNNING = -1 };
+enum : int32_t { ST_RUNNING = -1, ST_RESTART = -2 };  // ST_RESTART: the host relaunches from the current x
 enum : int32_t { PH_RUN = 0, PH_SCONV = 1, PH_DONE = 2 };
 
 // Tickets (arrival counters for last-block reductions), one per kernel kind.

@@ -238,7 +238,9 @@ template <class V>
 __global__ void __launch_bounds__(Prec<V>::R) k_v(KArgs<V> a) {
   using S = typename Prec<V>::S;
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ double red[32 * 2];
+  // the block sums reuse the staging buffer once the tiles are done (less
+  // static shared memory: one more block per SM)
+  double* red = reinterpret_cast<double*>(smem);
   SolverState* st = a.st;
   struct Epi {
     const KArgs<V>* a;
@@ -332,7 +334,7 @@ template <class V>
 __global__ void __launch_bounds__(Prec<V>::R) k_t(KArgs<V> a) {
   using S = typename Prec<V>::S;
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ double red[32 * 3];
+  double* red = reinterpret_cast<double*>(smem);  // the staging buffer, once the tiles are done
   SolverState* st = a.st;
   struct Epi {
     const KArgs<V>* a;

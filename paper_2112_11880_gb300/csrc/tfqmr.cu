@@ -33,7 +33,7 @@ struct TqArgs {
   const V* b;
   V* x;
   V *r0, *w, *u, *un, *v, *Au, *Aun, *d;
-  SolverState* st;  // rho, alpha, beta; aux[0] = eta, aux[1] = (theta, tau), aux[2] = gamma, aux[3].x = check
+  SolverState* st;  // rho, alpha, beta; aux[0] = eta, aux[1] = (theta, tau), aux[2] = gamma, aux[3] = (check, start iteration)
   double* partials;
   unsigned int* tickets;
   unsigned int* dev_err;
@@ -142,7 +142,9 @@ __global__ void __launch_bounds__(RT) k_tq_init_a(TqArgs a) {
     st->aux[1] = make_double2(0.0, rn);  // theta = 0, tau = ||r0||
     st->aux[0] = make_double2(0.0, 0.0);  // eta
     st->aux[2] = make_double2(0.0, 0.0);  // gamma
-    st->aux[3] = make_double2(0.0, 0.0);  // check flag
+    // check flag; iteration at which this (re)start began (the half-step
+    // index m of the bound tau sqrt(m + 2) counts from there)
+    st->aux[3] = make_double2(0.0, static_cast<double>(st->iter));
   }
   st->status = status;
 }
@@ -205,7 +207,7 @@ __global__ void __launch_bounds__(256) k_tq_even(TqArgs a) {
   if (!grid_sum_last<1>(part, a.partials, a.tickets + TK_S, red, tot)) return;
   if (threadIdx.x != 0) return;
   st->iter += 1;
-  tq_half_step_scalars(st, tot[0], 2 * (st->iter - 1));
+  tq_half_step_scalars(st, tot[0], 2 * (st->iter - 1 - static_cast<int32_t>(st->aux[3].y)));
   if (st->status == ST_RUNNING) tq_gamma(st);  // gamma of the odd half-step's d update (same alpha)
 }
 
@@ -250,7 +252,7 @@ __global__ void __launch_bounds__(256) k_tq_odd(TqArgs a) {
   double tot[3];
   if (!grid_sum_last<3>(part, a.partials, a.tickets + TK_T, red, tot)) return;
   if (threadIdx.x != 0) return;
-  tq_half_step_scalars(st, tot[0], 2 * (st->iter - 1) + 1);
+  tq_half_step_scalars(st, tot[0], 2 * (st->iter - 1 - static_cast<int32_t>(st->aux[3].y)) + 1);
   if (st->status != ST_RUNNING) return;
   const double2 rho_new = make_double2(tot[1], tot[2]);
   if (!cfinite(rho_new)) {
@@ -355,6 +357,9 @@ __global__ void __launch_bounds__(RT) k_tq_check(TqArgs a) {
   else if (rt <= st->tol) status = HELM_OK;
   else if (st->iter >= st->maxit) status = HELM_ERR_NOT_CONVERGED;
   else if (st->deadline_ns != 0ull && (globaltimer_ns() - st->t0) > st->deadline_ns) status = HELM_ERR_TIMEOUT;
+  // the bound is below tol but the true residual is not: the recurrence has
+  // drifted from b - A x, so the host starts again from the current x
+  else status = ST_RESTART;
   st->status = status;
   tq_cond(a, status == ST_RUNNING);
 }
@@ -466,32 +471,38 @@ helm_status tfqmr_fp64(helm_csr A, const double2* b, double2* x, const helm_opts
 
   // an explicit graph request does not fall back to the host-driven loop
   if (!g && o.launch == HELM_LAUNCH_GRAPH) return HELM_ERR_CUDA;
-  k_configure<<<1, 1, 0, s>>>(A->state, o.tol, o.maxit, o.use_x0 ? 1 : 0, o.deadline_s, 1);
-  HELM_CUDA_TRY(cudaGetLastError());
   SolverState* hs = A->state_host;
-  if (g) {
-    HELM_CUDA_TRY(cudaGraphLaunch(g->exec, s));
-  } else {
-    tq_init(a, sh, s);
-    for (;;) {
-      for (int k = 0; k < 8; ++k) tq_body(a, sh, s);
-      HELM_CUDA_TRY(cudaGetLastError());
-      HELM_CUDA_TRY(cudaMemcpyAsync(hs, A->state, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
-      HELM_CUDA_TRY(cudaStreamSynchronize(s));
-      if (hs->status != ST_RUNNING) break;
-    }
-    tq_tail(a, sh, s);
-  }
   unsigned int herr = 0;
-  HELM_CUDA_TRY(cudaMemcpyAsync(hs, A->state, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
-  HELM_CUDA_TRY(cudaMemcpyAsync(&herr, A->dev_err, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
-  HELM_CUDA_TRY(cudaStreamSynchronize(s));
-  if (herr) return HELM_ERR_CUDA;
+  int32_t use_x0 = o.use_x0 ? 1 : 0, fresh = 1;
+  for (;;) {
+    k_configure<<<1, 1, 0, s>>>(A->state, o.tol, o.maxit, use_x0, o.deadline_s, fresh);
+    HELM_CUDA_TRY(cudaGetLastError());
+    if (g) {
+      HELM_CUDA_TRY(cudaGraphLaunch(g->exec, s));
+    } else {
+      tq_init(a, sh, s);
+      for (;;) {
+        for (int k = 0; k < 8; ++k) tq_body(a, sh, s);
+        HELM_CUDA_TRY(cudaGetLastError());
+        HELM_CUDA_TRY(cudaMemcpyAsync(hs, A->state, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
+        HELM_CUDA_TRY(cudaStreamSynchronize(s));
+        if (hs->status != ST_RUNNING) break;
+      }
+      tq_tail(a, sh, s);
+    }
+    HELM_CUDA_TRY(cudaMemcpyAsync(hs, A->state, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
+    HELM_CUDA_TRY(cudaMemcpyAsync(&herr, A->dev_err, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+    HELM_CUDA_TRY(cudaStreamSynchronize(s));
+    if (herr) return HELM_ERR_CUDA;
+    if (hs->status != ST_RESTART) break;
+    use_x0 = 1;  // start again from the current x, iterations counted on
+    fresh = 0;
+  }
   helm_status result = hs->status == ST_RUNNING ? HELM_ERR_CUDA : static_cast<helm_status>(hs->status);
   if (result == HELM_OK && !(hs->relres_true <= 1.5 * o.tol)) result = HELM_ERR_NOT_CONVERGED;
   if (info) {
     info->iters = hs->iter;
-    info->restarts = 0;
+    info->restarts = hs->restarts;
     info->relres_recur = hs->relres;
     info->relres_true = hs->relres_true;
     info->status = result;

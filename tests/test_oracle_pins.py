@@ -34,6 +34,32 @@ def test_element_matrix_identities(h):
     assert np.all(Bf[~mask] == 0)
 
 
+def _golden_q1():
+    import os
+    from fractions import Fraction as Fr
+    path = os.path.join(os.path.dirname(__file__), "golden", "q1_element_h1.txt")
+    mats, cur = {}, None
+    for line in open(path):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        if line in ("K", "M", "B"):
+            cur = mats.setdefault(line, [])
+        else:
+            cur.append([float(Fr(t)) for t in line.split()])
+    return {k: np.array(v) for k, v in mats.items()}
+
+
+@pytest.mark.parametrize("h", [1.0, 0.5, 0.0375])
+def test_element_matrices_match_exact_fixture(h):
+    """The generator's element matrices equal the exact unit-cube rationals of
+    tests/golden/q1_element_h1.txt scaled by h, h^3, h^2 (a few ulps)."""
+    gold = _golden_q1()
+    Ke, Me, Bf = g.element_matrices(h)
+    for got, ref, sc in ((Ke, gold["K"], h), (Me, gold["M"], h ** 3), (Bf, gold["B"], h ** 2)):
+        assert np.allclose(got, ref * sc, rtol=8 * EPS, atol=8 * EPS * sc)
+
+
 def test_global_mass_and_area():
     cfg = g.tiny_config(4, 3, 5, h=0.2)
     p = g.assemble(cfg, c=np.ones(cfg.n_elem), dirichlet=False)
