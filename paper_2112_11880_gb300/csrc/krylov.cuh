@@ -188,6 +188,13 @@ __global__ void __launch_bounds__(Prec<V>::R) k_init(KArgs<V> a) {
 // arithmetic, so the 64-clock FP64 latency and the memory latency of one
 // element overlap the other's.
 constexpr int kVecThreads = 256;
+// At most this many element-wise blocks per SM (measured on the 120x60x50
+// cavity: 3 -> 161.4, 4 -> 158.2, all that fit (6 for K1, K3) -> 159.1 us per
+// iteration).
+#ifndef HELM_VEC_MAX_BPS
+#define HELM_VEC_MAX_BPS 4
+#endif
+constexpr int kVecMaxBlocksPerSm = HELM_VEC_MAX_BPS;
 
 // Rows of an element-wise kernel: block b takes the contiguous range
 // [b n / G, (b + 1) n / G) (sizes differ by at most one, so every SM of a
@@ -586,6 +593,7 @@ inline helm_status krylov_shapes(helm_csr A, KShapes<V>* sh) {
   auto wave = [&](const void* fn, int* out) -> helm_status {
     int b = 0;
     HELM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, kVecThreads, 0));
+    if (b > kVecMaxBlocksPerSm) b = kVecMaxBlocksPerSm;
     int64_t per_sm = b < 1 ? 1 : b;
     if (per_sm_rows < per_sm) per_sm = per_sm_rows < 1 ? 1 : per_sm_rows;
     *out = static_cast<int>(per_sm * A->num_sms);
