@@ -69,6 +69,11 @@ typedef struct helm_csr_s* helm_csr; /* opaque CSR handle */
  *   d_colind : int32[nnz], column of each entry, 0 <= colind < n.
  *   d_vals   : complex[nnz] of type dt (complex128 or complex64).
  *   flags    : HELM_CSR_VALIDATE or 0.
+ * Ownership: the handle keeps the three device pointers (no copy); they must
+ * stay valid and unchanged until helm_csr_destroy.  What it derives from them
+ * is its own: per-32-row "all entries real" flags and the real parts of the
+ * values (here), the complex64 and right-Jacobi copies (at the first solve
+ * that needs them).
  * Work done: row statistics and the choice of SpMV variant (one device pass),
  * workspace allocation.  Synchronises `stream` once.  Returns
  * HELM_ERR_INVALID on bad sizes, a misaligned pointer, or (with
