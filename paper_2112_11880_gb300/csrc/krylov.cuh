@@ -1,9 +1,9 @@
 // BiCGStab kernels with device-resident scalars, generic over the vector
 // precision (complex128 for the FP64 solver, complex64 for the inner solve of
 // mixed precision).  Section 4 of the paper: P-BiCGSTAB with residual
-// tolerance, zero initial guess and an iteration cap; identity
-// preconditioner; the recurrence of van der Vorst 1992 / Saad 2003
-// Algorithm 7.7 with conjugated inner products.
+// tolerance, zero initial guess and an iteration cap; identity preconditioner
+// (right Jacobi runs the same kernels on A D^-1); the recurrence of van der
+// Vorst 1992 / Saad 2003 Algorithm 7.7 with conjugated inner products.
 //
 // One iteration is five kernels; each dot product the recurrence needs is
 // fused into the kernel that produces its operands, and the scalar it feeds
@@ -19,8 +19,9 @@
 // and grid sums and every scalar of the recurrence are FP64.
 //
 // The loop runs inside one CUDA graph: an init kernel, a conditional WHILE
-// node whose body is K1..K5 (K5's last block sets the condition) and, for
-// the FP64 solver, a tail kernel that recomputes the true residual b - A x.
+// node whose body is four iterations of K1..K5 (K5's last block sets the
+// condition) and, for the FP64 solver, a tail kernel that recomputes the true
+// residual b - A x.
 #pragma once
 
 #include <cstring>
@@ -446,7 +447,7 @@ __global__ void __launch_bounds__(kVecThreads) k_xr(KArgs<V> a) {
   double tot[3];
   if (!grid_sum_last<3>(part, a.partials, a.tickets + TK_XR, red, tot)) return;
   if (threadIdx.x != 0) return;
-  // reliable mode runs on a scaled residual: b - A x ~ aux[2].x * r
+  // the inner loop of mixed precision runs on a scaled residual: b - A x ~ aux[2].x * r
   const double sc = st->method == kModeRefine ? st->aux[2].x : 1.0;
   int status = ST_RUNNING;
   if (phase == PH_SCONV) {

@@ -367,7 +367,7 @@ helm_status solve_mixed(helm_csr A, const double2* b, double2* x, const helm_opt
   k.v = W + 3 * N;
   k.s = W + 4 * N;
   k.t = W + 5 * N;
-  k.x = W + 6 * N;  // x32: the increment since the last reliable update
+  k.x = W + 6 * N;  // d: the inner solution of the current refinement step
   k.b = W + 7 * N;  // not read by the loop body
   k.st = A->state;
   k.partials = A->partials;
@@ -448,7 +448,7 @@ helm_status solve_mixed(helm_csr A, const double2* b, double2* x, const helm_opt
   if (result == HELM_OK && !(hs->relres_true <= o.tol)) result = HELM_ERR_NOT_CONVERGED;
   if (info) {
     info->iters = hs->iter;
-    info->restarts = hs->restarts;  // reliable updates
+    info->restarts = hs->restarts;  // refinement steps
     info->relres_recur = hs->relres;
     info->relres_true = hs->relres_true;
     info->status = result;
