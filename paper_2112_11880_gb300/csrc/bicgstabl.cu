@@ -43,6 +43,7 @@ struct BlArgs {
   SolverState* st;     // rho = rho0, alpha, omega, beta; aux[0] = rho1
   double* partials;
   unsigned int* tickets;
+  unsigned int* gtickets;  // group counters of the two-level sums of B2 and B4
   unsigned int* dev_err;
   cudaGraphConditionalHandle cond;
   int has_cond;
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(256) k_bl_u(BlArgs a, int j) {
 // B2: u_{j+1} = A u_j, gamma = (r~, u_{j+1}) -> alpha
 __global__ void __launch_bounds__(RT) k_bl_au(BlArgs a, int j) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ double red[32 * 2];
+  double* red = reinterpret_cast<double*>(smem);  // the staging buffer, once the tiles are done
   SolverState* st = a.st;
   if (st->status != ST_RUNNING) return;
   struct Epi {
@@ -166,7 +167,7 @@ __global__ void __launch_bounds__(RT) k_bl_au(BlArgs a, int j) {
   spmv_run<V>(a.A, a.u[j], epi, smem, a.dev_err);
   double part[2] = {epi.acc.x, epi.acc.y};
   double tot[2];
-  if (!grid_sum_last<2>(part, a.partials, a.tickets + TK_V, red, tot)) return;
+  if (!grid_sum_last2<2>(part, a.partials, a.tickets + TK_V, a.gtickets, red, tot)) return;
   if (threadIdx.x != 0) return;
   st->spmv_count += 1;
   const double2 gamma = make_double2(tot[0], tot[1]);
@@ -200,7 +201,7 @@ __global__ void __launch_bounds__(256) k_bl_r(BlArgs a, int j) {
 // B4: r_{j+1} = A r_j, rho1 = (r~, r_{j+1})
 __global__ void __launch_bounds__(RT) k_bl_ar(BlArgs a, int j) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ double red[32 * 2];
+  double* red = reinterpret_cast<double*>(smem);  // the staging buffer, once the tiles are done
   SolverState* st = a.st;
   if (st->status != ST_RUNNING) return;
   struct Epi {
@@ -216,7 +217,7 @@ __global__ void __launch_bounds__(RT) k_bl_ar(BlArgs a, int j) {
   spmv_run<V>(a.A, a.r[j], epi, smem, a.dev_err);
   double part[2] = {epi.acc.x, epi.acc.y};
   double tot[2];
-  if (!grid_sum_last<2>(part, a.partials, a.tickets + TK_T, red, tot)) return;
+  if (!grid_sum_last2<2>(part, a.partials, a.tickets + TK_T, a.gtickets + kGroupTickets, red, tot)) return;
   if (threadIdx.x != 0) return;
   st->spmv_count += 1;
   st->aux[0] = make_double2(tot[0], tot[1]);  // rho1 of the next BiCG step
@@ -412,7 +413,9 @@ __global__ void __launch_bounds__(RT) k_bl_tail(BlArgs a) {
 }
 
 struct BlShapes {
-  int spmv_grid, vec_grid, gram_grid;
+  int spmv_grid;  // B2, B4
+  int init_grid;  // init and tail
+  int vec_grid, gram_grid;
 };
 
 template <int L>
@@ -455,10 +458,11 @@ helm_status bicgstabl_fp64(helm_csr A, const double2* b, double2* x, const helm_
     HELM_CUDA_TRY(set_smem_attr(fn, kSmem));
   BlShapes sh;
   {
-    HELM_TRY(persistent_grid({reinterpret_cast<const void*>(&k_bl_init), reinterpret_cast<const void*>(&k_bl_au),
-                              reinterpret_cast<const void*>(&k_bl_ar), reinterpret_cast<const void*>(&k_bl_tail)},
-                             RT, kSmem, A->num_sms, (static_cast<int64_t>(A->n) + Engine<V>::R - 1) / Engine<V>::R,
-                             &sh.spmv_grid));
+    const int64_t ntiles = (static_cast<int64_t>(A->n) + Engine<V>::R - 1) / Engine<V>::R;
+    HELM_TRY(persistent_grid({reinterpret_cast<const void*>(&k_bl_au), reinterpret_cast<const void*>(&k_bl_ar)}, RT,
+                             kSmem, A->num_sms, ntiles, &sh.spmv_grid));
+    HELM_TRY(persistent_grid({reinterpret_cast<const void*>(&k_bl_init), reinterpret_cast<const void*>(&k_bl_tail)},
+                             RT, kSmem, A->num_sms, ntiles, &sh.init_grid));
     sh.vec_grid = A->vec_grid;
     // the Gram kernel keeps 2 (l+1)(l+2)/2 accumulators per thread: few
     // blocks, and its partials (blocks x 45 x 2 doubles + coefficients) must
@@ -483,6 +487,7 @@ helm_status bicgstabl_fp64(helm_csr A, const double2* b, double2* x, const helm_
   a.st = A->state;
   a.partials = A->partials;
   a.tickets = A->tickets;
+  a.gtickets = A->gtickets;
   a.dev_err = A->dev_err;
 
   GraphEntry* g = nullptr;
@@ -501,10 +506,10 @@ helm_status bicgstabl_fp64(helm_csr A, const double2* b, double2* x, const helm_
     GraphEntry e;
     if (build_while_graph(
             [&](cudaGraphConditionalHandle c, cudaStream_t cs) {
-              k_bl_init<<<sh.spmv_grid, RT, kSmem, cs>>>(with(c));
+              k_bl_init<<<sh.init_grid, RT, kSmem, cs>>>(with(c));
             },
             [&](cudaGraphConditionalHandle c, cudaStream_t cs) { bl_body(with(c), sh, cs); },
-            [&](cudaGraphConditionalHandle c, cudaStream_t cs) { k_bl_tail<<<sh.spmv_grid, RT, kSmem, cs>>>(with(c)); },
+            [&](cudaGraphConditionalHandle c, cudaStream_t cs) { k_bl_tail<<<sh.init_grid, RT, kSmem, cs>>>(with(c)); },
             &e) == HELM_OK)
       g = &(A->graphs[key] = e);
   }
@@ -517,7 +522,7 @@ helm_status bicgstabl_fp64(helm_csr A, const double2* b, double2* x, const helm_
   if (g) {
     HELM_CUDA_TRY(cudaGraphLaunch(g->exec, s));
   } else {
-    k_bl_init<<<sh.spmv_grid, RT, kSmem, s>>>(a);
+    k_bl_init<<<sh.init_grid, RT, kSmem, s>>>(a);
     for (;;) {
       for (int q = 0; q < 4; ++q) bl_body(a, sh, s);
       HELM_CUDA_TRY(cudaGetLastError());
@@ -525,7 +530,7 @@ helm_status bicgstabl_fp64(helm_csr A, const double2* b, double2* x, const helm_
       HELM_CUDA_TRY(cudaStreamSynchronize(s));
       if (hs->status != ST_RUNNING) break;
     }
-    k_bl_tail<<<sh.spmv_grid, RT, kSmem, s>>>(a);
+    k_bl_tail<<<sh.init_grid, RT, kSmem, s>>>(a);
   }
   unsigned int herr = 0;
   HELM_CUDA_TRY(cudaMemcpyAsync(hs, A->state, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
