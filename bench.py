@@ -203,10 +203,12 @@ def run_gpu(args):
     ms = barrier_max(ms, ws)
     ok = all(i["status"] == "ok" and i["relres_true"] <= 1.5 * cfg.tol for i in infos)
     iters = [i["iters"] for i in infos]
-    # per graph launch: configure, init, tail; the while node runs the 5
-    # kernels of an iteration in passes of 4 iterations (the kernels of a
-    # pass's iterations after convergence launch and return at once)
-    launches = sum(3 * (i["restarts"] + 1) + 20 * (-(-i["iters"] // 4)) for i in infos)
+    # per launch of the loop: configure, init, tail; the 5 kernels of an
+    # iteration run in passes of 4 iterations (graph) or 16 (host-driven loop),
+    # and the kernels of a pass's iterations after convergence launch and
+    # return at once
+    per_pass = 4 if args.launch == "graph" else 16
+    launches = sum(3 * (i["restarts"] + 1) + 5 * per_pass * (-(-i["iters"] // per_pass)) for i in infos)
     solves = args.steps * ws
     value = solves / (ms / 1e3)
     # independent check of the last solution with the CPU SpMV of the generator data
