@@ -469,6 +469,24 @@ def run_extensions(args):
     A.close()
     print(json.dumps(out), flush=True)
 
+    # (2b) mixed precision vs FP64 on the benchmark workload, at its 1e-8
+    cfg = helmgen.CONFIGS[WORKLOAD]
+    p, vals, bh = build_problem(cfg)
+    b = torch.as_tensor(bh, device=dev)
+    A = helm.CsrMatrix.from_host(p.rowptr, p.colind, vals, device=dev)
+    x64 = torch.empty_like(b)
+    x32 = torch.empty_like(b)
+    info64, t64 = timed(lambda: helm.helm_bicgstab_solve(A.handle, b, x64, helm.default_opts(tol=cfg.tol,
+                                                                                            maxit=100000)))
+    info32, t32 = timed(lambda: helm.helm_bicgstab_solve(A.handle, b, x32, helm.default_opts(
+        tol=cfg.tol, maxit=200000, precision=helm.HELM_PREC_MIXED, inner_tol=0.01)))
+    err = float(torch.linalg.vector_norm(x32 - x64) / torch.linalg.vector_norm(x64))
+    out[WORKLOAD + "_mixed"] = {"tol": cfg.tol, "fp64": {"s": round(t64, 3), **info64},
+                                "mixed": {"s": round(t32, 3), "inner_tol": 0.01, **info32},
+                                "speedup": round(t64 / t32, 3), "rel_err_mixed_vs_fp64": err}
+    A.close()
+    print(json.dumps(out), flush=True)
+
     # (3) adjoint gradient on the 80x40x32 cavity
     cfg = helmgen.CONFIGS["adjoint80"]
     p = helmgen.assemble(cfg)

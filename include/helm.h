@@ -171,9 +171,10 @@ typedef enum {
   HELM_PREC_MIXED = 1 /* iterative refinement: complex64 BiCGStab inner
                          solves (values converted once into a handle-owned
                          copy), each ended when its residual has dropped by
-                         opts.inner_tol; the solution is accumulated and the
-                         residual b - A x recomputed in FP64 after each, and
-                         convergence is decided on that FP64 residual */
+                         opts.inner_tol; after each, an FP64 GCR step over a
+                         window of the last 8 directions updates the
+                         solution, the residual b - A x is recomputed in
+                         FP64, and convergence is decided on it */
 } helm_precision;
 /* How the iteration loop is driven on the device. */
 typedef enum {

@@ -19,6 +19,12 @@ struct SolverState {
   double2 rho, alpha, omega, beta;
   double2 aux[4];          // method-specific scalars
   double2 gamma;           // mixed precision: step length of the last refinement step
+  // mixed precision, GCR window over the refinement steps: projections of the
+  // new direction on the stored ones, its norm after orthogonalisation,
+  // directions stored, next slot, whether this step's direction is kept
+  double2 gcr_beta[8];
+  double gcr_nrm;
+  int32_t gcr_n, gcr_next, gcr_keep;
   double bnorm, tol, relres, relres_true;
   double tau, theta, eta;  // TFQMR
   int32_t iter, maxit, status, phase;

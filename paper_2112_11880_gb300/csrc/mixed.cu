@@ -1,10 +1,11 @@
-// Mixed-precision solve: iterative refinement (defect correction) in FP64
-// around a complex64 BiCGStab, the whole solve in one CUDA graph.
+// Mixed-precision solve: FP64 outer GCR (iterative refinement with a window
+// of directions) around complex64 BiCGStab inner solves, the whole solve in
+// one CUDA graph.
 //
 // The paper's library covers single and double precision (Section 1); here
 // single precision does the bulk of the work and FP64 decides accuracy:
 //   inner (FP32):  BiCGStab on A32 (complex64 copy of the values owned by the
-//                  handle, 12 bytes per entry instead of 20), vectors
+//                  handle, 8 bytes per entry for real rows instead of 12), vectors
 //                  complex64; products and per-thread sums FP32, block and
 //                  grid sums and every recurrence scalar FP64.  The inner
 //                  system is A32 d = r / sigma with sigma = ||r|| / sqrt(n)
@@ -13,23 +14,28 @@
 //                  smallest normal float long before FP64 convergence).
 //   step (FP64):   when the inner recurrence residual has dropped by
 //                  inner_tol since the inner solve began, looks below the
-//                  outer tolerance, or after kInnerMax inner iterations:
-//                  w = A (sigma d), gamma = (w, r) / (w, w) (the step that
-//                  minimises ||r - gamma w||, so a poor inner solve cannot
-//                  increase the residual), x += gamma sigma d;
-//                  r = b - A x in FP64;  stop if ||r|| / ||b|| <= tol (or,
-//                  not converged, after three steps in a row without
-//                  halving ||r||);  else a fresh inner solve on the new r
-//                  (r^ = r, p = v = d = 0).
-// The inner operator is A rounded to complex64, so one step gains at most
-// about 1 / (kappa eps_float): an inner_tol near that bound wastes the fewest
-// inner iterations.  Keeping one inner process across steps (replacing its
-// residual only, Sleijpen & van der Vorst 1996) was tried first; on the
-// strongly indefinite 200x100x80 cavity its complex64 recurrence stagnated
-// (and diverged when combined with restarts), while restarted refinement
-// converges.  The convergence test is always the FP64 true residual.
-// Graph: init (+ first inner start) -> while(5 FP32 kernels + 5 step
+//                  outer tolerance, or after kInnerMax inner iterations, an
+//                  outer GCR step on z = sigma d: w = A z; c = w - sum beta_j
+//                  C_j and z -= sum beta_j Z_j over a window of the last
+//                  kGcr directions (C_j orthonormal, A Z_j = C_j; classical
+//                  Gram-Schmidt, beta_j = (C_j, w)); gamma = (c, r) / (c, c)
+//                  minimises ||r - gamma c||, so the residual is minimised
+//                  over the whole window and a poor inner solve cannot
+//                  increase it; x += gamma z; r = b - A x in FP64; stop if
+//                  ||r|| / ||b|| <= tol (or, not converged, after five steps
+//                  in a row without halving ||r||); else a fresh inner solve
+//                  on the new r (r^ = r, p = v = d = 0).
+// The inner operator is A rounded to complex64, so plain refinement gains at
+// most about kappa eps_float per step; the GCR window lets rough inner
+// solves add up instead.  Measured before it: one inner process kept across
+// steps with its residual replaced (Sleijpen & van der Vorst 1996) stagnated
+// on the strongly indefinite 200x100x80 cavity; plain restarted refinement
+// converged slowly and, folded without a step length, diverged whenever an
+// inner solve stagnated.  The convergence test is always the FP64 true
+// residual.
+// Graph: init (+ first inner start) -> while(5 FP32 kernels + 6 step
 // kernels) -> tail; the step kernels return at once when no step is due.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -38,6 +44,9 @@
 namespace helm {
 
 namespace {
+
+// Directions kept by the outer GCR (a window over the refinement steps).
+constexpr int kGcr = 8;
 
 constexpr int R128 = Engine<double2>::kThreads;  // threads per SpMV block
 constexpr size_t kSmem128 = Engine<double2>::kSmem;
@@ -48,6 +57,9 @@ struct RuArgs {
   double2* x;         // FP64 solution (the caller's)
   double2* r64;       // FP64 residual
   double2* d64;       // FP64 copy of the scaled inner solution
+  double2* w64;       // A d64
+  double2* Cw[kGcr];  // GCR window: orthonormal A z_j
+  double2* Zw[kGcr];  //   and the directions z_j
   float2 *x32, *r32, *rh32, *p32, *v32;
   SolverState* st;    // the inner loop's state
   double* partials;
@@ -123,6 +135,9 @@ __global__ void __launch_bounds__(R128) k_mx_init(RuArgs a) {
   st->aux[0] = make_double2(rn, 0.0);   // ||r64||, iteration of the last step
   st->aux[1] = make_double2(1.0, 0.0);  // inner start due
   st->aux[2] = make_double2(0.0, 0.0);  // no inner scale yet
+  st->gcr_n = 0;                         // empty GCR window
+  st->gcr_next = 0;
+  st->gcr_keep = 0;
   st->status = status;
 }
 
@@ -144,47 +159,147 @@ __global__ void __launch_bounds__(256) k_mx_lift(RuArgs a, int always) {
   }
 }
 
-// step 1b: w = A d64 (FP64) and gamma = (w, r64) / (w, w), the step length
-// that minimises ||r64 - gamma w||: x += gamma d64 never increases the FP64
-// residual, whatever the inner solve returned (gamma = 1 for an exact one).
-__global__ void __launch_bounds__(R128) k_mx_mr(RuArgs a, int always) {
+// Block and grid sums of K > 4 doubles: slices of four through the fixed-
+// order block tree (result in thread 0), then the last block adds the block
+// partials in block order.
+template <int K>
+__device__ __forceinline__ void block_sum_many(double (&v)[K], double* red) {
+#pragma unroll
+  for (int k0 = 0; k0 < K; k0 += 4) {
+    double q[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) q[k] = k0 + k < K ? v[k0 + k < K ? k0 + k : 0] : 0.0;
+    block_sum<4>(q, red);
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (k0 + k < K) v[k0 + k < K ? k0 + k : 0] = q[k];
+  }
+}
+template <int K>
+__device__ __forceinline__ bool grid_sum_last_many(double (&v)[K], double* partials, unsigned int* ticket,
+                                                   double* red, double (&tot)[K]) {
+  __shared__ bool s_last;
+  block_sum_many<K>(v, red);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) partials[(size_t)blockIdx.x * K + k] = v[k];
+    __threadfence();
+    s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+  double acc[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) acc[k] = 0.0;
+  for (unsigned int b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] += ld_cg(&partials[(size_t)b * K + k]);
+  block_sum_many<K>(acc, red);
+#pragma unroll
+  for (int k = 0; k < K; ++k) tot[k] = acc[k];
+  if (threadIdx.x == 0) *ticket = 0u;
+  return true;
+}
+
+// step 1b: w = A z (FP64, z = d64) and the projections beta_j = (C_j, w) on
+// the stored directions (classical Gram-Schmidt against the GCR window).
+__global__ void __launch_bounds__(R128) k_gcr_project(RuArgs a, int always) {
   extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int K = 2 * kGcr;
+  __shared__ double red[32 * 4];
+  SolverState* st = a.st;
+  if (!always && st->aux[1].x == 0.0) return;
+  const int nw = st->gcr_n;
+  struct Epi {
+    const RuArgs* a;
+    int nw;
+    double acc[K];
+    __device__ __forceinline__ void prefetch(int32_t) {}
+    __device__ __forceinline__ void row(int32_t i, double2 w) {
+      a->w64[i] = w;
+#pragma unroll
+      for (int j = 0; j < kGcr; ++j) {
+        if (j < nw) {
+          const double2 q = cfma_conj(a->Cw[j][i], w, make_double2(acc[2 * j], acc[2 * j + 1]));
+          acc[2 * j] = q.x;
+          acc[2 * j + 1] = q.y;
+        }
+      }
+    }
+  } epi{&a, nw, {}};
+  spmv_run<double2>(a.A, a.d64, epi, smem, a.dev_err);
+  double tot[K];
+  if (!grid_sum_last_many<K>(epi.acc, a.partials, a.tickets + TK_AUX2, red, tot)) return;
+  if (threadIdx.x != 0) return;
+  st->spmv_count += 1;
+#pragma unroll
+  for (int j = 0; j < kGcr; ++j) st->gcr_beta[j] = j < nw ? make_double2(tot[2 * j], tot[2 * j + 1]) : make_double2(0.0, 0.0);
+}
+
+// step 1c: c = w - sum beta_j C_j, z = d64 - sum beta_j Z_j into the window
+// slot; gamma = (c, r64) / (c, c), the step that minimises ||r64 - gamma c||
+// over the direction orthogonal to the window (so never an increase of the
+// FP64 residual, whatever the inner solve returned).
+__global__ void __launch_bounds__(256) k_gcr_orth(RuArgs a, int always) {
   __shared__ double red[32 * 3];
   SolverState* st = a.st;
   if (!always && st->aux[1].x == 0.0) return;
-  struct Epi {
-    const RuArgs* a;
-    double2 wr;
-    double ww;
-    double2 ri;
-    __device__ __forceinline__ void prefetch(int32_t i) { ri = a->r64[i]; }
-    __device__ __forceinline__ void row(int32_t i, double2 w) {
-      wr = cfma_conj(w, ri, wr);
-      ww = cabs2_acc(w, ww);
+  const int nw = st->gcr_n, slot = st->gcr_next;
+  double2 beta[kGcr];
+#pragma unroll
+  for (int j = 0; j < kGcr; ++j) beta[j] = st->gcr_beta[j];
+  double2 cr = make_double2(0.0, 0.0);
+  double cc = 0.0;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.A.n; i += gridDim.x * blockDim.x) {
+    double2 c = a.w64[i], z = a.d64[i];
+#pragma unroll
+    for (int j = 0; j < kGcr; ++j) {
+      if (j < nw) {
+        c = cfms(beta[j], a.Cw[j][i], c);
+        z = cfms(beta[j], a.Zw[j][i], z);
+      }
     }
-  } epi{&a, make_double2(0.0, 0.0), 0.0, make_double2(0.0, 0.0)};
-  spmv_run<double2>(a.A, a.d64, epi, smem, a.dev_err);
-  double part[3] = {epi.wr.x, epi.wr.y, epi.ww};
+    a.Cw[slot][i] = c;
+    a.Zw[slot][i] = z;
+    cr = cfma_conj(c, a.r64[i], cr);
+    cc = cabs2_acc(c, cc);
+  }
+  double part[3] = {cr.x, cr.y, cc};
   double tot[3];
-  if (!grid_sum_last<3, 8>(part, a.partials, a.tickets + TK_AUX2, red, tot)) return;
+  if (!grid_sum_last<3>(part, a.partials, a.tickets + TK_AUX3, red, tot)) return;
   if (threadIdx.x != 0) return;
-  st->spmv_count += 1;
   double2 gamma = make_double2(0.0, 0.0);
+  double nrm = 0.0;
+  int keep = 0;
   if (tot[2] > 0.0 && isfinite(tot[2])) {
     const double inv = 1.0 / tot[2];
     gamma = make_double2(tot[0] * inv, tot[1] * inv);
-    if (!cfinite(gamma)) gamma = make_double2(0.0, 0.0);
+    nrm = sqrt(tot[2]);
+    keep = cfinite(gamma) ? 1 : 0;
+    if (!keep) gamma = make_double2(0.0, 0.0);
   }
   st->gamma = gamma;
+  st->gcr_nrm = nrm;
+  st->gcr_keep = keep;
 }
 
-// step 1c: x += gamma d64
-__global__ void __launch_bounds__(256) k_mx_xupd(RuArgs a, int always) {
+// step 1d: x += gamma z, and the window slot normalised (|| C_slot || = 1)
+__global__ void __launch_bounds__(256) k_gcr_xupd(RuArgs a, int always) {
   const SolverState* st = a.st;
   if (!always && st->aux[1].x == 0.0) return;
   const double2 gamma = st->gamma;
-  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.A.n; i += gridDim.x * blockDim.x)
-    a.x[i] = cfma(gamma, a.d64[i], a.x[i]);
+  const int slot = st->gcr_next, keep = st->gcr_keep;
+  const double inv = keep ? 1.0 / st->gcr_nrm : 0.0;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.A.n; i += gridDim.x * blockDim.x) {
+    const double2 z = a.Zw[slot][i];
+    a.x[i] = cfma(gamma, z, a.x[i]);
+    if (keep) {
+      const double2 c = a.Cw[slot][i];
+      a.Cw[slot][i] = make_double2(c.x * inv, c.y * inv);
+      a.Zw[slot][i] = make_double2(z.x * inv, z.y * inv);
+    }
+  }
 }
 
 // step 2: r64 = b - A x (FP64), the convergence test
@@ -225,6 +340,12 @@ __global__ void __launch_bounds__(R128) k_mx_residual(RuArgs a) {
   st->aux[3].x = rn > 0.5 * prev ? st->aux[3].x + 1.0 : 0.0;
   if (st->status == ST_RUNNING && st->aux[3].x >= 5.0) st->status = HELM_ERR_NOT_CONVERGED;
   st->aux[0] = make_double2(rn, static_cast<double>(st->iter));
+  // the step's direction joins the GCR window (the oldest one leaves it)
+  if (st->gcr_keep) {
+    st->gcr_next = (st->gcr_next + 1) % kGcr;
+    if (st->gcr_n < kGcr) st->gcr_n += 1;
+    st->gcr_keep = 0;
+  }
 }
 
 // step 3: a fresh inner solve on r64: sigma = ||r64|| / sqrt(n),
@@ -311,6 +432,7 @@ __global__ void __launch_bounds__(R128) k_mx_tail(RuArgs a) {
 struct MxShapes {
   KShapes<float2> k;
   int grid128;
+  int grid_proj;  // the projection's 2 kGcr partial sums per block fit the partials buffer
   int vec_grid;
 };
 
@@ -320,8 +442,9 @@ void mx_init(const RuArgs& a, const MxShapes& sh, cudaStream_t s) {
 }
 void mx_fold(const RuArgs& a, const MxShapes& sh, int always, cudaStream_t s) {
   k_mx_lift<<<sh.vec_grid, 256, 0, s>>>(a, always);
-  k_mx_mr<<<sh.grid128, R128, kSmem128, s>>>(a, always);
-  k_mx_xupd<<<sh.vec_grid, 256, 0, s>>>(a, always);
+  k_gcr_project<<<sh.grid_proj, R128, kSmem128, s>>>(a, always);
+  k_gcr_orth<<<sh.vec_grid, 256, 0, s>>>(a, always);
+  k_gcr_xupd<<<sh.vec_grid, 256, 0, s>>>(a, always);
 }
 void mx_body(const RuArgs& a, const KArgs<float2>& k, const MxShapes& sh, cudaStream_t s) {
   enqueue_body(k, sh.k, s);
@@ -339,20 +462,22 @@ void mx_tail(const RuArgs& a, const MxShapes& sh, cudaStream_t s) {
 helm_status solve_mixed(helm_csr A, const double2* b, double2* x, const helm_opts& o, helm_info* info,
                         cudaStream_t s) {
   helm_status st = ensure_vals32(A, s);
-  if (st == HELM_OK) st = ensure_vectors(A, kNumVec);
+  if (st == HELM_OK) st = ensure_vectors(A, kNumVec > 3 + 2 * kGcr ? kNumVec : 3 + 2 * kGcr);
   if (st == HELM_OK) st = ensure_vectors32(A, 8);
   if (st == HELM_OK) st = prepare_krylov_kernels<float2>();
   if (st != HELM_OK) return st;
   for (const void* fn : {reinterpret_cast<const void*>(&k_mx_init), reinterpret_cast<const void*>(&k_mx_residual),
-                         reinterpret_cast<const void*>(&k_mx_mr), reinterpret_cast<const void*>(&k_mx_tail)})
+                         reinterpret_cast<const void*>(&k_gcr_project), reinterpret_cast<const void*>(&k_mx_tail)})
     HELM_CUDA_TRY(set_smem_attr(fn, kSmem128));
   MxShapes sh;
   st = krylov_shapes<float2>(A, &sh.k);
   if (st != HELM_OK) return st;
   HELM_TRY(persistent_grid({reinterpret_cast<const void*>(&k_mx_init), reinterpret_cast<const void*>(&k_mx_residual),
-                            reinterpret_cast<const void*>(&k_mx_mr), reinterpret_cast<const void*>(&k_mx_tail)},
+                            reinterpret_cast<const void*>(&k_gcr_project), reinterpret_cast<const void*>(&k_mx_tail)},
                            R128, kSmem128, A->num_sms,
                            (static_cast<int64_t>(A->n) + Engine<double2>::R - 1) / Engine<double2>::R, &sh.grid128));
+  // partials buffer: num_sms * 32 * 8 doubles (api.cu)
+  sh.grid_proj = std::min(sh.grid128, A->num_sms * 32 * 8 / (2 * kGcr));
   sh.vec_grid = A->vec_grid;
   const int32_t n = A->n;
   const size_t N = static_cast<size_t>(n);
@@ -382,6 +507,11 @@ helm_status solve_mixed(helm_csr A, const double2* b, double2* x, const helm_opt
   a.x = x;
   a.r64 = A->vec;
   a.d64 = A->vec + N;
+  a.w64 = A->vec + 2 * N;
+  for (int j = 0; j < kGcr; ++j) {
+    a.Cw[j] = A->vec + (3 + j) * N;
+    a.Zw[j] = A->vec + (3 + kGcr + j) * N;
+  }
   a.x32 = k.x;
   a.r32 = k.r;
   a.rh32 = k.rh;
