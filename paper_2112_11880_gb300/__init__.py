@@ -331,8 +331,10 @@ class Sweep:
     def solve(self, omegas, b, X=None, **opts):
         import torch
         F = len(omegas)
+        _check_vector(b, self.n, torch.complex128, "b", None if b.dim() == 1 else F)
         if X is None:
             X = torch.zeros((self.n, F), dtype=torch.complex128, device=b.device)
+        _check_vector(X, self.n, torch.complex128, "X", F)
         infos = helm_sweep_solve(self.handle, omegas, b, X, default_opts(**opts))
         return X, infos
 
@@ -353,6 +355,19 @@ def helm_status_string(status: int) -> str:
 
 
 # ---------------------------------------------------------------- conveniences
+
+def _check_vector(t, n: int, dtype, name: str, cols: Optional[int] = None) -> None:
+    """Dtype and shape of a vector (cols None: n entries) or a row-major n x cols
+    block against the matrix it meets.  The C ABI takes bare device pointers and
+    cannot see a buffer that is too short, so the convenience layer checks."""
+    if t.dtype != dtype:
+        raise TypeError(f"{name}: expected {dtype}, got {t.dtype}")
+    if cols is None:
+        if t.numel() != n:
+            raise ValueError(f"{name}: expected {n} entries, got {t.numel()}")
+    elif tuple(t.shape) != (n, cols):
+        raise ValueError(f"{name}: expected shape ({n}, {cols}), got {tuple(t.shape)}")
+
 
 class CsrMatrix:
     """A CSR matrix on the GPU with its libhelm handle.  Holds references to
@@ -379,8 +394,10 @@ class CsrMatrix:
 
     def matvec(self, x, y=None, alpha=1.0, beta=0.0, stream=None):
         import torch
+        _check_vector(x, self.n, self.dtype, "x")
         if y is None:
             y = torch.empty_like(x)
+        _check_vector(y, self.n, self.dtype, "y")
         helm_spmv(self.handle, alpha, x, beta, y, stream)
         return y
 
@@ -399,7 +416,9 @@ class CsrMatrix:
 def solve(A: CsrMatrix, b, x=None, stream=None, **opts):
     """x = A^{-1} b with BiCGStab (default options of helm_opts_default)."""
     import torch
+    _check_vector(b, A.n, torch.complex128, "b")
     if x is None:
         x = torch.empty_like(b)
+    _check_vector(x, A.n, torch.complex128, "x")
     info = helm_bicgstab_solve(A.handle, b, x, default_opts(**opts), stream)
     return x, info

@@ -20,8 +20,8 @@ from __future__ import annotations
 
 import torch
 
-from . import (CsrMatrix, HelmError, default_opts, helm_adjoint, helm_assemble_helmholtz, helm_bicgstab_solve,
-               helm_conj_scale, helm_grad_sound_speed)
+from . import (CsrMatrix, HelmError, _check_vector, default_opts, helm_adjoint, helm_assemble_helmholtz,
+               helm_bicgstab_solve, helm_conj_scale, helm_grad_sound_speed)
 
 
 class HelmholtzFEM:
@@ -78,6 +78,7 @@ class AssembleHelmholtz(torch.autograd.Function):
 class SolveHelmholtz(torch.autograd.Function):
     @staticmethod
     def forward(ctx, vals, b, fem: HelmholtzFEM, opts=None):
+        _check_vector(b, fem.n, torch.complex128, "b")
         A = CsrMatrix(fem.rowptr, fem.colind, vals.detach().contiguous())
         u = torch.empty_like(b)
         o = opts if opts is not None else default_opts()

@@ -64,3 +64,33 @@ def test_product_package_does_not_reach_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".hpp", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in re.sub(r"#.*|//.*", "", txt).lower() or f.endswith(".md"), f
+
+
+def test_convenience_layer_checks_vectors_before_the_call():
+    """The C ABI takes bare device pointers, so a short or mistyped vector
+    would be read or written out of bounds on the device: the Python
+    convenience layer rejects it before anything reaches the library."""
+    torch = pytest.importorskip("torch")
+    import paper_2112_11880_gb300 as h
+    A = object.__new__(h.CsrMatrix)
+    A.n, A.dtype, A.handle = 5, torch.complex128, None
+    ok = torch.zeros(5, dtype=torch.complex128)
+    with pytest.raises(ValueError, match="expected 5 entries"):
+        h.solve(A, torch.zeros(4, dtype=torch.complex128))
+    with pytest.raises(TypeError, match="complex128"):
+        h.solve(A, torch.zeros(5, dtype=torch.complex64))
+    with pytest.raises(ValueError, match="x: expected 5 entries"):
+        h.solve(A, ok, x=torch.zeros(6, dtype=torch.complex128))
+    with pytest.raises(TypeError):
+        A.matvec(torch.zeros(5, dtype=torch.complex64))
+    with pytest.raises(ValueError, match="y: expected 5 entries"):
+        A.matvec(ok, torch.zeros(3, dtype=torch.complex128))
+    S = object.__new__(h.Sweep)
+    S.n, S.handle = 5, None
+    with pytest.raises(ValueError, match=r"b: expected shape \(5, 2\)"):
+        S.solve([1.0, 2.0], torch.zeros(5, 3, dtype=torch.complex128))
+    with pytest.raises(ValueError, match=r"X: expected shape \(5, 2\)"):
+        S.solve([1.0, 2.0], ok, X=torch.zeros(5, 3, dtype=torch.complex128))
+    with pytest.raises(ValueError, match="b: expected 5 entries"):
+        S.solve([1.0, 2.0], torch.zeros(4, dtype=torch.complex128))
+    h._check_vector(torch.zeros(5, 2, dtype=torch.complex128), 5, torch.complex128, "X", 2)
