@@ -427,6 +427,25 @@ def test_tfqmr_matches_dense_lu_and_degenerate_cases():
     assert oracle.tfqmr(p.rowptr, p.colind, vals, bad)[1]["status"] == "nonfinite"
 
 
+@pytest.mark.parametrize("k", [2, 3, 4])
+def test_krylov_methods_terminate_in_the_number_of_distinct_eigenvalues(k):
+    """With k distinct eigenvalues the Krylov space of b has dimension k, so
+    the BiCG process underneath all three methods ends after k steps: TFQMR
+    (k CGS steps, two quasi-minimal-residual half-steps each) within k
+    iterations, BiCGStab(l) (l BiCG steps per cycle) within ceil(k/l) cycles.
+    A wrong coefficient or index in either recurrence delays that."""
+    d = np.array([1.0, 2.0 + 1j, 3.0 - 2j, 0.5 + 0.5j][:k] * 5)
+    rp, ci, v = _csr_diag(d)
+    b = g.complex_vector(d.size, 8)
+    x, info = oracle.tfqmr(rp, ci, v, b, tol=1e-12)
+    assert info["status"] == "ok" and info["iters"] <= k
+    assert np.allclose(x, b / d, rtol=1e-12, atol=0)
+    for ell in (1, 2, 4):
+        x, info = oracle.bicgstabl(rp, ci, v, b, ell=ell, tol=1e-12)
+        assert info["status"] == "ok" and info["iters"] <= -(-k // ell), ell
+        assert np.allclose(x, b / d, rtol=1e-12, atol=0)
+
+
 # ---------------------------------------------------------------- BiCGStab(l)
 
 @pytest.mark.parametrize("ell", [1, 2, 4, 8])
