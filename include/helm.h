@@ -223,7 +223,9 @@ typedef struct {
   int32_t iters;        /* iterations performed (all restarts / refinement
                            steps included; for mixed precision, inner
                            iterations) */
-  int32_t restarts;     /* restarts (BiCGStab) or FP64 refinement steps (mixed) */
+  int32_t restarts;     /* restarts from the current x (BiCGStab, TFQMR; 0 for
+                           BiCGStab(l) and the sweep) or FP64 refinement
+                           steps (mixed) */
   double relres_recur;  /* last recurrence residual / ||b|| */
   double relres_true;   /* ||b - A x|| / ||b|| recomputed in FP64 at the end */
   helm_status status;
