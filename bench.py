@@ -396,6 +396,64 @@ def run_spmv_only(args):
     A.close()
 
 
+# Vector lengths of the paper's BLAS-1 measurements (Section 3, Tables 2-7):
+# the order of Audi3D-4 and three larger sizes.
+VECTOR_SIZES = (648_849, 2_000_000, 9_000_000, 14_000_000)
+
+
+def run_vectors(args):
+    """The BLAS-1 operations of Section 3 alone, through the C ABI, on
+    complex128 vectors of the paper's lengths: assign (y = x, Table 2), scal
+    (y = beta y, Table 3), axpy (y = alpha x + y, Table 4), zdotc (Tables 5-6)
+    and the 2-norm (Table 7).  Every launch is timed alone with CUDA events
+    after a 256 MB write that evicts the vectors from L2; the median launch
+    gives GB/s on the algorithmic bytes (each vector read or written once).
+    One JSON line per length."""
+    import torch
+
+    import paper_2112_11880_gb300 as helm
+    from paper_2112_11880_gb300 import build as hbuild
+    hbuild.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    peaks, peak_src = load_peaks()
+    peak = float(peaks["hbm_gbs"])
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB, above L2
+    out_c = torch.zeros(1, dtype=torch.complex128, device=dev)
+    out_r = torch.zeros(1, dtype=torch.float64, device=dev)
+    for n in VECTOR_SIZES:
+        x = torch.as_tensor(helmgen.complex_vector(n, 4), device=dev)
+        y = torch.as_tensor(helmgen.complex_vector(n, 5), device=dev)
+        # name -> (call, algorithmic bytes); |beta| = 1 in scal keeps y's scale
+        ops = {
+            "assign": (lambda: helm.helm_axpby(1.0, x, 0.0, y), 32 * n),
+            "scal": (lambda: helm.helm_axpby(0.0, None, 0.6 + 0.8j, y), 32 * n),
+            "axpy": (lambda: helm.helm_axpby(0.3 - 0.1j, x, 1.0, y), 48 * n),
+            "zdotc": (lambda: helm.helm_dot(x, y, out_c), 32 * n),
+            "nrm2": (lambda: helm.helm_nrm2(x, out_r), 16 * n),
+        }
+        res = {}
+        for name, (fn, nbytes) in ops.items():
+            for _ in range(args.warmup):
+                fn()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.reps)]
+            torch.cuda.synchronize()
+            for e0, e1 in ev:
+                flush.zero_()
+                e0.record()
+                fn()
+                e1.record()
+            torch.cuda.synchronize()
+            us = statistics.median(e0.elapsed_time(e1) for e0, e1 in ev) * 1e3
+            gbs = nbytes / us / 1e3
+            res[name] = {"us": round(us, 2), "gbs": round(gbs, 1), "frac": round(gbs / peak, 3)}
+        print(json.dumps({"mode": "vectors", "n": n, "dtype": "c128", "ops": res, "peak_gbs": peak,
+                          "peak_source": peak_src, "reps": args.reps, "warmup": args.warmup,
+                          "l2": "256 MB write before every launch"}), flush=True)
+        del x, y
+
+
 def run_extensions(args):
     """Throughput of the three extensions against plain FP64 solves on the same
     GPU (one JSON line): the 64-frequency sweep on the 60x30x25 cavity, mixed
@@ -558,8 +616,9 @@ def main():
     ap.add_argument("--ref-iters-per-solve", type=int, default=int(os.environ.get("HELM_ITERS_PER_SOLVE", "0")) or 0)
     ap.add_argument("--mixed-maxit", type=int, default=200000)
     ap.add_argument("--inner-tol", type=float, default=1e-3)
-    ap.add_argument("--mode", default="bench", choices=["bench", "spmv", "extensions"],
-                    help="spmv: only the complex128 SpMV loop on the same matrix (profiling target)")
+    ap.add_argument("--mode", default="bench", choices=["bench", "spmv", "extensions", "vectors"],
+                    help="spmv: only the complex128 SpMV loop on the same matrix (profiling target); "
+                         "vectors: the BLAS-1 operations alone at the paper's vector lengths")
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--launch", default="graph", choices=["graph", "host"],
                     help="host: drive the iteration loop from the host (same kernels; for profilers that "
@@ -569,6 +628,8 @@ def main():
         run_spmv_only(args)
     elif args.mode == "extensions":
         run_extensions(args)
+    elif args.mode == "vectors":
+        run_vectors(args)
     elif args.impl == "reference":
         if not args.ref_iters_per_solve:
             args.ref_iters_per_solve = REF_ITERS_PER_SOLVE
