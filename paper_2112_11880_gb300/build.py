@@ -2,7 +2,7 @@
 
 Each .cu file is one translation unit compiled in parallel; the objects are
 linked into paper_2112_11880_gb300/lib/libhelm.so (CUDA runtime linked
-statically, so the library needs only the driver).
+statically, so the library needs only libcuda, the CUDA driver library).
 """
 from __future__ import annotations
 

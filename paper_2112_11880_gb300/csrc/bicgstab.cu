@@ -1,4 +1,4 @@
-// Complex128 BiCGStab driver (Section 4 of the paper: P-BiCGSTAB, residual
+// Complex128 BiCGStab solver (Section 4 of the paper: P-BiCGSTAB, residual
 // tolerance, zero initial guess, iteration cap; identity preconditioner).
 // The kernels are the precision-generic ones of krylov.cuh instantiated for
 // complex128; this file adds the true-residual tail, the graph cache and the
