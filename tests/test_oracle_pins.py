@@ -446,6 +446,27 @@ def test_krylov_methods_terminate_in_the_number_of_distinct_eigenvalues(k):
         assert np.allclose(x, b / d, rtol=1e-12, atol=0)
 
 
+def test_tfqmr_reports_ok_only_with_the_true_residual_below_tol():
+    """TFQMR's stop test is a bound on the residual; near rounding level the
+    recurrence drifts from b - A x, so the bound can pass while the true
+    residual has not.  The oracle then checks the true residual and restarts
+    from the current x: ok is reported only when b - A x itself meets tol
+    (at 3e-16 the 8x6x5 mesh needs restarts to get there)."""
+    cases = 0
+    for dims, F in (((8, 6, 5), 700.0), ((9, 7, 6), 900.0)):
+        p = g.assemble(g.tiny_config(*dims, h=0.1, F=F, seed=2))
+        vals = g.helmholtz_values(p, F)
+        b = g.source(p) + 0.1 * g.complex_vector(p.n, 4) * (~p.dirichlet)
+        for tol in (1e-13, 1e-15, 3e-16):
+            x, info = oracle.tfqmr(p.rowptr, p.colind, vals, b, tol=tol, maxit=3000)
+            r = np.linalg.norm(b - oracle.spmv(p.rowptr, p.colind, vals, x)) / np.linalg.norm(b)
+            assert abs(r - info["relres_true"]) <= 1e-3 * r
+            if info["status"] == "ok":
+                assert info["relres_true"] <= tol, (p.n, tol, info)
+                cases += 1
+    assert cases >= 5
+
+
 # ---------------------------------------------------------------- BiCGStab(l)
 
 @pytest.mark.parametrize("ell", [1, 2, 4, 8])
