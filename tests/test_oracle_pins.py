@@ -451,7 +451,7 @@ def test_tfqmr_reports_ok_only_with_the_true_residual_below_tol():
     recurrence drifts from b - A x, so the bound can pass while the true
     residual has not.  The oracle then checks the true residual and restarts
     from the current x: ok is reported only when b - A x itself meets tol
-    (at 3e-16 the 8x6x5 mesh needs restarts to get there)."""
+    (on these meshes the bound passes first from tol = 1e-15 down)."""
     cases = 0
     for dims, F in (((8, 6, 5), 700.0), ((9, 7, 6), 900.0)):
         p = g.assemble(g.tiny_config(*dims, h=0.1, F=F, seed=2))
