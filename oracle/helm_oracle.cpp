@@ -89,8 +89,9 @@ struct Csr {
 // the "P-BiCGSTAB" of Section 4 with the identity as preconditioner.  Complex
 // version with conjugated inner products.  Stopping rule (Section 4): the
 // recurrence residual ||r|| / ||b|| <= tol, at most maxit iterations.  After
-// the loop the true residual b - A x is recomputed; if it exceeds 1.5 tol while
-// iterations remain, the method restarts from the current x.
+// the loop the true residual b - A x is recomputed; if it exceeds tol while
+// iterations remain, the method restarts from the current x, and the solve
+// reports ok only with a true residual at most tol.
 //
 // Breakdown (this project's reading; the paper is silent): rho == 0,
 // (r^, v) == 0, (t, t) == 0 or omega == 0 exactly, or any non-finite scalar.
@@ -164,7 +165,8 @@ int bicgstab(const Csr& A, const cplx* b, cplx* x, double tol, int32_t maxit, in
     for (int32_t i = 0; i < n; ++i) tmp[i] = b[i] - tmp[i];
     const double rtrue = dznrm2(n, tmp.data()) / bnorm;
     *relres_true_out = rtrue;
-    if (status == ST_OK && rtrue > 1.5 * tol && it < maxit) { status = ST_NOT_CONVERGED; continue; }
+    if (status == ST_OK && rtrue > tol && it < maxit) { status = ST_NOT_CONVERGED; continue; }
+    if (status == ST_OK && rtrue > tol) status = ST_NOT_CONVERGED;
     break;
   }
   *iters_out = it;
@@ -285,8 +287,8 @@ int tfqmr(const Csr& A, const cplx* b, cplx* x, double tol, int32_t maxit, int u
 // One iteration = one outer cycle = 2 l products with A.  Stop when the
 // recurrence residual ||r_0|| / ||b|| <= tol, tested after each BiCG step and
 // after the minimal-residual step; the true residual is then recomputed and,
-// as for BiCGStab, the method restarts from x if it exceeds 1.5 tol while
-// iterations remain.  Breakdown: rho0, gamma or sigma_j exactly 0, or a
+// as for BiCGStab, the method restarts from x if it exceeds tol while
+// iterations remain, and reports ok only with a true residual at most tol.  Breakdown: rho0, gamma or sigma_j exactly 0, or a
 // non-finite scalar.
 int bicgstabl(const Csr& A, const cplx* b, cplx* x, int ell, double tol, int32_t maxit, int use_x0,
               int32_t* iters_out, double* relres_recur_out, double* relres_true_out) {
@@ -389,7 +391,8 @@ int bicgstabl(const Csr& A, const cplx* b, cplx* x, int ell, double tol, int32_t
   for (int32_t i = 0; i < n; ++i) tmp[i] = b[i] - tmp[i];
   const double rtrue = dznrm2(n, tmp.data()) / bnorm;
   *relres_true_out = rtrue;
-  if (status == ST_OK && rtrue > 1.5 * tol && it < maxit) { status = ST_NOT_CONVERGED; continue; }
+  if (status == ST_OK && rtrue > tol && it < maxit) { status = ST_NOT_CONVERGED; continue; }
+  if (status == ST_OK && rtrue > tol) status = ST_NOT_CONVERGED;
   break;
   }
   *iters_out = it;

@@ -467,6 +467,34 @@ def test_tfqmr_reports_ok_only_with_the_true_residual_below_tol():
     assert cases >= 5
 
 
+@pytest.mark.parametrize("method", ["bicgstab", "bicgstabl"])
+def test_bicgstab_reports_ok_only_with_the_true_residual_below_tol(method):
+    """One acceptance rule for every method: near rounding level the
+    BiCGStab recurrence drifts from b - A x, so its residual can pass tol
+    while the true residual has not; the oracle then restarts from the current
+    x, and reports ok only when b - A x itself, recomputed here with the plain
+    SpMV, meets tol.  An oracle that accepted up to 1.5 tol (or took the
+    recurrence's word) fails the assertion on these meshes."""
+    cases = 0
+    for dims, F in (((8, 6, 5), 700.0), ((9, 7, 6), 900.0)):
+        p = g.assemble(g.tiny_config(*dims, h=0.1, F=F, seed=2))
+        vals = g.helmholtz_values(p, F)
+        b = g.source(p) + 0.1 * g.complex_vector(p.n, 4) * (~p.dirichlet)
+        for tol in (1e-13, 1e-15, 3e-16):
+            if method == "bicgstab":
+                x, info = oracle.bicgstab(p.rowptr, p.colind, vals, b, tol=tol, maxit=3000)
+            else:
+                x, info = oracle.bicgstabl(p.rowptr, p.colind, vals, b, ell=2, tol=tol, maxit=1500)
+            r = np.linalg.norm(b - oracle.spmv(p.rowptr, p.colind, vals, x)) / np.linalg.norm(b)
+            assert abs(r - info["relres_true"]) <= 1e-3 * r
+            if info["status"] == "ok":
+                assert r <= tol * (1 + 1e-3), (p.n, tol, info)
+                cases += 1
+            else:
+                assert info["status"] == "not_converged" and info["relres_true"] > tol
+    assert cases >= 3
+
+
 # ---------------------------------------------------------------- BiCGStab(l)
 
 @pytest.mark.parametrize("ell", [1, 2, 4, 8])
