@@ -201,7 +201,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     ms = barrier_max(ms, ws)
-    ok = all(i["status"] == "ok" and i["relres_true"] <= 1.5 * cfg.tol for i in infos)
+    ok = all(i["status"] == "ok" and i["relres_true"] <= cfg.tol for i in infos)
     iters = [i["iters"] for i in infos]
     # per launch of the loop: configure, init, tail; the 5 kernels of an
     # iteration run in passes of 4 iterations (graph) or 16 (host-driven loop),
@@ -249,7 +249,7 @@ def run_gpu(args):
     roofline = {"bound": "hbm", "achieved": round(spmv_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(spmv_gbs / hbm_peak, 4), "traffic": traffic,
                 "peak_src": f"{peak_src} (MEASURED_PEAKS hbm_gbs)" if peak_src == "measured" else "fallback",
-                "kernel": "k_spmv<double2>: complex128 CSR SpMV, TMA-staged 32-row tiles",
+                "kernel": "k_spmv<double2>: complex128 CSR SpMV on the handle's sliced-ELLPACK copy (SELL-32)",
                 "launch_ms": round(spmv_ms, 5), "alg_bytes_per_launch": spmv_bytes,
                 "alu": {"fp64_tflops_issued": round(fp64_tflops, 4), "peak": FP64_PEAK_TFLOPS,
                         "frac": round(fp64_tflops / FP64_PEAK_TFLOPS, 4),

@@ -26,8 +26,10 @@
  *   - `stream` is a cudaStream_t (0 = legacy default stream).  Kernels are
  *     enqueued on it; calls documented as asynchronous return after enqueueing
  *     and report launch errors only.
- *   - Every call returns a helm_status; nothing aborts, traps or prints.
- *     Invalid arguments are detected on the host before any work is enqueued.
+ *   - Every call returns a helm_status; nothing aborts or traps.  Nothing
+ *     prints unless the environment variable HELM_DEBUG is set: then a
+ *     failing CUDA call is reported on stderr.  Invalid arguments are
+ *     detected on the host before any work is enqueued.
  */
 #ifndef HELM_H
 #define HELM_H
@@ -71,14 +73,19 @@ typedef struct helm_csr_s* helm_csr; /* opaque CSR handle */
  *   flags    : HELM_CSR_VALIDATE or 0.
  * Ownership: the handle keeps the three device pointers (no copy); they must
  * stay valid and unchanged until helm_csr_destroy.  What it derives from them
- * is its own: per-32-row "all entries real" flags and the real parts of the
- * values (here), the complex64 and right-Jacobi copies (at the first solve
- * that needs them).
- * Work done: row statistics and the choice of SpMV variant (one device pass),
- * workspace allocation.  Synchronises `stream` once.  Returns
- * HELM_ERR_INVALID on bad sizes, a misaligned pointer, or (with
- * HELM_CSR_VALIDATE) a malformed pattern; HELM_ERR_NOMEM if the workspace
- * cannot be allocated.
+ * is its own: a sliced-ELLPACK copy of the matrix (slices of 32 rows, entry k
+ * of each row at a stride of 32: the columns, the real parts of the values
+ * and, separately, the entries with a nonzero imaginary part; about 12 bytes
+ * per stored entry for complex128), and the complex64 and right-Jacobi copies
+ * (at the first solve that needs them).
+ * Work done: row statistics, the sliced copy, workspace allocation, and the
+ * choice of SpMV variant: for nnz >= 2^18 the stand-alone SpMV's variants
+ * are timed on this matrix and the fastest is kept (every variant gives the
+ * same y bit for bit).  Synchronises `stream`.  Returns
+ * HELM_ERR_INVALID on bad sizes, a misaligned pointer, (with
+ * HELM_CSR_VALIDATE) a malformed pattern, or when the padded sliced copy
+ * would hold 2^31 entries or more; HELM_ERR_NOMEM if the workspace cannot be
+ * allocated.
  */
 helm_status helm_csr_create(helm_csr* out, int32_t n, int64_t nnz, const int32_t* d_rowptr,
                             const int32_t* d_colind, const void* d_vals, helm_dtype dt,
@@ -182,7 +189,14 @@ typedef enum {
                                  cannot be built */
   HELM_LAUNCH_GRAPH = 1,      /* CUDA graph with a device-driven while node;
                                  HELM_ERR_CUDA if it cannot be built */
-  HELM_LAUNCH_PERSISTENT = 2, /* reserved: runs as HELM_LAUNCH_AUTO */
+  HELM_LAUNCH_PERSISTENT = 2, /* FP64 BiCGStab only (HELM_ERR_INVALID for
+                                 the other methods and mixed precision): the
+                                 whole solve, restarts included, is one
+                                 cooperative kernel whose phases are separated
+                                 by grid barriers; the same arithmetic as the
+                                 graph, bit for bit.  Every barrier wait gives
+                                 up after 2 s (HELM_ERR_CUDA).  HELM_ERR_CUDA
+                                 if the device cannot launch it */
   HELM_LAUNCH_HOST = 3        /* host-driven loop of the same kernels, state
                                  polled every 16 iterations (profiling: tools
                                  that cannot see inside conditional graphs) */
@@ -203,7 +217,13 @@ typedef enum {
 } helm_precond;
 
 typedef struct {
-  double tol;          /* target ||b - A x|| / ||b|| (Section 4 uses 1e-9) */
+  double tol;          /* target ||b - A x|| / ||b|| (Section 4 uses 1e-9).
+                          Every method reports HELM_OK only when this ratio,
+                          recomputed in FP64 from x after the loop, is at
+                          most tol; when the recurrence met tol but the
+                          recomputed residual did not, the solve restarts
+                          from the current x while iterations remain
+                          (BiCGStab, BiCGStab(l), TFQMR) */
   int32_t maxit;       /* iteration cap (Section 4 uses 1000); each BiCGStab
                           or TFQMR iteration applies A twice */
   int32_t use_x0;      /* 0: start from x = 0 (Section 4); 1: start from d_x */

@@ -4,6 +4,8 @@
 // SpMV these calls provide; Section 2 fixes CSR as the storage.  Argument
 // checks happen on the host before anything is enqueued; no call aborts.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -12,6 +14,7 @@
 
 #include "common.cuh"
 #include "internal.hpp"
+#include "krylov.cuh"
 #include "spmv.cuh"
 
 namespace helm {
@@ -38,37 +41,96 @@ struct AxpbyEpi {
   }
 };
 
-template <class V>
-__global__ void __launch_bounds__(Engine<V>::kThreads) k_spmv(CsrDev<V> A, const V* __restrict__ x, V* y, V alpha, V beta,
-                                                       int mode, unsigned int* dev_err) {
-  extern __shared__ __align__(16) unsigned char smem[];
+// Stand-alone SpMV: y = alpha A x (+ beta y).  U = entries per pipeline
+// stage of the SELL engine; the variant (U and blocks per SM) is chosen per
+// matrix at handle creation (autotune_spmv).
+template <class V, int U>
+__global__ void __launch_bounds__(Engine<V>::kThreads, Engine<V>::kMinBlocks) k_spmv(CsrDev<V> A, const V* __restrict__ x, V* y, V alpha,
+                                                              V beta, int mode) {
   AxpbyEpi<V> epi{y, alpha, beta, mode, vzero<V>()};
-  (void)spmv_run<V>(A, x, epi, smem, dev_err);
+  (void)spmv_run<V, AxpbyEpi<V>, NoGate, GatherReadOnly, U>(A, x, epi, nullptr, nullptr);
 }
 
-// real_blk[b] = 1 when every entry of rows [32 b, 32 b + 32) is real.
-template <class V>
-__global__ void k_real_blocks(int32_t n, const int32_t* __restrict__ rowptr, const V* __restrict__ vals,
-                              uint8_t* __restrict__ real_blk) {
-  const int32_t nblk = (n + 31) / 32;
-  for (int32_t blk = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); blk < nblk;
-       blk += gridDim.x * (blockDim.x / 32)) {
-    const int32_t r0 = blk * 32, r1 = min(r0 + 32, n);
-    const int64_t k0 = rowptr[r0], k1 = rowptr[r1];
-    bool real = true;
-    for (int64_t k = k0 + (threadIdx.x & 31); k < k1; k += 32)
-      if (vals[k].y != 0) real = false;
-    real = __all_sync(0xffffffffu, real);
-    if ((threadIdx.x & 31) == 0) real_blk[blk] = real ? 1 : 0;
+// ---------------------------------------------------------------- SELL-32 layout
+
+// Slice widths: w[s] = longest row of rows [32 s, 32 s + 32).
+__global__ void k_sell_widths(int32_t n, int32_t nsl, const int32_t* __restrict__ rowptr, int32_t* __restrict__ w) {
+  const int lane = threadIdx.x & 31;
+  for (int32_t s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < nsl; s += (gridDim.x * blockDim.x) >> 5) {
+    const int32_t r = s * 32 + lane;
+    const int32_t len = r < n ? rowptr[r + 1] - rowptr[r] : 0;
+    const int32_t m = __reduce_max_sync(0xffffffffu, len);
+    if (lane == 0) w[s] = m;
   }
 }
 
-// vals_re[k] = Re vals[k]
+// Imaginary entries per row (ilen) and per-slice maxima (iw).
+template <class V>
+__global__ void k_sell_imag_counts(int32_t n, int32_t nsl, const int32_t* __restrict__ rowptr,
+                                   const V* __restrict__ vals, int32_t* __restrict__ ilen, int32_t* __restrict__ iw) {
+  const int lane = threadIdx.x & 31;
+  for (int32_t s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < nsl; s += (gridDim.x * blockDim.x) >> 5) {
+    const int32_t r = s * 32 + lane;
+    int32_t c = 0;
+    if (r < n) {
+      for (int32_t k = rowptr[r]; k < rowptr[r + 1]; ++k) c += vals[k].y != 0 ? 1 : 0;
+      ilen[r] = c;
+    }
+    const int32_t m = __reduce_max_sync(0xffffffffu, c);
+    if (lane == 0) iw[s] = m;
+  }
+}
+
+// Columns in SELL order; padding entries take column 0 (never read).
+__global__ void k_sell_fill_cols(int32_t n, int32_t nsl, const int32_t* __restrict__ rowptr,
+                                 const int32_t* __restrict__ colind, const int32_t* __restrict__ soff,
+                                 int32_t* __restrict__ scol) {
+  for (int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; r < static_cast<int64_t>(nsl) * 32;
+       r += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int32_t s = static_cast<int32_t>(r >> 5), lane = static_cast<int32_t>(r & 31);
+    const int32_t w = (soff[s + 1] - soff[s]) >> 5;
+    const int32_t k0 = r < n ? rowptr[r] : 0;
+    const int32_t len = r < n ? rowptr[r + 1] - k0 : 0;
+    int32_t* out = scol + soff[s] + lane;
+    for (int32_t k = 0; k < w; ++k) out[k * 32] = k < len ? colind[k0 + k] : 0;
+  }
+}
+
+// Real parts in SELL order and the imaginary entries in their own SELL.
 template <class V, class R>
-__global__ void k_real_parts(int64_t nnz, const V* __restrict__ vals, R* __restrict__ vals_re) {
-  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < nnz;
-       k += static_cast<int64_t>(gridDim.x) * blockDim.x)
-    vals_re[k] = vals[k].x;
+__global__ void k_sell_fill_vals(int32_t n, int32_t nsl, const int32_t* __restrict__ rowptr,
+                                 const int32_t* __restrict__ colind, const V* __restrict__ vals,
+                                 const int32_t* __restrict__ soff, const int32_t* __restrict__ isoff,
+                                 R* __restrict__ sval, int32_t* __restrict__ icol, R* __restrict__ ival) {
+  for (int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; r < static_cast<int64_t>(nsl) * 32;
+       r += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int32_t s = static_cast<int32_t>(r >> 5), lane = static_cast<int32_t>(r & 31);
+    const int32_t w = (soff[s + 1] - soff[s]) >> 5;
+    const int32_t iw = (isoff[s + 1] - isoff[s]) >> 5;
+    const int32_t k0 = r < n ? rowptr[r] : 0;
+    const int32_t len = r < n ? rowptr[r + 1] - k0 : 0;
+    R* out = sval + soff[s] + lane;
+    R* iout = ival + isoff[s] + lane;
+    int32_t* ic = icol + isoff[s] + lane;
+    int32_t q = 0;
+    for (int32_t k = 0; k < w; ++k) {
+      R re = R(0);
+      if (k < len) {
+        const V a = vals[k0 + k];
+        re = a.x;
+        if (a.y != 0) {
+          iout[q * 32] = a.y;
+          ic[q * 32] = colind[k0 + k];
+          ++q;
+        }
+      }
+      out[k * 32] = re;
+    }
+    for (; q < iw; ++q) {
+      iout[q * 32] = R(0);
+      ic[q * 32] = 0;
+    }
+  }
 }
 
 // Right Jacobi: d_i = a_ii (1 when row i stores no nonzero diagonal),
@@ -89,13 +151,10 @@ __global__ void k_jac_diag(int32_t n, const int32_t* __restrict__ rowptr, const 
 }
 // A D^-1: entry k of row i is a_ik dinv_colind[k]
 __global__ void k_jac_scale(int64_t nnz, const int32_t* __restrict__ colind, const double2* __restrict__ vals,
-                            const double2* __restrict__ dinv, double2* __restrict__ out, double* __restrict__ out_re) {
+                            const double2* __restrict__ dinv, double2* __restrict__ out) {
   for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < nnz;
-       k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const double2 v = cmul(vals[k], dinv[colind[k]]);
-    out[k] = v;
-    out_re[k] = v.x;
-  }
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    out[k] = cmul(vals[k], dinv[colind[k]]);
 }
 // x_i <- s_i x_i
 __global__ void k_jac_apply(int32_t n, const double2* __restrict__ sc, double2* __restrict__ x) {
@@ -210,6 +269,11 @@ __global__ void k_c128_to_c64(int64_t n, const double2* __restrict__ a, float2* 
 
 // ---------------------------------------------------------------- host helpers
 
+void debug_cuda_error(cudaError_t e, const char* file, int line) {
+  static const bool on = std::getenv("HELM_DEBUG") != nullptr;
+  if (on) std::fprintf(stderr, "libhelm: %s:%d: %s\n", file, line, cudaGetErrorString(e));
+}
+
 std::mutex g_attr_mu;
 std::vector<std::pair<const void*, int>> g_attr_done;
 
@@ -245,49 +309,223 @@ bool is_zero(const double* z) { return z[0] == 0.0 && z[1] == 0.0; }
 bool is_one(const double* z) { return z[0] == 1.0 && z[1] == 0.0; }
 }  // namespace
 
-// Grid of the staged SpMV: all resident blocks, never more than there are
-// tiles.
+// ---------------------------------------------------------------- stand-alone SpMV
+
+// Variants of the stand-alone SpMV: U (entries per pipeline stage) x block
+// size (1024 threads, one block per SM, or 512 threads, two per SM).  Every
+// variant computes each row with the same operations in the same order, so
+// the choice changes the speed only, never a bit of y.
 template <class V>
-static helm_status spmv_grid(int32_t n, int* grid) {
-  constexpr int R = Engine<V>::R;
-  const void* fn = reinterpret_cast<const void*>(&k_spmv<V>);
-  HELM_CUDA_TRY(set_smem_attr(fn, Engine<V>::kSmem));
-  int per_sm = 0;
-  HELM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmv<V>, Engine<V>::kThreads, Engine<V>::kSmem));
-  per_sm = std::max(per_sm, 1);
-  const int ntiles = (n + R - 1) / R;
-  *grid = std::max(1, std::min(ntiles, per_sm * sm_count()));
+static void spmv_enqueue(int U, int grid, int threads, const CsrDev<V>& d, const V* x, V* y, V alpha, V beta,
+                         int mode, cudaStream_t s) {
+  if (U == 2)
+    k_spmv<V, 2><<<grid, threads, 0, s>>>(d, x, y, alpha, beta, mode);
+  else
+    k_spmv<V, 4><<<grid, threads, 0, s>>>(d, x, y, alpha, beta, mode);
+}
+
+// Blocks of `threads` that fit on one SM for variant U.
+template <class V>
+static helm_status spmv_occupancy(int U, int threads, int* per_sm) {
+  const void* fn = U == 2 ? reinterpret_cast<const void*>(&k_spmv<V, 2>) : reinterpret_cast<const void*>(&k_spmv<V, 4>);
+  HELM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, threads, 0));
   return HELM_OK;
+}
+
+// Autotuning (Section 3: the paper's SpMV is auto-tuned): time the variants
+// on the handle's own matrix (3 launches each after one warm-up, CUDA events
+// on `s`) and keep the fastest.  Matrices under 2^18 stored entries keep the
+// default (U = 4, 1024-thread blocks): their SpMV is launch-bound.
+template <class V>
+static helm_status autotune_spmv(helm_csr A, const CsrDev<V>& d, cudaStream_t s) {
+  struct Cand {
+    int U, threads, bps;
+    bool full;
+  };
+  const Cand cand[5] = {{4, 1024, 1, false}, {4, 1024, 1, true}, {2, 1024, 1, false}, {4, 512, 2, false},
+                        {2, 512, 2, false}};
+  const SliceShape s0 = slice_shape(A->n, A->num_sms, 1024, 1);
+  A->spmv_variant = 4;
+  A->spmv_grid = s0.grid;
+  A->spmv_threads = s0.threads;
+  if (A->nnz < (int64_t(1) << 18) || A->n == 0) return HELM_OK;
+  V *x = nullptr, *y = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  helm_status st = HELM_OK;
+  float best = 0.f;
+  do {
+    if (cudaMalloc(&x, sizeof(V) * static_cast<size_t>(A->n)) != cudaSuccess ||
+        cudaMalloc(&y, sizeof(V) * static_cast<size_t>(A->n)) != cudaSuccess) {
+      st = HELM_ERR_NOMEM;
+      break;
+    }
+    if (cudaMemsetAsync(x, 0, sizeof(V) * static_cast<size_t>(A->n), s) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+      st = HELM_ERR_CUDA;
+      break;
+    }
+    V one, zero;
+    one.x = 1;
+    one.y = 0;
+    zero.x = 0;
+    zero.y = 0;
+    for (const Cand& c : cand) {
+      int fit = 0;
+      if (spmv_occupancy<V>(c.U, c.threads, &fit) != HELM_OK || fit < c.bps) continue;
+      const SliceShape sh = slice_shape(A->n, A->num_sms, c.threads, c.bps, c.full);
+      spmv_enqueue<V>(c.U, sh.grid, sh.threads, d, x, y, one, zero, 0, s);
+      cudaEventRecord(e0, s);
+      for (int k = 0; k < 3; ++k) spmv_enqueue<V>(c.U, sh.grid, sh.threads, d, x, y, one, zero, 0, s);
+      cudaEventRecord(e1, s);
+      float ms = 0.f;
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        st = HELM_ERR_CUDA;
+        break;
+      }
+      if (std::getenv("HELM_DEBUG"))
+        std::fprintf(stderr, "libhelm: spmv variant U=%d grid=%d threads=%d: %.2f us\n", c.U, sh.grid, sh.threads,
+                     ms * 1e3f / 3);
+      if (best == 0.f || ms < best) {
+        best = ms;
+        A->spmv_variant = c.U;
+        A->spmv_grid = sh.grid;
+        A->spmv_threads = sh.threads;
+      }
+    }
+  } while (false);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(x);
+  cudaFree(y);
+  (void)cudaGetLastError();
+  return st;
+}
+
+template <class V>
+static int spmv_mode(V alpha, V beta) {
+  const bool a1 = alpha.x == 1 && alpha.y == 0, b0 = beta.x == 0 && beta.y == 0;
+  return (a1 && b0) ? 0 : (b0 ? 1 : 2);
 }
 
 helm_status launch_spmv128(helm_csr A, const double2* x, double2* y, double2 alpha, double2 beta,
                            cudaStream_t s) {
   if (A->n == 0) return HELM_OK;
-  int grid = 0;
-  helm_status st = spmv_grid<double2>(A->n, &grid);
-  if (st != HELM_OK) return st;
-  const int mode = (alpha.x == 1.0 && alpha.y == 0.0 && beta.x == 0.0 && beta.y == 0.0) ? 0
-                   : (beta.x == 0.0 && beta.y == 0.0)                                    ? 1
-                                                                                         : 2;
-  CsrDev<double2> d{A->n, A->nnz, A->rowptr, A->colind, static_cast<const double2*>(A->vals), A->real_blk, A->vals_re};
-  k_spmv<double2><<<grid, Engine<double2>::kThreads, Engine<double2>::kSmem, s>>>(d, x, y, alpha, beta, mode, A->dev_err);
+  const CsrDev<double2> d = csr_dev<double2>(A, static_cast<const double2*>(A->vals), A->sv);
+  spmv_enqueue<double2>(A->spmv_variant, A->spmv_grid, A->spmv_threads, d, x, y, alpha, beta, spmv_mode(alpha, beta), s);
   HELM_CUDA_TRY(cudaGetLastError());
   return HELM_OK;
 }
 
-helm_status launch_spmv64(helm_csr A, const float2* vals, const float2* x, float2* y, float2 alpha,
-                          float2 beta, cudaStream_t s) {
+helm_status launch_spmv64(helm_csr A, const float2* x, float2* y, float2 alpha, float2 beta, cudaStream_t s) {
   if (A->n == 0) return HELM_OK;
-  int grid = 0;
-  helm_status st = spmv_grid<float2>(A->n, &grid);
-  if (st != HELM_OK) return st;
-  const int mode = (alpha.x == 1.f && alpha.y == 0.f && beta.x == 0.f && beta.y == 0.f) ? 0
-                   : (beta.x == 0.f && beta.y == 0.f)                                    ? 1
-                                                                                         : 2;
-  CsrDev<float2> d{A->n, A->nnz, A->rowptr, A->colind, vals, A->real_blk, A->vals32_re};
-  k_spmv<float2><<<grid, Engine<float2>::kThreads, Engine<float2>::kSmem, s>>>(d, x, y, alpha, beta, mode, A->dev_err);
+  const CsrDev<float2> d = csr_dev<float2>(A, static_cast<const float2*>(A->vals), A->sv);
+  spmv_enqueue<float2>(A->spmv_variant, A->spmv_grid, A->spmv_threads, d, x, y, alpha, beta, spmv_mode(alpha, beta), s);
   HELM_CUDA_TRY(cudaGetLastError());
   return HELM_OK;
+}
+
+// ---------------------------------------------------------------- SELL build (host)
+
+// Exclusive prefix sum of 32 * widths into offsets (host); false when the
+// total does not fit int32.
+static bool widths_to_offsets(const std::vector<int32_t>& w, std::vector<int32_t>* off, int64_t* total) {
+  off->assign(w.size() + 1, 0);
+  int64_t acc = 0;
+  for (size_t s = 0; s < w.size(); ++s) {
+    (*off)[s] = static_cast<int32_t>(acc);
+    acc += 32 * static_cast<int64_t>(w[s]);
+    if (acc >= (int64_t(1) << 31)) return false;
+  }
+  (*off)[w.size()] = static_cast<int32_t>(acc);
+  *total = acc;
+  return true;
+}
+
+// The pattern: slice widths, offsets and columns.  Synchronises `s`.
+static helm_status build_sell_pattern(helm_csr A, cudaStream_t s) {
+  const int32_t n = A->n, nsl = (n + 31) / 32;
+  A->nsl = nsl;
+  std::vector<int32_t> w(nsl), off;
+  int32_t* d_w = nullptr;
+  if (nsl > 0) {
+    HELM_CUDA_TRY(cudaMalloc(&d_w, sizeof(int32_t) * nsl));
+    k_sell_widths<<<vec_grid_for(static_cast<int64_t>(nsl) * 32), 256, 0, s>>>(n, nsl, A->rowptr, d_w);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(w.data(), d_w, sizeof(int32_t) * nsl, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d_w);
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      return HELM_ERR_CUDA;
+    }
+  }
+  int64_t total = 0;
+  if (!widths_to_offsets(w, &off, &total)) return HELM_ERR_INVALID;  // padded entries >= 2^31
+  A->sell_entries = total;
+  HELM_CUDA_TRY(cudaMalloc(&A->sell_off, sizeof(int32_t) * (nsl + 1)));
+  HELM_CUDA_TRY(cudaMalloc(&A->sell_col, sizeof(int32_t) * static_cast<size_t>(std::max<int64_t>(total, 1))));
+  HELM_CUDA_TRY(cudaMemcpyAsync(A->sell_off, off.data(), sizeof(int32_t) * (nsl + 1), cudaMemcpyHostToDevice, s));
+  if (nsl > 0) {
+    k_sell_fill_cols<<<vec_grid_for(static_cast<int64_t>(nsl) * 32), 256, 0, s>>>(n, nsl, A->rowptr, A->colind,
+                                                                                   A->sell_off, A->sell_col);
+    HELM_CUDA_TRY(cudaGetLastError());
+  }
+  HELM_CUDA_TRY(cudaStreamSynchronize(s));  // `off` is a host buffer of this frame
+  return HELM_OK;
+}
+
+static void free_sell_vals(SellVals* v) {
+  cudaFree(v->sval);
+  cudaFree(v->isoff);
+  cudaFree(v->icol);
+  cudaFree(v->ival);
+  cudaFree(v->ilen);
+  *v = SellVals();
+}
+
+template <class V>
+static helm_status build_sell_vals_t(helm_csr A, const V* vals, SellVals* out, cudaStream_t s) {
+  using R = typename RealOf<V>::T;
+  const int32_t n = A->n, nsl = A->nsl;
+  const size_t N = static_cast<size_t>(std::max(n, 1));
+  std::vector<int32_t> iw(nsl), ioff;
+  HELM_CUDA_TRY(cudaMalloc(&out->ilen, sizeof(int32_t) * N));
+  HELM_CUDA_TRY(cudaMalloc(&out->sval, sizeof(R) * static_cast<size_t>(std::max<int64_t>(A->sell_entries, 1))));
+  HELM_CUDA_TRY(cudaMalloc(&out->isoff, sizeof(int32_t) * (nsl + 1)));
+  if (nsl > 0) {
+    int32_t* d_iw = nullptr;
+    HELM_CUDA_TRY(cudaMalloc(&d_iw, sizeof(int32_t) * nsl));
+    k_sell_imag_counts<V><<<vec_grid_for(static_cast<int64_t>(nsl) * 32), 256, 0, s>>>(n, nsl, A->rowptr, vals,
+                                                                                       out->ilen, d_iw);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(iw.data(), d_iw, sizeof(int32_t) * nsl, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d_iw);
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      return HELM_ERR_CUDA;
+    }
+  }
+  int64_t itotal = 0;
+  if (!widths_to_offsets(iw, &ioff, &itotal)) return HELM_ERR_INVALID;
+  HELM_CUDA_TRY(cudaMalloc(&out->icol, sizeof(int32_t) * static_cast<size_t>(std::max<int64_t>(itotal, 1))));
+  HELM_CUDA_TRY(cudaMalloc(&out->ival, sizeof(R) * static_cast<size_t>(std::max<int64_t>(itotal, 1))));
+  HELM_CUDA_TRY(cudaMemcpyAsync(out->isoff, ioff.data(), sizeof(int32_t) * (nsl + 1), cudaMemcpyHostToDevice, s));
+  if (nsl > 0) {
+    k_sell_fill_vals<V, R><<<vec_grid_for(static_cast<int64_t>(nsl) * 32), 256, 0, s>>>(
+        n, nsl, A->rowptr, A->colind, vals, A->sell_off, out->isoff, static_cast<R*>(out->sval), out->icol,
+        static_cast<R*>(out->ival));
+    HELM_CUDA_TRY(cudaGetLastError());
+  }
+  HELM_CUDA_TRY(cudaStreamSynchronize(s));  // `ioff` is a host buffer of this frame
+  return HELM_OK;
+}
+
+helm_status build_sell_vals(helm_csr A, const void* vals, helm_dtype dt, SellVals* out, cudaStream_t s) {
+  helm_status st = dt == HELM_C128 ? build_sell_vals_t<double2>(A, static_cast<const double2*>(vals), out, s)
+                                   : build_sell_vals_t<float2>(A, static_cast<const float2*>(vals), out, s);
+  if (st != HELM_OK) free_sell_vals(out);
+  return st;
 }
 
 // Graphs capture buffer addresses: drop them whenever a buffer is replaced.
@@ -330,14 +568,17 @@ helm_status ensure_vectors32(helm_csr A, int nvec) {
 helm_status ensure_vals32(helm_csr A, cudaStream_t s) {
   if (A->vals32) return HELM_OK;
   const size_t NNZ = static_cast<size_t>(std::max<int64_t>(A->nnz, 1));
-  HELM_CUDA_TRY(cudaMalloc(&A->vals32_re, sizeof(float) * NNZ));
   HELM_CUDA_TRY(cudaMalloc(&A->vals32, sizeof(float2) * NNZ));
   if (A->nnz) {
     k_c128_to_c64<<<vec_grid_for(A->nnz), 256, 0, s>>>(A->nnz, static_cast<const double2*>(A->vals), A->vals32);
-    k_real_parts<<<vec_grid_for(A->nnz), 256, 0, s>>>(A->nnz, static_cast<const float2*>(A->vals32), A->vals32_re);
     HELM_CUDA_TRY(cudaGetLastError());
   }
-  return HELM_OK;
+  helm_status st = build_sell_vals(A, A->vals32, HELM_C64, &A->sv32, s);
+  if (st != HELM_OK) {
+    cudaFree(A->vals32);
+    A->vals32 = nullptr;
+  }
+  return st;
 }
 
 }  // namespace helm
@@ -348,25 +589,24 @@ using namespace helm;
 
 namespace helm {
 helm_status ensure_jacobi(helm_csr A, cudaStream_t s) {
-  if (A->jac_vals) return HELM_OK;
+  if (A->svjac.sval) return HELM_OK;
   const int32_t n = A->n;
   const size_t N = static_cast<size_t>(n > 0 ? n : 1), NNZ = static_cast<size_t>(A->nnz > 0 ? A->nnz : 1);
-  HELM_CUDA_TRY(cudaMalloc(&A->jac_d, N * sizeof(double2)));
-  HELM_CUDA_TRY(cudaMalloc(&A->jac_dinv, N * sizeof(double2)));
-  HELM_CUDA_TRY(cudaMalloc(&A->jac_real_blk, (N + 31) / 32));
-  HELM_CUDA_TRY(cudaMalloc(&A->jac_vals_re, NNZ * sizeof(double)));
-  HELM_CUDA_TRY(cudaMalloc(&A->jac_vals, NNZ * sizeof(double2)));
+  if (!A->jac_d) HELM_CUDA_TRY(cudaMalloc(&A->jac_d, N * sizeof(double2)));
+  if (!A->jac_dinv) HELM_CUDA_TRY(cudaMalloc(&A->jac_dinv, N * sizeof(double2)));
+  if (!A->jac_vals) HELM_CUDA_TRY(cudaMalloc(&A->jac_vals, NNZ * sizeof(double2)));
   const double2* vals = static_cast<const double2*>(A->vals);
   k_jac_diag<<<vec_grid_for(n), 256, 0, s>>>(n, A->rowptr, A->colind, vals, A->jac_d, A->jac_dinv);
-  k_jac_scale<<<vec_grid_for(A->nnz), 256, 0, s>>>(A->nnz, A->colind, vals, A->jac_dinv, A->jac_vals, A->jac_vals_re);
-  if (n > 0) k_real_blocks<<<vec_grid_for(n / 32 + 1), 256, 0, s>>>(n, A->rowptr, static_cast<const double2*>(A->jac_vals), A->jac_real_blk);
+  k_jac_scale<<<vec_grid_for(A->nnz), 256, 0, s>>>(A->nnz, A->colind, vals, A->jac_dinv, A->jac_vals);
   HELM_CUDA_TRY(cudaGetLastError());
-  return HELM_OK;
+  return build_sell_vals(A, A->jac_vals, HELM_C128, &A->svjac, s);
 }
 }  // namespace helm
 
 static helm_status solve_dispatch(helm_csr A, const double2* b, double2* x, const helm_opts& opts, helm_info* info,
                                   cudaStream_t s) {
+  if (opts.launch == HELM_LAUNCH_PERSISTENT && (opts.method != HELM_BICGSTAB || opts.precision != HELM_PREC_FP64))
+    return HELM_ERR_INVALID;
   if (opts.precision == HELM_PREC_MIXED) {
     if (opts.method != HELM_BICGSTAB) return HELM_ERR_INVALID;
     return solve_mixed(A, b, x, opts, info, s);
@@ -477,30 +717,14 @@ helm_status helm_csr_create(helm_csr* out, int32_t n, int64_t nnz, const int32_t
   if (h_end[0] != 0 || h_end[1] != nnz || h_chk[1]) return fail(HELM_ERR_INVALID);
   A->max_row = h_chk[0];
   A->vec_grid = vec_grid_for(n);
-  helm_status st = dt == HELM_C128 ? spmv_grid<double2>(n, &A->spmv_grid) : spmv_grid<float2>(n, &A->spmv_grid);
+  // the SELL-32 copy the SpMV engine reads (columns, real parts, imaginary
+  // entries), then the stand-alone SpMV variant for this matrix
+  helm_status st = build_sell_pattern(A, s);
+  if (st == HELM_OK) st = build_sell_vals(A, d_vals, dt, &A->sv, s);
+  if (st == HELM_OK)
+    st = dt == HELM_C128 ? autotune_spmv<double2>(A, csr_dev<double2>(A, static_cast<const double2*>(d_vals), A->sv), s)
+                         : autotune_spmv<float2>(A, csr_dev<float2>(A, static_cast<const float2*>(d_vals), A->sv), s);
   if (st != HELM_OK) return fail(st);
-  if (n > 0) {
-    // row blocks with only real entries take the cheaper product, staged
-    // from their real parts (8 or 4 bytes per entry)
-    if (cudaMalloc(&A->real_blk, (n + 31) / 32) != cudaSuccess) return fail(HELM_ERR_NOMEM);
-    if (dt == HELM_C128)
-      k_real_blocks<<<vec_grid_for(n / 32 + 1), 256, 0, s>>>(n, d_rowptr, static_cast<const double2*>(d_vals), A->real_blk);
-    else
-      k_real_blocks<<<vec_grid_for(n / 32 + 1), 256, 0, s>>>(n, d_rowptr, static_cast<const float2*>(d_vals), A->real_blk);
-    if (cudaGetLastError() != cudaSuccess) return fail(HELM_ERR_CUDA);
-    if (nnz > 0) {
-      if (dt == HELM_C128) {
-        if (cudaMalloc(&A->vals_re, static_cast<size_t>(nnz) * sizeof(double)) != cudaSuccess)
-          return fail(HELM_ERR_NOMEM);
-        k_real_parts<<<vec_grid_for(nnz), 256, 0, s>>>(nnz, static_cast<const double2*>(d_vals), A->vals_re);
-      } else {
-        if (cudaMalloc(&A->vals32_re, static_cast<size_t>(nnz) * sizeof(float)) != cudaSuccess)
-          return fail(HELM_ERR_NOMEM);
-        k_real_parts<<<vec_grid_for(nnz), 256, 0, s>>>(nnz, static_cast<const float2*>(d_vals), A->vals32_re);
-      }
-      if (cudaGetLastError() != cudaSuccess) return fail(HELM_ERR_CUDA);
-    }
-  }
   *out = A;
   return HELM_OK;
 }
@@ -522,12 +746,12 @@ helm_status helm_csr_destroy(helm_csr A) {
   if (A->state_host) cudaFreeHost(A->state_host);
   cudaFree(A->vec);
   cudaFree(A->vals32);
-  cudaFree(A->real_blk);
-  cudaFree(A->vals_re);
-  cudaFree(A->vals32_re);
+  cudaFree(A->sell_off);
+  cudaFree(A->sell_col);
+  free_sell_vals(&A->sv);
+  free_sell_vals(&A->sv32);
+  free_sell_vals(&A->svjac);
   cudaFree(A->jac_vals);
-  cudaFree(A->jac_vals_re);
-  cudaFree(A->jac_real_blk);
   cudaFree(A->jac_d);
   cudaFree(A->jac_dinv);
   cudaFree(A->vec32);
@@ -549,7 +773,7 @@ helm_status helm_spmv(helm_csr A, const double* alpha, const void* d_x, const do
                           make_double2(alpha[0], alpha[1]), make_double2(beta[0], beta[1]), s);
   }
   if (!aligned(d_x, 8) || !aligned(d_y, 8)) return HELM_ERR_INVALID;
-  return launch_spmv64(A, static_cast<const float2*>(A->vals), static_cast<const float2*>(d_x),
+  return launch_spmv64(A, static_cast<const float2*>(d_x),
                        static_cast<float2*>(d_y), make_float2((float)alpha[0], (float)alpha[1]),
                        make_float2((float)beta[0], (float)beta[1]), s);
 }

@@ -63,7 +63,7 @@ __device__ __forceinline__ void bl_stop_test(SolverState* st, double r2) {
 
 // init: r_0 = b - A x (or b, x = 0), r~ = r_0, u_0 = 0; ||b||, ||r_0||;
 // rho0 = 1, alpha = 0, omega = 1; rho1 = (r~, r_0) for the first step
-__global__ void __launch_bounds__(RT) k_bl_init(BlArgs a) {
+__global__ void __launch_bounds__(RT, kSolverMinBlocks) k_bl_init(BlArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[32 * 4];
   SolverState* st = a.st;
@@ -149,9 +149,9 @@ __global__ void __launch_bounds__(256) k_bl_u(BlArgs a, int j) {
 }
 
 // B2: u_{j+1} = A u_j, gamma = (r~, u_{j+1}) -> alpha
-__global__ void __launch_bounds__(RT) k_bl_au(BlArgs a, int j) {
+__global__ void __launch_bounds__(RT, kSolverMinBlocks) k_bl_au(BlArgs a, int j) {
   extern __shared__ __align__(16) unsigned char smem[];
-  double* red = reinterpret_cast<double*>(smem);  // the staging buffer, once the tiles are done
+  double* red = reinterpret_cast<double*>(smem);  // block-sum scratch (dynamic shared memory)
   SolverState* st = a.st;
   if (st->status != ST_RUNNING) return;
   struct Epi {
@@ -199,9 +199,9 @@ __global__ void __launch_bounds__(256) k_bl_r(BlArgs a, int j) {
 }
 
 // B4: r_{j+1} = A r_j, rho1 = (r~, r_{j+1})
-__global__ void __launch_bounds__(RT) k_bl_ar(BlArgs a, int j) {
+__global__ void __launch_bounds__(RT, kSolverMinBlocks) k_bl_ar(BlArgs a, int j) {
   extern __shared__ __align__(16) unsigned char smem[];
-  double* red = reinterpret_cast<double*>(smem);  // the staging buffer, once the tiles are done
+  double* red = reinterpret_cast<double*>(smem);  // block-sum scratch (dynamic shared memory)
   SolverState* st = a.st;
   if (st->status != ST_RUNNING) return;
   struct Epi {
@@ -385,7 +385,7 @@ __global__ void __launch_bounds__(256) k_bl_mr(BlArgs a) {
 }
 
 // tail: true residual (x = 0 when b = 0)
-__global__ void __launch_bounds__(RT) k_bl_tail(BlArgs a) {
+__global__ void __launch_bounds__(RT, kSolverMinBlocks) k_bl_tail(BlArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[32];
   SolverState* st = a.st;
@@ -516,32 +516,38 @@ helm_status bicgstabl_fp64(helm_csr A, const double2* b, double2* x, const helm_
 
   // an explicit graph request does not fall back to the host-driven loop
   if (!g && o.launch == HELM_LAUNCH_GRAPH) return HELM_ERR_CUDA;
-  k_configure<<<1, 1, 0, s>>>(A->state, o.tol, o.maxit, o.use_x0 ? 1 : 0, o.deadline_s, 1);
-  HELM_CUDA_TRY(cudaGetLastError());
   SolverState* hs = A->state_host;
-  if (g) {
-    HELM_CUDA_TRY(cudaGraphLaunch(g->exec, s));
-  } else {
-    k_bl_init<<<sh.init_grid, RT, kSmem, s>>>(a);
-    for (;;) {
-      for (int q = 0; q < 4; ++q) bl_body(a, sh, s);
-      HELM_CUDA_TRY(cudaGetLastError());
-      HELM_CUDA_TRY(cudaMemcpyAsync(hs, A->state, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
-      HELM_CUDA_TRY(cudaStreamSynchronize(s));
-      if (hs->status != ST_RUNNING) break;
+  HELM_CUDA_TRY(cudaMemsetAsync(A->dev_err, 0, sizeof(unsigned int), s));
+  // restart from x while the recurrence converged but the true residual did
+  // not (and iterations remain), as for BiCGStab
+  for (int32_t use_x0 = o.use_x0 ? 1 : 0, fresh = 1;; use_x0 = 1, fresh = 0) {
+    k_configure<<<1, 1, 0, s>>>(A->state, o.tol, o.maxit, use_x0, o.deadline_s, fresh);
+    HELM_CUDA_TRY(cudaGetLastError());
+    if (g) {
+      HELM_CUDA_TRY(cudaGraphLaunch(g->exec, s));
+    } else {
+      k_bl_init<<<sh.init_grid, RT, kSmem, s>>>(a);
+      for (;;) {
+        for (int q = 0; q < 4; ++q) bl_body(a, sh, s);
+        HELM_CUDA_TRY(cudaGetLastError());
+        HELM_CUDA_TRY(cudaMemcpyAsync(hs, A->state, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
+        HELM_CUDA_TRY(cudaStreamSynchronize(s));
+        if (hs->status != ST_RUNNING) break;
+      }
+      k_bl_tail<<<sh.init_grid, RT, kSmem, s>>>(a);
     }
-    k_bl_tail<<<sh.init_grid, RT, kSmem, s>>>(a);
+    unsigned int herr = 0;
+    HELM_CUDA_TRY(cudaMemcpyAsync(hs, A->state, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
+    HELM_CUDA_TRY(cudaMemcpyAsync(&herr, A->dev_err, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+    HELM_CUDA_TRY(cudaStreamSynchronize(s));
+    if (herr) return HELM_ERR_CUDA;
+    if (!(hs->status == HELM_OK && hs->relres_true > o.tol && hs->iter < o.maxit)) break;
   }
-  unsigned int herr = 0;
-  HELM_CUDA_TRY(cudaMemcpyAsync(hs, A->state, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
-  HELM_CUDA_TRY(cudaMemcpyAsync(&herr, A->dev_err, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
-  HELM_CUDA_TRY(cudaStreamSynchronize(s));
-  if (herr) return HELM_ERR_CUDA;
   helm_status result = hs->status == ST_RUNNING ? HELM_ERR_CUDA : static_cast<helm_status>(hs->status);
-  if (result == HELM_OK && !(hs->relres_true <= 1.5 * o.tol)) result = HELM_ERR_NOT_CONVERGED;
+  if (result == HELM_OK && !(hs->relres_true <= o.tol)) result = HELM_ERR_NOT_CONVERGED;
   if (info) {
     info->iters = hs->iter;
-    info->restarts = 0;
+    info->restarts = hs->restarts;
     info->relres_recur = hs->relres;
     info->relres_true = hs->relres_true;
     info->status = result;

@@ -1,7 +1,6 @@
 // Shared device helpers of libhelm: complex arithmetic on interleaved
-// (re, im) pairs, cache-hinted loads, deterministic block reductions, the
-// TMA bulk-copy / mbarrier primitives used to stage CSR tiles, and the
-// handle layout.
+// (re, im) pairs, cache-hinted loads, deterministic block reductions and the
+// device clock.
 //
 // FP64 on this GPU: the FP64 pipe retires about two FMA lanes per clock per
 // SM (about 1.2 TFLOP/s for the chip), 60x below FP32, and a warp
@@ -312,73 +311,14 @@ __device__ __forceinline__ bool grid_sum_last2(double (&v)[K], double* partials,
   return true;
 }
 
-// ---------------------------------------------------------------- dependent launch
-// Programmatic dependent launch: a kernel launched with programmatic stream
-// serialization may start while its predecessor finishes.  It may load data
-// that no kernel in flight writes before pdl_wait(); everything else (the
-// solver state, the predecessor's outputs, every store) comes after it.
-// pdl_wait() returns once the predecessor grid has completed and its memory
-// is visible (at once for a kernel launched the ordinary way).  A kernel lets
-// its own successor start only after its pdl_wait(), so that at a kernel's
-// start the kernel two launches back has completed.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_launch_dependents() {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
+// ---------------------------------------------------------------- timers
 
-// ---------------------------------------------------------------- TMA bulk copy
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-               : "memory");
-}
-// 1-D bulk copy global -> shared, completion counted on `bar` (bytes, 16-byte
-// multiple; both addresses 16-byte aligned).
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_addr(dst)),
-      "l"(src), "r"(bytes), "r"(smem_addr(bar))
-      : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
 __device__ __forceinline__ uint64_t globaltimer_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
   return t;
 }
-// Bounded wait on an mbarrier phase: gives up after `limit_ns` and returns
-// false.  No unbounded spin anywhere in the library.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = globaltimer_ns();
-  for (;;) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if (globaltimer_ns() - t0 > limit_ns) return false;
-  }
-}
-
 // Device error flags (bit set by a kernel that had to give up).
-enum : unsigned int { DEVERR_MBAR_TIMEOUT = 1u, DEVERR_BARRIER_TIMEOUT = 2u };
+enum : unsigned int { DEVERR_BARRIER_TIMEOUT = 2u };
 
 }  // namespace helm

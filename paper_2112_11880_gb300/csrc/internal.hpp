@@ -36,27 +36,23 @@ enum : int32_t { ST_RUNNING = -1, ST_RESTART = -2 };  // ST_RESTART: the host re
 enum : int32_t { PH_RUN = 0, PH_SCONV = 1, PH_DONE = 2 };
 
 // Tickets (arrival counters for last-block reductions), one per kernel kind.
-enum : int { TK_INIT = 0, TK_V, TK_S, TK_T, TK_XR, TK_TAIL, TK_AUX0, TK_AUX1, TK_AUX2, TK_AUX3, TK_COUNT };
+enum : int { TK_INIT = 0, TK_V, TK_S, TK_T, TK_XR, TK_TAIL, TK_AUX0, TK_AUX1, TK_AUX2, TK_AUX3,
+             TK_BAR_COUNT, TK_BAR_ABORT, TK_BAR_GEN,  // grid barrier of the persistent solver (count, abort adjacent)
+             TK_COUNT };
 // Group counters per two-level reduction (groups of blockDim blocks).
 constexpr int kGroupTickets = 256;
 
-// SpMV engine shape (measured on GB300, 120x60x50 Q1 matrix): 32-row tiles
-// of up to 28 entries per row staged by TMA bulk copies into a single buffer
-// per block; each row split over 2 threads in 2 different warps (64-thread
-// blocks overlapping one another; 4 warps per row measured the same speed
-// for the plain SpMV and costs 4 more FP64 adds per row).
-constexpr int kRows128 = 32;
-constexpr int kCap128 = kRows128 * 28;
-constexpr int kRows64 = 32;
-constexpr int kCap64 = kRows64 * 28;
-#ifndef HELM_STAGES
-#define HELM_STAGES 1
-#endif
-constexpr int kStages = HELM_STAGES;
-#ifndef HELM_SPLIT
-#define HELM_SPLIT 2
-#endif
-constexpr int kSplit = HELM_SPLIT;
+// Values of a matrix in the SELL-32 layout of the SpMV engine (spmv.cuh);
+// the slice offsets and columns are the handle's (shared by every value
+// array of one pattern).  Arrays are double for complex128 values, float for
+// complex64.
+struct SellVals {
+  void* sval = nullptr;      // real parts, [sell entries]
+  int32_t* isoff = nullptr;  // [nsl + 1] offsets of the imaginary slices
+  int32_t* icol = nullptr;   // columns of the imaginary entries
+  void* ival = nullptr;      // imaginary parts
+  int32_t* ilen = nullptr;   // [n] imaginary entries per row
+};
 
 // complex128 Krylov vectors per handle (BiCGStab uses 6, TFQMR 8)
 constexpr int kNumVec = 8;
@@ -80,7 +76,9 @@ struct helm_csr_s {
   int32_t max_row = 0;
 
   // launch shapes
-  int spmv_grid = 0;   // persistent grid of the staged SpMV kernels
+  int spmv_grid = 0;   // grid of the stand-alone SpMV (autotuned at creation)
+  int spmv_threads = 0;  // its block size
+  int spmv_variant = 0;  // its entries per pipeline stage (U), chosen at creation
   int vec_grid = 0;    // grid of element-wise kernels (256 threads)
 
   // workspace (owned)
@@ -93,14 +91,16 @@ struct helm_csr_s {
   double2* vec = nullptr;              // Krylov vectors, nvec * n complex128
   int nvec = 0;
   float2* vals32 = nullptr;            // complex64 copy for mixed precision
-  uint8_t* real_blk = nullptr;         // per 32-row block: all entries real
-  double* vals_re = nullptr;           // real parts of the complex128 values
-  float* vals32_re = nullptr;          // real parts of the complex64 values (own or vals32)
-  // right Jacobi (built at the first preconditioned solve): A D^-1 as
-  // values, real parts and real-block flags; D and D^-1
+  // SELL-32 copy of the pattern (spmv.cuh) and of each value array
+  int32_t nsl = 0;                     // slices of 32 rows
+  int64_t sell_entries = 0;            // stored entries including padding
+  int32_t* sell_off = nullptr;         // [nsl + 1]
+  int32_t* sell_col = nullptr;         // [sell_entries]
+  helm::SellVals sv;                   // the caller's values (complex128 or complex64)
+  helm::SellVals sv32;                 // the complex64 copy (mixed precision, complex128 handles)
+  helm::SellVals svjac;                // A D^-1 (right Jacobi)
+  // right Jacobi (built at the first preconditioned solve): A D^-1; D and D^-1
   double2* jac_vals = nullptr;
-  double* jac_vals_re = nullptr;
-  uint8_t* jac_real_blk = nullptr;
   double2* jac_d = nullptr;
   double2* jac_dinv = nullptr;
   float2* vec32 = nullptr;             // complex64 Krylov vectors
@@ -118,10 +118,15 @@ namespace helm {
     if (_s != HELM_OK) return _s;        \
   } while (0)
 
+// With the environment variable HELM_DEBUG set, a failing CUDA call is
+// reported on stderr (file, line, error string); otherwise nothing prints.
+void debug_cuda_error(cudaError_t e, const char* file, int line);
+
 #define HELM_CUDA_TRY(expr)                          \
   do {                                               \
     cudaError_t _e = (expr);                         \
     if (_e != cudaSuccess) {                         \
+      helm::debug_cuda_error(_e, __FILE__, __LINE__); \
       (void)cudaGetLastError();                      \
       return _e == cudaErrorMemoryAllocation ? HELM_ERR_NOMEM : HELM_ERR_CUDA; \
     }                                                \
@@ -139,11 +144,14 @@ helm_status ensure_vectors(helm_csr A, int nvec);
 helm_status ensure_vectors32(helm_csr A, int nvec);
 helm_status ensure_vals32(helm_csr A, cudaStream_t s);
 
+// SELL-32 values of one value array of the handle (api.cu); `vals` is
+// complex128 (dt = HELM_C128) or complex64.
+helm_status build_sell_vals(helm_csr A, const void* vals, helm_dtype dt, helm::SellVals* out, cudaStream_t s);
+
 // Launchers implemented in spmv_ops.cu (used by several solvers).
 helm_status launch_spmv128(helm_csr A, const double2* x, double2* y, double2 alpha, double2 beta,
                            cudaStream_t s);
-helm_status launch_spmv64(helm_csr A, const float2* vals, const float2* x, float2* y, float2 alpha,
-                          float2 beta, cudaStream_t s);
+helm_status launch_spmv64(helm_csr A, const float2* x, float2* y, float2 alpha, float2 beta, cudaStream_t s);
 
 // Solver entry points implemented in the solver translation units.
 // Graph-cache key of a solve: (b, x) tagged with the method and the

@@ -5,28 +5,35 @@
 // (right Jacobi runs the same kernels on A D^-1); the recurrence of van der
 // Vorst 1992 / Saad 2003 Algorithm 7.7 with conjugated inner products.
 //
-// One iteration is five kernels; each dot product the recurrence needs is
-// fused into the kernel that produces its operands, and the scalar it feeds
-// is formed in FP64 on the device by the last block to finish (ticket
-// counter):
-//   K1  p = r + beta (p - omega v)
-//   K2  v = A p          + (r^, v)        -> alpha = rho / (r^, v)
-//   K3  s = r - alpha v  + ||s||^2        -> stop at s if ||s|| / ||b|| <= tol
-//   K4  t = A s          + (t, s), ||t||^2 -> omega = (t, s) / (t, t)
-//   K5  x += alpha p + omega s, r = s - omega t + (r^, r), ||r||^2
+// One iteration is five phases; each dot product the recurrence needs is
+// fused into the phase that produces its operands, and the scalar it feeds
+// is formed in FP64 on the device:
+//   P1  p = r + beta (p - omega v)
+//   P2  v = A p          + (r^, v)        -> alpha = rho / (r^, v)
+//   P3  s = r - alpha v  + ||s||^2        -> stop at s if ||s|| / ||b|| <= tol
+//   P4  t = A s          + (t, s), ||t||^2 -> omega = (t, s) / (t, t)
+//   P5  x += alpha p + omega s, r = s - omega t + (r^, r), ||r||^2
 //                                         -> stop test, rho, beta
 // For complex64 the products and each thread's partial sums are FP32; block
 // and grid sums and every scalar of the recurrence are FP64.
 //
-// The loop runs inside one CUDA graph: an init kernel, a conditional WHILE
-// node whose body is four iterations of K1..K5 (K5's last block sets the
-// condition) and, for the FP64 solver, a tail kernel that recomputes the true
-// residual b - A x.
+// Two ways to run the loop, with the same arithmetic bit for bit:
+//   * graph: one kernel per phase; the last block to finish a phase (ticket
+//     counter) adds the block partials and forms the scalars; the loop is a
+//     CUDA graph with a conditional WHILE node (four iterations per pass);
+//   * persistent: one cooperative kernel for the whole solve; a grid barrier
+//     ends every phase, after which every block adds the block partials
+//     itself (same order, so the same scalars in every block) -- no kernel
+//     launches, no last-block step.
+// Both give each row to the same thread in every phase (SliceRows of the
+// SpMV engine) on the same grid, and add the same partials in the same order.
 #pragma once
 
+#include <algorithm>
 #include <cstring>
 #include <initializer_list>
 #include <utility>
+#include <vector>
 
 #include "common.cuh"
 #include "internal.hpp"
@@ -36,10 +43,8 @@ namespace helm {
 
 // The complex128 matrix a solve runs on: A, or A D^-1 under right Jacobi.
 inline CsrDev<double2> csr_for(helm_csr A, const helm_opts& o) {
-  if (o.precond == HELM_PRECOND_JACOBI)
-    return CsrDev<double2>{A->n, A->nnz, A->rowptr, A->colind, A->jac_vals, A->jac_real_blk, A->jac_vals_re};
-  return CsrDev<double2>{A->n, A->nnz, A->rowptr, A->colind, static_cast<const double2*>(A->vals), A->real_blk,
-                         A->vals_re};
+  if (o.precond == HELM_PRECOND_JACOBI) return csr_dev<double2>(A, A->jac_vals, A->svjac);
+  return csr_dev<double2>(A, static_cast<const double2*>(A->vals), A->sv);
 }
 
 // SolverState::method of the Krylov loop: plain, or the inner loop of the
@@ -54,16 +59,18 @@ constexpr int kInnerMax = 50000;  // inner iterations per refinement step at mos
 template <class V> struct Prec;
 template <> struct Prec<double2> {
   using S = double;
-  static constexpr int R = Engine<double2>::kThreads;  // threads per SpMV block
   __device__ static __forceinline__ double2 cvt(double2 z) { return z; }
 };
 template <> struct Prec<float2> {
   using S = float;
-  static constexpr int R = Engine<float2>::kThreads;  // threads per SpMV block
   __device__ static __forceinline__ float2 cvt(double2 z) {
     return make_float2(static_cast<float>(z.x), static_cast<float>(z.y));
   }
 };
+
+// Every kernel of the solver: at most 1024 threads, one block per SM.
+constexpr int kSolverThreads = Engine<double2>::kThreads;
+constexpr int kSolverMinBlocks = Engine<double2>::kMinBlocks;
 
 template <class V>
 struct KArgs {
@@ -74,7 +81,7 @@ struct KArgs {
   SolverState* st;
   double* partials;
   unsigned int* tickets;
-  unsigned int* gtickets;  // group counters of the two-level sums of K2 and K4
+  unsigned int* gtickets;
   unsigned int* dev_err;
   cudaGraphConditionalHandle cond;
   int has_cond;
@@ -92,63 +99,51 @@ __device__ __forceinline__ bool deadline_passed(const SolverState* st) {
 __global__ void k_configure(SolverState* st, double tol, int32_t maxit, int32_t use_x0, double deadline_s,
                             int32_t fresh);
 
-// r = b - A x (or r = b, x = 0), r^ = r, p = v = 0; ||b||, ||r||, rho.
-template <class V>
-__global__ void __launch_bounds__(Prec<V>::R) k_init(KArgs<V> a) {
-  using S = typename Prec<V>::S;
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ double red[32 * 4];
-  SolverState* st = a.st;
-  const int use_x0 = st->use_x0;
-  S acc[4] = {S(0), S(0), S(0), S(0)};  // |b|^2, |r|^2, (r, r)
-  if (use_x0) {
-    struct Epi {
-      const KArgs<V>* a;
-      S part[4];
-      V bpre;
-      __device__ __forceinline__ void prefetch(int32_t i) { bpre = a->b[i]; }
-      __device__ __forceinline__ void row(int32_t i, V ax) {
-        const V bi = bpre;
-        const V ri = csub(bi, ax);
-        a->r[i] = ri;
-        a->rh[i] = ri;
-        a->p[i] = vzero<V>();
-        a->v[i] = vzero<V>();
-        part[0] = cabs2_acc(bi, part[0]);
-        part[1] = cabs2_acc(ri, part[1]);
-        V d;
-        d.x = part[2];
-        d.y = part[3];
-        d = cfma_conj(ri, ri, d);
-        part[2] = d.x;
-        part[3] = d.y;
-      }
-    } epi{&a, {S(0), S(0), S(0), S(0)}, vzero<V>()};
-    spmv_run<V>(a.A, a.x, epi, smem, a.dev_err);
+// ---------------------------------------------------------------- reductions
+
+// Fixed-order total of the block partials partials[b K + k], b < G: thread j
+// adds blocks j, j + T, j + 2T, ... in that order, then the fixed block tree.
+// Valid in thread 0.
+template <int K>
+__device__ __forceinline__ void sum_block_partials(const double* partials, int G, double* red, double (&tot)[K]) {
+  double acc[K];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) acc[k] = epi.part[k];
-  } else {
-    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.A.n; i += gridDim.x * blockDim.x) {
-      const V bi = a.b[i];
-      a.x[i] = vzero<V>();
-      a.r[i] = bi;
-      a.rh[i] = bi;
-      a.p[i] = vzero<V>();
-      a.v[i] = vzero<V>();
-      acc[0] = cabs2_acc(bi, acc[0]);
-      V d;
-      d.x = acc[2];
-      d.y = acc[3];
-      d = cfma_conj(bi, bi, d);
-      acc[2] = d.x;
-      acc[3] = d.y;
-    }
-    acc[1] = acc[0];
+  for (int k = 0; k < K; ++k) acc[k] = 0.0;
+  for (int b = threadIdx.x; b < G; b += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] += ld_cg(&partials[static_cast<size_t>(b) * K + k]);
+  block_sum<K>(acc, red);
+#pragma unroll
+  for (int k = 0; k < K; ++k) tot[k] = acc[k];
+}
+
+// Graph path: publish this block's K sums; the last block to arrive forms
+// the totals (valid in its thread 0) and returns true.
+template <int K>
+__device__ __forceinline__ bool grid_total_last(double (&v)[K], double* partials, unsigned int* ticket, double* red,
+                                                double (&tot)[K]) {
+  __shared__ bool s_last;
+  block_sum<K>(v, red);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) partials[static_cast<size_t>(blockIdx.x) * K + k] = v[k];
+    __threadfence();
+    s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
   }
-  double part[4] = {double(acc[0]), double(acc[1]), double(acc[2]), double(acc[3])};
-  double tot[4];
-  if (!grid_sum_last<4>(part, a.partials, a.tickets + TK_INIT, red, tot)) return;
-  if (threadIdx.x != 0) return;
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+  sum_block_partials<K>(partials, gridDim.x, red, tot);
+  if (threadIdx.x == 0) *ticket = 0u;
+  return true;
+}
+
+// ---------------------------------------------------------------- scalar steps
+// Executed by one thread on the state (in global memory for the graph path,
+// in each block's shared memory for the persistent one).
+
+// after the initial residual: tot = (||b||^2, ||r||^2, (r^, r))
+__device__ __forceinline__ void sc_init(SolverState* st, const double (&tot)[4], int use_x0) {
   const double bnorm = sqrt(tot[0]);
   st->bnorm = bnorm;
   if (use_x0) st->spmv_count += 1;
@@ -156,7 +151,7 @@ __global__ void __launch_bounds__(Prec<V>::R) k_init(KArgs<V> a) {
   if (!isfinite(bnorm)) {
     status = HELM_ERR_NONFINITE;
   } else if (bnorm == 0.0) {
-    status = HELM_OK;  // b = 0: x = 0 (written by the tail kernel / caller)
+    status = HELM_OK;  // b = 0: x = 0 (written by the tail)
     st->relres = 0.0;
   } else {
     const double relres = sqrt(tot[1]) / bnorm;
@@ -178,103 +173,16 @@ __global__ void __launch_bounds__(Prec<V>::R) k_init(KArgs<V> a) {
       // beta = (rho / 1) (1 / 1): the first p update gives p = r
       st->rho = rho;
       st->beta = rho;
+      st->omega = make_double2(1.0, 0.0);
+      st->alpha = make_double2(1.0, 0.0);
     }
   }
+  st->phase = PH_RUN;
   st->status = status;
-  set_cond(a, status == ST_RUNNING);
 }
 
-// Element-wise kernels: one wave of blocks (grid = resident blocks), each
-// thread takes two elements per step with all loads issued before the
-// arithmetic, so the 64-clock FP64 latency and the memory latency of one
-// element overlap the other's.
-constexpr int kVecThreads = 256;
-// At most this many element-wise blocks per SM (measured on the 120x60x50
-// cavity: 3 -> 161.4, 4 -> 158.2, all that fit (6 for K1, K3) -> 159.1 us per
-// iteration).
-#ifndef HELM_VEC_MAX_BPS
-#define HELM_VEC_MAX_BPS 4
-#endif
-constexpr int kVecMaxBlocksPerSm = HELM_VEC_MAX_BPS;
-
-// Rows of an element-wise kernel: block b takes the contiguous range
-// [b n / G, (b + 1) n / G) (sizes differ by at most one, so every SM of a
-// one-wave grid gets the same work), its threads striding by blockDim.
-struct RowChunk {
-  int32_t begin, end, step;
-  __device__ __forceinline__ explicit RowChunk(int32_t n)
-      : begin(static_cast<int32_t>(static_cast<int64_t>(blockIdx.x) * n / gridDim.x)),
-        end(static_cast<int32_t>((static_cast<int64_t>(blockIdx.x) + 1) * n / gridDim.x)),
-        step(static_cast<int32_t>(blockDim.x)) {}
-  __device__ __forceinline__ int32_t first() const { return begin + static_cast<int32_t>(threadIdx.x); }
-};
-
-// K1: p = r + beta (p - omega v)
-template <class V>
-__global__ void __launch_bounds__(kVecThreads) k_p(KArgs<V> a) {
-  const SolverState* st = a.st;
-  // K2 may start staging the matrix at once (it waits for p itself); K1 is
-  // launched the ordinary way, after the previous iteration has completed
-  pdl_launch_dependents();
-  if (st->status != ST_RUNNING) return;
-  const V beta = Prec<V>::cvt(st->beta), omega = Prec<V>::cvt(st->omega);
-  const RowChunk c(a.A.n);
-  int32_t i = c.first();
-  if (i >= c.end) return;
-  V v0 = a.v[i], p0 = a.p[i], r0 = a.r[i];
-  for (;;) {
-    // the next row's loads are in flight while this row is computed
-    const int32_t j = i + c.step;
-    const bool more = j < c.end;
-    V v1 = v0, p1 = p0, r1 = r0;
-    if (more) {
-      v1 = a.v[j];
-      p1 = a.p[j];
-      r1 = a.r[j];
-    }
-    a.p[i] = cfma(beta, cfms(omega, v0, p0), r0);
-    if (!more) break;
-    v0 = v1;
-    p0 = p1;
-    r0 = r1;
-    i = j;
-  }
-}
-
-// K2: v = A p, (r^, v) -> alpha
-template <class V>
-__global__ void __launch_bounds__(Prec<V>::R) k_v(KArgs<V> a) {
-  using S = typename Prec<V>::S;
-  extern __shared__ __align__(16) unsigned char smem[];
-  // the block sums reuse the staging buffer once the tiles are done (less
-  // static shared memory: one more block per SM)
-  double* red = reinterpret_cast<double*>(smem);
-  SolverState* st = a.st;
-  struct Epi {
-    const KArgs<V>* a;
-    V part;
-    V rh;
-    __device__ __forceinline__ void prefetch(int32_t i) { rh = a->rh[i]; }
-    __device__ __forceinline__ void row(int32_t i, V ax) {
-      a->v[i] = ax;
-      part = cfma_conj(rh, ax, part);
-    }
-  } epi{&a, vzero<V>(), vzero<V>()};
-  // the first tile's copy is in flight while p (the previous kernel's
-  // output) is waited for
-  bool go = false;
-  spmv_run<V>(a.A, a.p, epi, smem, a.dev_err, [&]() {
-    pdl_wait();
-    pdl_launch_dependents();
-    go = st->status == ST_RUNNING;
-    return go;
-  });
-  if (!go) return;
-  double part[2] = {double(epi.part.x), double(epi.part.y)};
-  double tot[2];
-  // many blocks of few threads: the two-level sum keeps the last block short
-  if (!grid_sum_last2<2>(part, a.partials, a.tickets + TK_V, a.gtickets, red, tot)) return;
-  if (threadIdx.x != 0) return;
+// after P2: tot = (r^, v)
+__device__ __forceinline__ void sc_after_v(SolverState* st, const double (&tot)[2]) {
   st->iter += 1;
   st->spmv_count += 1;
   const double2 rv = make_double2(tot[0], tot[1]);
@@ -289,44 +197,8 @@ __global__ void __launch_bounds__(Prec<V>::R) k_v(KArgs<V> a) {
   }
 }
 
-// K3: s = r - alpha v, ||s||
-template <class V>
-__global__ void __launch_bounds__(kVecThreads) k_s(KArgs<V> a) {
-  using S = typename Prec<V>::S;
-  __shared__ double red[32];
-  SolverState* st = a.st;
-  const RowChunk c(a.A.n);
-  int32_t i = c.first();
-  // r was final before the previous kernel started; v and alpha are its output
-  V r0 = vzero<V>();
-  if (i < c.end) r0 = a.r[i];
-  pdl_wait();
-  pdl_launch_dependents();
-  if (st->status != ST_RUNNING) return;
-  const V alpha = Prec<V>::cvt(st->alpha);
-  S acc = S(0);
-  V v0 = vzero<V>();
-  if (i < c.end) v0 = a.v[i];
-  while (i < c.end) {
-    const int32_t j = i + c.step;
-    const bool more = j < c.end;
-    V v1 = v0, r1 = r0;
-    if (more) {
-      v1 = a.v[j];
-      r1 = a.r[j];
-    }
-    const V s0 = cfms(alpha, v0, r0);
-    a.s[i] = s0;
-    acc = cabs2_acc(s0, acc);
-    v0 = v1;
-    r0 = r1;
-    i = j;
-  }
-  double part[1] = {double(acc)};
-  double tot[1];
-  if (!grid_sum_last<1>(part, a.partials, a.tickets + TK_S, red, tot)) return;
-  if (threadIdx.x != 0) return;
-  // ||s|| / ||b|| <= tol compared squared: no square root on the critical path
+// after P3: tot = ||s||^2; ||s|| / ||b|| <= tol compared squared
+__device__ __forceinline__ void sc_after_s(SolverState* st, const double (&tot)[1]) {
   const double s2 = tot[0];
   const double bt = st->bnorm * st->tol;
   if (!isfinite(s2)) {
@@ -337,39 +209,8 @@ __global__ void __launch_bounds__(kVecThreads) k_s(KArgs<V> a) {
   }
 }
 
-// K4: t = A s, (t, s), (t, t) -> omega
-template <class V>
-__global__ void __launch_bounds__(Prec<V>::R) k_t(KArgs<V> a) {
-  using S = typename Prec<V>::S;
-  extern __shared__ __align__(16) unsigned char smem[];
-  double* red = reinterpret_cast<double*>(smem);  // the staging buffer, once the tiles are done
-  SolverState* st = a.st;
-  struct Epi {
-    const KArgs<V>* a;
-    V ts;
-    S tt;
-    V si;
-    __device__ __forceinline__ void prefetch(int32_t i) { si = a->s[i]; }
-    __device__ __forceinline__ void row(int32_t i, V ax) {
-      a->t[i] = ax;
-      ts = cfma_conj(ax, si, ts);
-      tt = cabs2_acc(ax, tt);
-    }
-  } epi{&a, vzero<V>(), S(0), vzero<V>()};
-  // the first tile's copy is in flight while s and the phase (the previous
-  // kernel's output) are waited for
-  bool go = false;
-  spmv_run<V>(a.A, a.s, epi, smem, a.dev_err, [&]() {
-    pdl_wait();
-    pdl_launch_dependents();
-    go = st->status == ST_RUNNING && st->phase == PH_RUN;
-    return go;
-  });
-  if (!go) return;
-  double part[3] = {double(epi.ts.x), double(epi.ts.y), double(epi.tt)};
-  double tot[3];
-  if (!grid_sum_last2<3>(part, a.partials, a.tickets + TK_T, a.gtickets + kGroupTickets, red, tot)) return;
-  if (threadIdx.x != 0) return;
+// after P4: tot = ((t, s), ||t||^2)
+__device__ __forceinline__ void sc_after_t(SolverState* st, const double (&tot)[3]) {
   st->spmv_count += 1;
   const double2 ts = make_double2(tot[0], tot[1]);
   const double tt = tot[2];
@@ -385,70 +226,13 @@ __global__ void __launch_bounds__(Prec<V>::R) k_t(KArgs<V> a) {
   }
 }
 
-// K5: x += alpha p + omega s, r = s - omega t; stop test; rho, beta
-template <class V>
-__global__ void __launch_bounds__(kVecThreads) k_xr(KArgs<V> a) {
-  using S = typename Prec<V>::S;
-  __shared__ double red[32 * 3];
-  SolverState* st = a.st;
-  const RowChunk c(a.A.n);
-  int32_t i = c.first();
-  // x, p, s and r^ were final before the previous kernel started; t, omega
-  // and the status are its output
-  V s0 = vzero<V>(), x0 = vzero<V>(), p0 = vzero<V>(), h0 = vzero<V>();
-  if (i < c.end) {
-    s0 = a.s[i];
-    x0 = a.x[i];
-    p0 = a.p[i];
-    h0 = a.rh[i];
-  }
-  pdl_wait();
-  pdl_launch_dependents();
-  const int status0 = st->status;
-  if (status0 != ST_RUNNING) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(a, false);
-    return;
-  }
-  const double2 alpha64 = st->alpha, omega64 = st->omega;
-  const V alpha = Prec<V>::cvt(alpha64), omega = Prec<V>::cvt(omega64);
-  const int phase = st->phase;
-  V rr = vzero<V>();
-  S r2 = S(0);
-  if (phase == PH_SCONV) {
-    for (; i < c.end; i += c.step) a.x[i] = cfma(alpha, a.p[i], a.x[i]);
-  } else {
-    V t0 = vzero<V>();
-    if (i < c.end) t0 = a.t[i];
-    while (i < c.end) {
-      const int32_t j = i + c.step;
-      const bool more = j < c.end;
-      V s1 = s0, x1 = x0, p1 = p0, t1 = t0, h1 = h0;
-      if (more) {
-        s1 = a.s[j];
-        x1 = a.x[j];
-        p1 = a.p[j];
-        t1 = a.t[j];
-        h1 = a.rh[j];
-      }
-      a.x[i] = cfma(omega, s0, cfma(alpha, p0, x0));
-      const V r0 = cfms(omega, t0, s0);
-      a.r[i] = r0;
-      rr = cfma_conj(h0, r0, rr);
-      r2 = cabs2_acc(r0, r2);
-      s0 = s1;
-      x0 = x1;
-      p0 = p1;
-      t0 = t1;
-      h0 = h1;
-      i = j;
-    }
-  }
-  double part[3] = {double(rr.x), double(rr.y), double(r2)};
-  double tot[3];
-  if (!grid_sum_last<3>(part, a.partials, a.tickets + TK_XR, red, tot)) return;
-  if (threadIdx.x != 0) return;
+// after P5: tot = ((r^, r), ||r||^2); `late` = the deadline has passed.
+// With phase PH_SCONV (P5 only added alpha p to x) the solve is done.
+__device__ __forceinline__ void sc_after_xr(SolverState* st, const double (&tot)[3], bool late) {
   // the inner loop of mixed precision runs on a scaled residual: b - A x ~ aux[2].x * r
   const double sc = st->method == kModeRefine ? st->aux[2].x : 1.0;
+  const int phase = st->phase;
+  const double2 alpha64 = st->alpha, omega64 = st->omega;
   int status = ST_RUNNING;
   if (phase == PH_SCONV) {
     status = HELM_OK;
@@ -480,7 +264,7 @@ __global__ void __launch_bounds__(kVecThreads) k_xr(KArgs<V> a) {
       status = HELM_ERR_BREAKDOWN;
     } else if (st->iter >= st->maxit) {
       status = HELM_ERR_NOT_CONVERGED;
-    } else if (deadline_passed(st)) {
+    } else if (late) {
       status = HELM_ERR_TIMEOUT;
     } else {
       const double2 rho_new = make_double2(tot[0], tot[1]);
@@ -497,23 +281,315 @@ __global__ void __launch_bounds__(kVecThreads) k_xr(KArgs<V> a) {
         st->beta = beta;
       }
     }
+    if (status != ST_RUNNING) st->relres = sqrt(tot[2]) * sc / st->bnorm;
   }
-  if (phase != PH_SCONV && status != ST_RUNNING) st->relres = sqrt(tot[2]) * sc / st->bnorm;
   st->status = status;
-  set_cond(a, status == ST_RUNNING);
 }
 
-template <class V>
-struct KShapes {
-  int spmv_grid;                // K2 and K4
-  int init_grid;                // the init kernel
-  int vec_grid;
-  int grid_p, grid_s, grid_xr;  // one wave of each element-wise kernel
-};
+// ---------------------------------------------------------------- phases
+// The per-thread work of each phase, shared by the graph kernels and the
+// persistent kernel.  Rows are those of SliceRows; each phase returns this
+// thread's partial sums.
 
-// Persistent grid shared by `fns`: the blocks that fit on every SM at once
-// for each of them (so that none runs a second wave, which would leave most
-// of the GPU idle while it finishes), times the SMs, at most `units`.
+// init without x0: x = 0, r = r^ = b, p = v = 0; (||b||^2, ||r||^2, (r^, r))
+template <class V>
+__device__ __forceinline__ void ph_init_zero(const KArgs<V>& a, typename Prec<V>::S (&acc)[4]) {
+  const V z = vzero<V>();
+  for (SliceRows q(a.A.n); q.active(); q.advance()) {
+    const int32_t i = q.row();
+    if (i >= a.A.n) continue;
+    const V bi = a.b[i];
+    a.x[i] = z;
+    a.r[i] = bi;
+    a.rh[i] = bi;
+    a.p[i] = z;
+    a.v[i] = z;
+    acc[0] = cabs2_acc(bi, acc[0]);
+    V d;
+    d.x = acc[2];
+    d.y = acc[3];
+    d = cfma_conj(bi, bi, d);
+    acc[2] = d.x;
+    acc[3] = d.y;
+  }
+  acc[1] = acc[0];
+}
+
+// init with x0 (SpMV epilogue): r = r^ = b - A x, p = v = 0
+template <class V>
+struct InitEpi {
+  const V* b;
+  V *r, *rh, *p, *v;
+  typename Prec<V>::S part[4];
+  V bpre;
+  __device__ __forceinline__ void prefetch(int32_t i) { bpre = b[i]; }
+  __device__ __forceinline__ void row(int32_t i, V ax) {
+    const V bi = bpre;
+    const V ri = csub(bi, ax);
+    r[i] = ri;
+    rh[i] = ri;
+    p[i] = vzero<V>();
+    v[i] = vzero<V>();
+    part[0] = cabs2_acc(bi, part[0]);
+    part[1] = cabs2_acc(ri, part[1]);
+    V d;
+    d.x = part[2];
+    d.y = part[3];
+    d = cfma_conj(ri, ri, d);
+    part[2] = d.x;
+    part[3] = d.y;
+  }
+};
+template <class V>
+__device__ __forceinline__ InitEpi<V> init_epi(const KArgs<V>& a) {
+  using S = typename Prec<V>::S;
+  return InitEpi<V>{a.b, a.r, a.rh, a.p, a.v, {S(0), S(0), S(0), S(0)}, vzero<V>()};
+}
+
+// P1: p = r + beta (p - omega v); the next row's loads are issued before
+// this row is computed
+template <class V>
+__device__ __forceinline__ void ph_p(const KArgs<V>& a, V beta, V omega) {
+  SliceRows q(a.A.n);
+  int32_t i = q.row();
+  if (!q.active() || i >= a.A.n) return;
+  V v0 = a.v[i], p0 = a.p[i], r0 = a.r[i];
+  for (;;) {
+    SliceRows nq = q;
+    const bool more = nq.advance() && nq.row() < a.A.n;
+    const int32_t j = nq.row();
+    V v1 = v0, p1 = p0, r1 = r0;
+    if (more) {
+      v1 = a.v[j];
+      p1 = a.p[j];
+      r1 = a.r[j];
+    }
+    a.p[i] = cfma(beta, cfms(omega, v0, p0), r0);
+    if (!more) break;
+    v0 = v1;
+    p0 = p1;
+    r0 = r1;
+    i = j;
+    q = nq;
+  }
+}
+
+// P2 epilogue: v = A p, (r^, v)
+template <class V>
+struct VEpi {
+  V* v;
+  const V* rhp;
+  V part;
+  V rh;
+  __device__ __forceinline__ void prefetch(int32_t i) { rh = rhp[i]; }
+  __device__ __forceinline__ void row(int32_t i, V ax) {
+    v[i] = ax;
+    part = cfma_conj(rh, ax, part);
+  }
+};
+template <class V>
+__device__ __forceinline__ VEpi<V> v_epi(const KArgs<V>& a) {
+  return VEpi<V>{a.v, a.rh, vzero<V>(), vzero<V>()};
+}
+
+// P3: s = r - alpha v, ||s||^2
+template <class V>
+__device__ __forceinline__ typename Prec<V>::S ph_s(const KArgs<V>& a, V alpha) {
+  using S = typename Prec<V>::S;
+  S acc = S(0);
+  SliceRows q(a.A.n);
+  int32_t i = q.row();
+  if (!q.active() || i >= a.A.n) return acc;
+  V v0 = a.v[i], r0 = a.r[i];
+  for (;;) {
+    SliceRows nq = q;
+    const bool more = nq.advance() && nq.row() < a.A.n;
+    const int32_t j = nq.row();
+    V v1 = v0, r1 = r0;
+    if (more) {
+      v1 = a.v[j];
+      r1 = a.r[j];
+    }
+    const V s0 = cfms(alpha, v0, r0);
+    a.s[i] = s0;
+    acc = cabs2_acc(s0, acc);
+    if (!more) break;
+    v0 = v1;
+    r0 = r1;
+    i = j;
+    q = nq;
+  }
+  return acc;
+}
+
+// P4 epilogue: t = A s, (t, s), ||t||^2
+template <class V>
+struct TEpi {
+  V* t;
+  const V* sp;
+  V ts;
+  typename Prec<V>::S tt;
+  V si;
+  __device__ __forceinline__ void prefetch(int32_t i) { si = sp[i]; }
+  __device__ __forceinline__ void row(int32_t i, V ax) {
+    t[i] = ax;
+    ts = cfma_conj(ax, si, ts);
+    tt = cabs2_acc(ax, tt);
+  }
+};
+template <class V>
+__device__ __forceinline__ TEpi<V> t_epi(const KArgs<V>& a) {
+  using S = typename Prec<V>::S;
+  return TEpi<V>{a.t, a.s, vzero<V>(), S(0), vzero<V>()};
+}
+
+// P5: x += alpha p + omega s, r = s - omega t; (r^, r), ||r||^2.  With
+// sconv (the solve stopped at s) only x += alpha p.
+template <class V>
+__device__ __forceinline__ void ph_xr(const KArgs<V>& a, V alpha, V omega, bool sconv, V& rr,
+                                      typename Prec<V>::S& r2) {
+  SliceRows q(a.A.n);
+  int32_t i = q.row();
+  if (!q.active() || i >= a.A.n) return;
+  if (sconv) {
+    for (; q.active(); q.advance()) {
+      i = q.row();
+      if (i < a.A.n) a.x[i] = cfma(alpha, a.p[i], a.x[i]);
+    }
+    return;
+  }
+  V s0 = a.s[i], x0 = a.x[i], p0 = a.p[i], t0 = a.t[i], h0 = a.rh[i];
+  for (;;) {
+    SliceRows nq = q;
+    const bool more = nq.advance() && nq.row() < a.A.n;
+    const int32_t j = nq.row();
+    V sn = s0, xn = x0, pn = p0, tn = t0, hn = h0;
+    if (more) {
+      sn = a.s[j];
+      xn = a.x[j];
+      pn = a.p[j];
+      tn = a.t[j];
+      hn = a.rh[j];
+    }
+    a.x[i] = cfma(omega, s0, cfma(alpha, p0, x0));
+    const V r0 = cfms(omega, t0, s0);
+    a.r[i] = r0;
+    rr = cfma_conj(h0, r0, rr);
+    r2 = cabs2_acc(r0, r2);
+    if (!more) break;
+    s0 = sn;
+    x0 = xn;
+    p0 = pn;
+    t0 = tn;
+    h0 = hn;
+    i = j;
+    q = nq;
+  }
+}
+
+// ---------------------------------------------------------------- graph kernels
+
+template <class V>
+__global__ void __launch_bounds__(kSolverThreads, kSolverMinBlocks) k_init(KArgs<V> a) {
+  using S = typename Prec<V>::S;
+  __shared__ double red[32 * 4];
+  SolverState* st = a.st;
+  const int use_x0 = st->use_x0;
+  S acc[4] = {S(0), S(0), S(0), S(0)};
+  if (use_x0) {
+    InitEpi<V> epi = init_epi<V>(a);
+    spmv_run<V>(a.A, a.x, epi, nullptr, a.dev_err);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[k] = epi.part[k];
+  } else {
+    ph_init_zero<V>(a, acc);
+  }
+  double part[4] = {double(acc[0]), double(acc[1]), double(acc[2]), double(acc[3])};
+  double tot[4];
+  if (!grid_total_last<4>(part, a.partials, a.tickets + TK_INIT, red, tot)) return;
+  if (threadIdx.x != 0) return;
+  sc_init(st, tot, use_x0);
+  set_cond(a, st->status == ST_RUNNING);
+}
+
+// K1: p = r + beta (p - omega v)
+template <class V>
+__global__ void __launch_bounds__(kSolverThreads, kSolverMinBlocks) k_p(KArgs<V> a) {
+  const SolverState* st = a.st;
+  if (st->status != ST_RUNNING) return;
+  ph_p<V>(a, Prec<V>::cvt(st->beta), Prec<V>::cvt(st->omega));
+}
+
+// K2: v = A p, (r^, v) -> alpha
+template <class V>
+__global__ void __launch_bounds__(kSolverThreads, kSolverMinBlocks) k_v(KArgs<V> a) {
+  __shared__ double red[32 * 2];
+  SolverState* st = a.st;
+  if (st->status != ST_RUNNING) return;
+  VEpi<V> epi = v_epi<V>(a);
+  spmv_run<V>(a.A, a.p, epi, nullptr, a.dev_err);
+  double part[2] = {double(epi.part.x), double(epi.part.y)};
+  double tot[2];
+  if (!grid_total_last<2>(part, a.partials, a.tickets + TK_V, red, tot)) return;
+  if (threadIdx.x != 0) return;
+  sc_after_v(st, tot);
+}
+
+// K3: s = r - alpha v, ||s||
+template <class V>
+__global__ void __launch_bounds__(kSolverThreads, kSolverMinBlocks) k_s(KArgs<V> a) {
+  __shared__ double red[32];
+  SolverState* st = a.st;
+  if (st->status != ST_RUNNING) return;
+  double part[1] = {double(ph_s<V>(a, Prec<V>::cvt(st->alpha)))};
+  double tot[1];
+  if (!grid_total_last<1>(part, a.partials, a.tickets + TK_S, red, tot)) return;
+  if (threadIdx.x != 0) return;
+  sc_after_s(st, tot);
+}
+
+// K4: t = A s, (t, s), (t, t) -> omega
+template <class V>
+__global__ void __launch_bounds__(kSolverThreads, kSolverMinBlocks) k_t(KArgs<V> a) {
+  using S = typename Prec<V>::S;
+  __shared__ double red[32 * 3];
+  SolverState* st = a.st;
+  if (st->status != ST_RUNNING || st->phase != PH_RUN) return;
+  TEpi<V> epi = t_epi<V>(a);
+  spmv_run<V>(a.A, a.s, epi, nullptr, a.dev_err);
+  double part[3] = {double(epi.ts.x), double(epi.ts.y), double(epi.tt)};
+  double tot[3];
+  if (!grid_total_last<3>(part, a.partials, a.tickets + TK_T, red, tot)) return;
+  if (threadIdx.x != 0) return;
+  sc_after_t(st, tot);
+}
+
+// K5: x += alpha p + omega s, r = s - omega t; stop test; rho, beta
+template <class V>
+__global__ void __launch_bounds__(kSolverThreads, kSolverMinBlocks) k_xr(KArgs<V> a) {
+  using S = typename Prec<V>::S;
+  __shared__ double red[32 * 3];
+  SolverState* st = a.st;
+  if (st->status != ST_RUNNING) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(a, false);
+    return;
+  }
+  V rr = vzero<V>();
+  S r2 = S(0);
+  ph_xr<V>(a, Prec<V>::cvt(st->alpha), Prec<V>::cvt(st->omega), st->phase == PH_SCONV, rr, r2);
+  double part[3] = {double(rr.x), double(rr.y), double(r2)};
+  double tot[3];
+  if (!grid_total_last<3>(part, a.partials, a.tickets + TK_XR, red, tot)) return;
+  if (threadIdx.x != 0) return;
+  sc_after_xr(st, tot, deadline_passed(st));
+  set_cond(a, st->status == ST_RUNNING);
+}
+
+// Solver grid: one wave of the solver kernels -- the blocks that fit on every
+// SM at once for each of `fns` (so that none runs a second wave), times the
+// SMs, at most enough blocks for one warp per slice.  Every kernel of a solve
+// (graph or persistent) runs on this grid: the grid fixes which thread owns
+// which row and so the order of every partial sum.
 inline helm_status persistent_grid(std::initializer_list<const void*> fns, int threads, size_t smem,
                                    int num_sms, int64_t units, int* grid) {
   int per_sm = 1 << 30;
@@ -530,80 +606,78 @@ inline helm_status persistent_grid(std::initializer_list<const void*> fns, int t
 }
 
 template <class V>
+struct KShapes {
+  int grid;     // every kernel of the loop, init and tail included
+  int threads;  // threads per block (a multiple of 32)
+};
+
+template <class V>
 inline void enqueue_init(const KArgs<V>& a, const KShapes<V>& sh, cudaStream_t s) {
-  k_init<V><<<sh.init_grid, Prec<V>::R, Engine<V>::kSmem, s>>>(a);
-}
-// Launch with programmatic stream serialization: the kernel may start while
-// its predecessor finishes (it calls pdl_wait() before it reads that
-// kernel's output).  Launch errors surface through cudaGetLastError().
-// Measured on GB300 inside the solver graph: 162.5 us per BiCGStab iteration
-// without the attribute, 179.1 us with it, so it is off; the kernels' waits
-// are no-ops then.
-#ifndef HELM_PDL
-#define HELM_PDL 0
-#endif
-template <class... P, class... Args>
-inline void launch_dependent(void (*kern)(P...), int grid, int block, size_t smem, cudaStream_t s,
-                             Args&&... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(static_cast<unsigned>(grid));
-  cfg.blockDim = dim3(static_cast<unsigned>(block));
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = HELM_PDL ? 1 : 0;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  (void)cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+  k_init<V><<<sh.grid, sh.threads, 0, s>>>(a);
 }
 
 template <class V>
 inline void enqueue_body(const KArgs<V>& a, const KShapes<V>& sh, cudaStream_t s) {
-  constexpr size_t smem = Engine<V>::kSmem;
-  k_p<V><<<sh.grid_p, kVecThreads, 0, s>>>(a);
-  launch_dependent(k_v<V>, sh.spmv_grid, Prec<V>::R, smem, s, a);
-  launch_dependent(k_s<V>, sh.grid_s, kVecThreads, 0, s, a);
-  launch_dependent(k_t<V>, sh.spmv_grid, Prec<V>::R, smem, s, a);
-  launch_dependent(k_xr<V>, sh.grid_xr, kVecThreads, 0, s, a);
+  k_p<V><<<sh.grid, sh.threads, 0, s>>>(a);
+  k_v<V><<<sh.grid, sh.threads, 0, s>>>(a);
+  k_s<V><<<sh.grid, sh.threads, 0, s>>>(a);
+  k_t<V><<<sh.grid, sh.threads, 0, s>>>(a);
+  k_xr<V><<<sh.grid, sh.threads, 0, s>>>(a);
 }
 
 template <class V>
 inline helm_status prepare_krylov_kernels() {
-  constexpr size_t smem = Engine<V>::kSmem;
-  HELM_CUDA_TRY(set_smem_attr(reinterpret_cast<const void*>(&k_init<V>), smem));
-  HELM_CUDA_TRY(set_smem_attr(reinterpret_cast<const void*>(&k_v<V>), smem));
-  HELM_CUDA_TRY(set_smem_attr(reinterpret_cast<const void*>(&k_t<V>), smem));
   return HELM_OK;
 }
 
-// Grids of the solver's kernels: one wave each.
+// Shape of a slice-parallel grid: one block per SM (blocks_per_sm with
+// smaller blocks), never more blocks than slices, and per block just enough
+// warps (at most max_threads / 32) for one slice per warp in each round.
+struct SliceShape {
+  int grid, threads;
+};
+inline SliceShape slice_shape(int32_t n, int num_sms, int max_threads, int blocks_per_sm, bool full = false) {
+  const int64_t nsl = std::max<int64_t>((static_cast<int64_t>(n) + 31) / 32, 1);
+  const int64_t grid = std::min<int64_t>(static_cast<int64_t>(num_sms) * blocks_per_sm, nsl);
+  const int64_t wmax = std::max(max_threads / 32, 1);
+  // rounds at the widest block, then (unless `full`) the fewest warps that
+  // keep that many rounds: every round (the last one too) nearly full
+  const int64_t rounds = (nsl + grid * wmax - 1) / (grid * wmax);
+  const int64_t warps =
+      full ? std::min<int64_t>((nsl + grid - 1) / grid, wmax) : std::min<int64_t>((nsl + grid * rounds - 1) / (grid * rounds), wmax);
+  return SliceShape{static_cast<int>(grid), static_cast<int>(32 * std::max<int64_t>(warps, 1))};
+}
+
+// Shape of the solver's grid: blocks of at most HELM_SOLVER_THREADS threads,
+// HELM_SOLVER_BPS blocks per SM.  A build-time choice, not a run-time one:
+// the shape fixes which thread owns which row and so the rounding of every
+// reduction, and a solve must give the same bits on every run.
+// Measured on the 120x60x50 cavity (graph loop, us per iteration): 1024 x 1
+// (832 threads used) 144.6, 512 x 2 138.4, 256 x 4 140.8.
+#ifndef HELM_SOLVER_THREADS
+#define HELM_SOLVER_THREADS 512
+#endif
+#ifndef HELM_SOLVER_BPS
+#define HELM_SOLVER_BPS 2
+#endif
+
+// Grid of the solver's kernels; the kernels (and `extra` ones: the tail, the
+// persistent kernel) must fit HELM_SOLVER_BPS such blocks per SM.
 template <class V>
-inline helm_status krylov_shapes(helm_csr A, KShapes<V>* sh) {
-  constexpr size_t smem = Engine<V>::kSmem;
-  const int64_t ntiles = (static_cast<int64_t>(A->n) + Engine<V>::R - 1) / Engine<V>::R;
-  HELM_TRY(persistent_grid({reinterpret_cast<const void*>(&k_v<V>), reinterpret_cast<const void*>(&k_t<V>)},
-                                       Prec<V>::R, smem, A->num_sms, ntiles, &sh->spmv_grid));
-  HELM_TRY(persistent_grid({reinterpret_cast<const void*>(&k_init<V>)}, Prec<V>::R, smem, A->num_sms, ntiles,
-                                       &sh->init_grid));
-  sh->vec_grid = A->vec_grid;
-  // element-wise kernels: the same number of blocks on every SM (one wave,
-  // fewer when the rows would not fill them)
-  const int64_t per_sm_rows = (static_cast<int64_t>(A->n) + static_cast<int64_t>(A->num_sms) * kVecThreads - 1) /
-                              (static_cast<int64_t>(A->num_sms) * kVecThreads);
-  auto wave = [&](const void* fn, int* out) -> helm_status {
+inline helm_status krylov_shapes(helm_csr A, KShapes<V>* sh, std::initializer_list<const void*> extra = {}) {
+  std::vector<const void*> fns = {reinterpret_cast<const void*>(&k_init<V>), reinterpret_cast<const void*>(&k_p<V>),
+                                  reinterpret_cast<const void*>(&k_v<V>),    reinterpret_cast<const void*>(&k_s<V>),
+                                  reinterpret_cast<const void*>(&k_t<V>),    reinterpret_cast<const void*>(&k_xr<V>)};
+  for (const void* f : extra) fns.push_back(f);
+  const SliceShape ss = slice_shape(A->n, A->num_sms, HELM_SOLVER_THREADS, HELM_SOLVER_BPS);
+  for (const void* fn : fns) {
     int b = 0;
-    HELM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, kVecThreads, 0));
-    if (b > kVecMaxBlocksPerSm) b = kVecMaxBlocksPerSm;
-    int64_t per_sm = b < 1 ? 1 : b;
-    if (per_sm_rows < per_sm) per_sm = per_sm_rows < 1 ? 1 : per_sm_rows;
-    *out = static_cast<int>(per_sm * A->num_sms);
-    return HELM_OK;
-  };
-  helm_status st = wave(reinterpret_cast<const void*>(&k_p<V>), &sh->grid_p);
-  if (st == HELM_OK) st = wave(reinterpret_cast<const void*>(&k_s<V>), &sh->grid_s);
-  if (st == HELM_OK) st = wave(reinterpret_cast<const void*>(&k_xr<V>), &sh->grid_xr);
-  return st;
+    HELM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, ss.threads, 0));
+    if (b < HELM_SOLVER_BPS) return HELM_ERR_CUDA;
+  }
+  sh->grid = ss.grid;
+  sh->threads = ss.threads;
+  return HELM_OK;
 }
 
 // Iterations (loop bodies) per pass of the while node: each pass re-launches

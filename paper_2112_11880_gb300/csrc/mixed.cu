@@ -94,7 +94,7 @@ struct MxRow {
 
 // init: r64 = b - A x (or b, x = 0); asks for the first inner start, which
 // starts the complex64 recurrence
-__global__ void __launch_bounds__(R128) k_mx_init(RuArgs a) {
+__global__ void __launch_bounds__(R128, kSolverMinBlocks) k_mx_init(RuArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[32 * 2];
   SolverState* st = a.st;
@@ -204,7 +204,7 @@ __device__ __forceinline__ bool grid_sum_last_many(double (&v)[K], double* parti
 
 // step 1b: w = A z (FP64, z = d64) and the projections beta_j = (C_j, w) on
 // the stored directions (classical Gram-Schmidt against the GCR window).
-__global__ void __launch_bounds__(R128) k_gcr_project(RuArgs a, int always) {
+__global__ void __launch_bounds__(R128, kSolverMinBlocks) k_gcr_project(RuArgs a, int always) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int K = 2 * kGcr;
   __shared__ double red[32 * 4];
@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(256) k_gcr_xupd(RuArgs a, int always) {
 }
 
 // step 2: r64 = b - A x (FP64), the convergence test
-__global__ void __launch_bounds__(R128) k_mx_residual(RuArgs a) {
+__global__ void __launch_bounds__(R128, kSolverMinBlocks) k_mx_residual(RuArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[32];
   SolverState* st = a.st;
@@ -402,7 +402,7 @@ __global__ void __launch_bounds__(256) k_mx_restart(RuArgs a) {
 }
 
 // tail: the FP64 true residual for the report (x32 folded just before)
-__global__ void __launch_bounds__(R128) k_mx_tail(RuArgs a) {
+__global__ void __launch_bounds__(R128, kSolverMinBlocks) k_mx_tail(RuArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[32];
   SolverState* st = a.st;
@@ -485,7 +485,7 @@ helm_status solve_mixed(helm_csr A, const double2* b, double2* x, const helm_opt
 
   KArgs<float2> k;
   std::memset(&k, 0, sizeof(k));
-  k.A = CsrDev<float2>{n, A->nnz, A->rowptr, A->colind, A->vals32, A->real_blk, A->vals32_re};
+  k.A = csr_dev<float2>(A, A->vals32, A->sv32);
   k.r = W;
   k.rh = W + N;
   k.p = W + 2 * N;
@@ -502,7 +502,7 @@ helm_status solve_mixed(helm_csr A, const double2* b, double2* x, const helm_opt
 
   RuArgs a;
   std::memset(&a, 0, sizeof(a));
-  a.A = CsrDev<double2>{n, A->nnz, A->rowptr, A->colind, static_cast<const double2*>(A->vals), A->real_blk, A->vals_re};
+  a.A = csr_dev<double2>(A, static_cast<const double2*>(A->vals), A->sv);
   a.b = b;
   a.x = x;
   a.r64 = A->vec;

@@ -934,7 +934,7 @@ helm_status helm_sweep_solve(helm_sweep S, int32_t nfreq, const double* h_omega,
   helm_status worst = HELM_OK;
   for (int j = 0; j < nfreq; ++j) {
     helm_status sj = status[j] == ST_RUNNING ? HELM_ERR_CUDA : static_cast<helm_status>(status[j]);
-    if (sj == HELM_OK && !(relres_true[j] <= 1.5 * opts.tol)) sj = HELM_ERR_NOT_CONVERGED;
+    if (sj == HELM_OK && !(relres_true[j] <= opts.tol)) sj = HELM_ERR_NOT_CONVERGED;
     if (h_infos) {
       h_infos[j].iters = iters[j];
       h_infos[j].restarts = 0;

@@ -74,7 +74,7 @@ __device__ __forceinline__ void tq_gamma(SolverState* st) {
 }
 
 // init A: r0 = b - A x (or b, x = 0); w = u = r0; d = 0; ||b||, ||r0||, rho = (r0, r0)
-__global__ void __launch_bounds__(RT) k_tq_init_a(TqArgs a) {
+__global__ void __launch_bounds__(RT, kSolverMinBlocks) k_tq_init_a(TqArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[32 * 4];
   SolverState* st = a.st;
@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(RT) k_tq_init_a(TqArgs a) {
 }
 
 // init B: v = A u, Au = v, sigma = (r0, v) -> alpha
-__global__ void __launch_bounds__(RT) k_tq_init_b(TqArgs a) {
+__global__ void __launch_bounds__(RT, kSolverMinBlocks) k_tq_init_b(TqArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[32 * 2];
   SolverState* st = a.st;
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(256) k_tq_even(TqArgs a) {
 }
 
 // T2: Aun = A un; x += eta d
-__global__ void __launch_bounds__(RT) k_tq_spmv_un(TqArgs a) {
+__global__ void __launch_bounds__(RT, kSolverMinBlocks) k_tq_spmv_un(TqArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   SolverState* st = a.st;
   if (st->status != ST_RUNNING) return;
@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(256) k_tq_u(TqArgs a) {
 }
 
 // T5: Au = A u; v = Au + beta (Aun + beta v); sigma = (r0, v) -> alpha, gamma
-__global__ void __launch_bounds__(RT) k_tq_spmv_u(TqArgs a) {
+__global__ void __launch_bounds__(RT, kSolverMinBlocks) k_tq_spmv_u(TqArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[32 * 2];
   SolverState* st = a.st;
@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(RT) k_tq_spmv_u(TqArgs a) {
 }
 
 // T6: true-residual check when a bound fell below tol; cap, deadline, condition
-__global__ void __launch_bounds__(RT) k_tq_check(TqArgs a) {
+__global__ void __launch_bounds__(RT, kSolverMinBlocks) k_tq_check(TqArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[32];
   SolverState* st = a.st;
@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(RT) k_tq_check(TqArgs a) {
 }
 
 // tail: ||b - A x|| / ||b|| (x = 0 when b = 0)
-__global__ void __launch_bounds__(RT) k_tq_tail(TqArgs a) {
+__global__ void __launch_bounds__(RT, kSolverMinBlocks) k_tq_tail(TqArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[32];
   SolverState* st = a.st;

@@ -33,7 +33,7 @@ def test_bicgstabl_vs_dense_lu(ell, dims, F):
     assert info["status"] == "ok", info
     xg = x.cpu().numpy()
     res = np.linalg.norm(b - oracle.spmv(p.rowptr, p.colind, vals, xg)) / np.linalg.norm(b)
-    assert res <= 1.5e-12
+    assert res <= 1e-12 * (1 + 1e-6)
     xs = oracle.dense_solve(p.rowptr, p.colind, vals, b)
     xo, io = oracle.bicgstabl(p.rowptr, p.colind, vals, b, ell=ell, tol=1e-12, maxit=10000)
     e_g = np.linalg.norm(xg - xs) / np.linalg.norm(xs)
@@ -52,7 +52,7 @@ def test_bicgstabl_box20_parity(ell):
     x, info = helm.solve(A, _dev(b), tol=1e-8, maxit=20000, method=helm.HELM_BICGSTABL, ell=ell)
     assert info["status"] == "ok", info
     xg = x.cpu().numpy()
-    assert np.linalg.norm(b - oracle.spmv(p.rowptr, p.colind, vals, xg)) / np.linalg.norm(b) <= 1.5e-8
+    assert np.linalg.norm(b - oracle.spmv(p.rowptr, p.colind, vals, xg)) / np.linalg.norm(b) <= 1e-8 * (1 + 1e-6)
     xo, io = oracle.bicgstabl(p.rowptr, p.colind, vals, b, ell=ell, tol=1e-8, maxit=20000)
     x_t, _ = oracle.bicgstab(p.rowptr, p.colind, vals, b, tol=1e-13, maxit=60000)
     nt = np.linalg.norm(x_t)

@@ -207,7 +207,7 @@ def test_bicgstab_vs_dense_lu(dims, F):
     xr, rinfo = oracle.bicgstab(p.rowptr, p.colind, vals, b, tol=1e-12, maxit=10000)
     xg = x.cpu().numpy()
     res = np.linalg.norm(b - oracle.spmv(p.rowptr, p.colind, vals, xg)) / np.linalg.norm(b)
-    assert res <= 1.5e-12
+    assert res <= 1e-12 * (1 + 1e-6)
     e_g = np.linalg.norm(xg - xs) / np.linalg.norm(xs)
     e_o = np.linalg.norm(xr - xs) / np.linalg.norm(xs)
     assert e_g <= max(1e-8, 2 * e_o)
@@ -232,7 +232,7 @@ def test_bicgstab_box20_parity(box20):
     assert info["status"] == "ok", info
     xg = x.cpu().numpy()
     res = np.linalg.norm(b - oracle.spmv(p.rowptr, p.colind, vals, xg)) / np.linalg.norm(b)
-    assert res <= 1.5e-8 and abs(res - info["relres_true"]) <= 1e-3 * res
+    assert res <= 1e-8 * (1 + 1e-6) and abs(res - info["relres_true"]) <= 1e-3 * res
     nt = np.linalg.norm(x_t)
     e_g = np.linalg.norm(xg - x_t) / nt
     e_o = np.linalg.norm(x_o - x_t) / nt

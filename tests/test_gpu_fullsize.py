@@ -47,7 +47,7 @@ def test_full_size_solve_meets_tolerance(cavity120, name, kw):
     xh = x.cpu().numpy()
     r = float(np.linalg.norm(b - Ah @ xh) / np.linalg.norm(b))
     print(f"cavity120 {name}: iters {info['iters']} relres {r:.3e}")
-    assert r <= 1.5 * cfg.tol
+    assert r <= cfg.tol * (1 + 1e-6)
     # both are b - A x with cancellation (A x ~ b): agreement to 1e-3 of the residual
     assert abs(r - info["relres_true"]) <= 1e-3 * r + 1e-15
     assert np.all(xh[p.dirichlet] == 0)  # identity rows with b = 0 keep x = 0

@@ -43,7 +43,7 @@ def test_jacobi_vs_dense_lu(method, dims, F):
     assert info["status"] == "ok", info
     xg = x.cpu().numpy()
     r = _relres(p, vals, b, xg)
-    assert r <= 1.5e-11 and abs(r - info["relres_true"]) <= 1e-3 * r + 1e-16
+    assert r <= 1e-11 * (1 + 1e-6) and abs(r - info["relres_true"]) <= 1e-3 * r + 1e-16
     xs = oracle.dense_solve(p.rowptr, p.colind, vals, b)
     cond = np.linalg.cond(oracle.densify(p.rowptr, p.colind, vals))
     assert np.linalg.norm(xg - xs) / np.linalg.norm(xs) <= max(1e-8, 10 * cond * 1e-11)
@@ -63,7 +63,7 @@ def test_jacobi_box20_10ppw_against_oracle():
     xg = x.cpu().numpy()
     print(f"box20_10ppw Jacobi: gpu iters {info['iters']} oracle iters {i_o['iters']}")
     assert abs(info["iters"] - i_o["iters"]) <= max(5, 0.1 * i_o["iters"])
-    assert _relres(p, vals, b, xg) <= 1.5 * cfg.tol
+    assert _relres(p, vals, b, xg) <= cfg.tol * (1 + 1e-6)
     e_g = np.linalg.norm(xg - x_t) / np.linalg.norm(x_t)
     e_o = np.linalg.norm(x_o - x_t) / np.linalg.norm(x_t)
     assert e_g <= max(1e-8, 2 * e_o)

@@ -48,7 +48,7 @@ def test_sweep_small_vs_oracle(dims, freqs, shared_b):
         vals = oracle.helmholtz_values(p.K, p.Mc, p.Bc, w[j])
         assert infos[j]["status"] == "ok", (j, infos[j])
         r = _relres(p, vals, bs[j], Xh[:, j])
-        assert r <= 1.5e-12 and abs(r - infos[j]["relres_true"]) <= 1e-3 * r + 1e-15
+        assert r <= 1e-12 * (1 + 1e-6) and abs(r - infos[j]["relres_true"]) <= 1e-3 * r + 1e-15
         xs = oracle.dense_solve(p.rowptr, p.colind, vals, bs[j])
         xo, _ = oracle.bicgstab(p.rowptr, p.colind, vals, bs[j], tol=1e-12, maxit=20000)
         e_g = np.linalg.norm(Xh[:, j] - xs) / np.linalg.norm(xs)
@@ -73,7 +73,7 @@ def test_sweep60_against_single_solves():
     for j in range(0, 64, 9):
         vals = oracle.helmholtz_values(p.K, p.Mc, p.Bc, w[j])
         assert infos[j]["status"] == "ok", (j, infos[j])
-        assert _relres(p, vals, b, Xh[:, j]) <= 1.5e-8
+        assert _relres(p, vals, b, Xh[:, j]) <= 1e-8 * (1 + 1e-6)
         A = helm.CsrMatrix.from_host(p.rowptr, p.colind, vals, device=DEV)
         x1, i1 = helm.solve(A, torch.as_tensor(b, device=DEV), tol=1e-12, maxit=60000)
         x_t = x1.cpu().numpy()
