@@ -365,7 +365,11 @@ helm_status helm_sweep_destroy(helm_sweep S);
  *   d_X     : complex128 solutions, x_j[i] = d_X[i * ldx + j], ldx >= nfreq
  *             (read first when o->use_x0).
  *   o       : tol, maxit, use_x0, deadline_s used (BiCGStab, FP64 only).
- *   h_infos : host helm_info[nfreq] or NULL; filled after one synchronisation.
+ *             A frequency reports HELM_OK only when its true residual is at
+ *             most tol; one whose recurrence met tol while its true residual
+ *             did not restarts from its x (the others stay frozen), its
+ *             iteration count continuing.
+ *   h_infos : host helm_info[nfreq] or NULL; filled after the last pass.
  * The first call on a sweep times three tile shapes of the batched SpMV and
  * keeps the fastest (autotuning).  Returns HELM_OK when every frequency
  * converged, else the first failing frequency's status.
@@ -373,6 +377,21 @@ helm_status helm_sweep_destroy(helm_sweep S);
 helm_status helm_sweep_solve(helm_sweep S, int32_t nfreq, const double* h_omega, const void* d_b,
                              int32_t b_ld, void* d_X, int32_t ldx, const helm_opts* o,
                              helm_info* h_infos, helm_stream_t stream);
+
+/*
+ * helm_sweep_spmv -- Y_j = A_j X_j for j < nfreq (1 <= nfreq <= 128), with
+ * A_j = K - w_j^2 M + i w_j B formed on the fly exactly as inside
+ * helm_sweep_solve (the same row sums: each entry fma(-w_j^2, M, K) +
+ * i w_j B, CSR order) -- the frequency sweep's product (Section 3's SpMV at
+ * the wavenumbers of Section 1, k_j = w_j / c).
+ *   h_omega : host double[nfreq].
+ *   d_X     : complex128, x_j[i] = d_X[i * ldx + j], ldx >= nfreq.
+ *   d_Y     : complex128 out, y_j[i] = d_Y[i * ldy + j], ldy >= nfreq; must
+ *             not alias d_X.
+ * Asynchronous (h_omega is copied before the call returns).
+ */
+helm_status helm_sweep_spmv(helm_sweep S, int32_t nfreq, const double* h_omega, const void* d_X, int32_t ldx,
+                            void* d_Y, int32_t ldy, helm_stream_t stream);
 
 /* helm_status_string -- static description of a status code. */
 const char* helm_status_string(helm_status s);

@@ -93,6 +93,7 @@ SIGNATURES = {
     "helm_sweep_destroy": (ctypes.c_int, [_P]),
     "helm_sweep_solve": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, ctypes.c_int32, _P, ctypes.c_int32,
                                         ctypes.POINTER(helm_opts), _P, _P]),
+    "helm_sweep_spmv": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, ctypes.c_int32, _P, ctypes.c_int32, _P]),
 }
 
 _lib = None
@@ -294,6 +295,16 @@ def helm_sweep_destroy(handle) -> None:
     _check(load_library().helm_sweep_destroy(handle), "helm_sweep_destroy")
 
 
+def helm_sweep_spmv(handle, omegas, X, Y, stream=None) -> None:
+    """Y[:, j] = A_j X[:, j] for the frequencies `omegas` (X, Y: n x F
+    complex128, row-major, device)."""
+    import numpy as np
+    w = np.ascontiguousarray(np.asarray(omegas, dtype=np.float64))
+    F = int(w.size)
+    _check(load_library().helm_sweep_spmv(handle, F, w.ctypes.data_as(ctypes.c_void_p), _ptr(X), int(X.stride(0)),
+                                          _ptr(Y), int(Y.stride(0)), _stream(stream)), "helm_sweep_spmv")
+
+
 def helm_sweep_solve(handle, omegas, b, X, opts: Optional[helm_opts] = None, stream=None):
     """Solve all frequencies; b is [n] (shared) or [n, F]; X is [n, F]
     complex128 (row-major).  Returns a list of per-frequency info dicts."""
@@ -337,6 +348,17 @@ class Sweep:
         _check_vector(X, self.n, torch.complex128, "X", F)
         infos = helm_sweep_solve(self.handle, omegas, b, X, default_opts(**opts))
         return X, infos
+
+    def matvec(self, omegas, X, Y=None):
+        """Y[:, j] = A_j X[:, j], the sweep's own on-the-fly product."""
+        import torch
+        F = len(omegas)
+        _check_vector(X, self.n, torch.complex128, "X", F)
+        if Y is None:
+            Y = torch.empty_like(X)
+        _check_vector(Y, self.n, torch.complex128, "Y", F)
+        helm_sweep_spmv(self.handle, omegas, X, Y)
+        return Y
 
     def close(self):
         if getattr(self, "handle", None):

@@ -152,6 +152,34 @@ __device__ bool sweep_grid_sum(const SweepArgs& a, const double (&v)[K], double*
   return true;
 }
 
+// Row i of A_j x for frequency j (w_j, w2 = w_j^2): the entries of A_j are
+// formed as (fma(-w2, M, K), w_j B) and multiplied in CSR order; rows of a
+// 32-row block where B = 0 take the real x complex product (bit-identical
+// for finite x: the skipped terms are exact zeros).  x[col * ld + j].
+__device__ __forceinline__ double2 sweep_row(const SweepDev& A, int32_t i, int j, double wj, double w2,
+                                             const double2* __restrict__ x, int64_t ld) {
+  const int64_t k0 = __ldg(A.rowptr + i), k1 = __ldg(A.rowptr + i + 1);
+  double2 acc = make_double2(0.0, 0.0);
+  if (A.bzero_blk[i >> 5] != 0) {
+#pragma unroll 4
+    for (int64_t k = k0; k < k1; ++k) {
+      const int32_t c = __ldg(A.colind + k);
+      const double are = fma(-w2, __ldg(A.M + k), __ldg(A.K + k));
+      const double2 xv = __ldg(x + static_cast<int64_t>(c) * ld + j);
+      acc.x = fma(are, xv.x, acc.x);
+      acc.y = fma(are, xv.y, acc.y);
+    }
+  } else {
+#pragma unroll 2
+    for (int64_t k = k0; k < k1; ++k) {
+      const int32_t c = __ldg(A.colind + k);
+      const double2 av = make_double2(fma(-w2, __ldg(A.M + k), __ldg(A.K + k)), wj * __ldg(A.B + k));
+      acc = cfma(av, __ldg(x + static_cast<int64_t>(c) * ld + j), acc);
+    }
+  }
+  return acc;
+}
+
 // Batched SpMV over the warp's (row, group) units: acc[j] = sum_k A_j[k] x[col][j].
 // Calls epi(i, lane_frequency, acc) for running frequencies.
 template <class Epi>
@@ -171,43 +199,46 @@ __device__ __forceinline__ void sweep_spmv(const SweepArgs& a, const double2* __
   for (int64_t u = gw; u < units; u += nwarps) {
     if (!grp_on) break;
     const int32_t i = static_cast<int32_t>(u / a.G);
-    const int64_t k0 = __ldg(a.A.rowptr + i), k1 = __ldg(a.A.rowptr + i + 1);
-    double2 acc = make_double2(0.0, 0.0);
-    const bool real_rows = a.A.bzero_blk[i >> 5] != 0;
-    if (real_rows) {
-#pragma unroll 4
-      for (int64_t k = k0; k < k1; ++k) {
-        const int32_t c = __ldg(a.A.colind + k);
-        const double are = fma(-w2, __ldg(a.A.M + k), __ldg(a.A.K + k));
-        const double2 xv = __ldg(x + static_cast<size_t>(c) * a.Fp + j);
-        acc.x = fma(are, xv.x, acc.x);
-        acc.y = fma(are, xv.y, acc.y);
-      }
-    } else {
-#pragma unroll 2
-      for (int64_t k = k0; k < k1; ++k) {
-        const int32_t c = __ldg(a.A.colind + k);
-        const double2 av = make_double2(fma(-w2, __ldg(a.A.M + k), __ldg(a.A.K + k)), wj * __ldg(a.A.B + k));
-        acc = cfma(av, __ldg(x + static_cast<size_t>(c) * a.Fp + j), acc);
-      }
-    }
+    const double2 acc = sweep_row(a.A, i, j, wj, w2, x, a.Fp);
     if (run) epi(i, j, acc);
   }
 }
 
-__global__ void k_sw_configure(SweepArgs a, double tol, int32_t maxit, int32_t use_x0, double deadline_s) {
+// Y_j = A_j X_j for the stand-alone batched product (helm_sweep_spmv): warp
+// per (row, 32-frequency group), lane = frequency, the solver's row sum.
+__global__ void __launch_bounds__(256) k_sw_apply(SweepDev A, int32_t F, int32_t G, const double* __restrict__ w,
+                                                  const double2* __restrict__ X, int32_t ldx, double2* __restrict__ Y,
+                                                  int32_t ldy) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t u = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+       u < static_cast<int64_t>(A.n) * G; u += nwarps) {
+    const int32_t i = static_cast<int32_t>(u / G);
+    const int j = static_cast<int>(u % G) * 32 + lane;
+    if (j >= F) continue;
+    const double wj = w[j];
+    Y[static_cast<int64_t>(i) * ldy + j] = sweep_row(A, i, j, wj, wj * wj, X, ldx);
+  }
+}
+
+// fresh: every frequency starts (iteration counts from 0).  Otherwise a
+// restart from x: the frequencies with restart[j] != 0 run again (their
+// iteration counts continue), the others keep their status and result.
+__global__ void k_sw_configure(SweepArgs a, double tol, int32_t maxit, int32_t use_x0, double deadline_s,
+                               int32_t fresh, const int32_t* __restrict__ restart) {
   SolverState* st = a.st;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     st->tol = tol;
     st->maxit = maxit;
     st->use_x0 = use_x0;
     st->deadline_ns = deadline_s > 0.0 ? static_cast<unsigned long long>(deadline_s * 1e9) : 0ull;
-    st->t0 = globaltimer_ns();
+    if (fresh) st->t0 = globaltimer_ns();
     st->status = ST_RUNNING;
   }
   for (int j = threadIdx.x; j < a.Fp; j += blockDim.x) {
+    if (!fresh && !(j < a.F && restart[j] != 0)) continue;
     a.status[j] = j < a.F ? ST_RUNNING : HELM_OK;
-    a.iters[j] = 0;
+    if (fresh) a.iters[j] = 0;
     a.phase[j] = PH_RUN;
     a.relres[j] = 0.0;
     a.relres_true[j] = 0.0;
@@ -261,7 +292,7 @@ __global__ void __launch_bounds__(512) k_sw_init(SweepArgs a) {
     sweep_spmv(a, a.x, body);
   } else {
     const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
-    const bool run = j < a.F;
+    const bool run = j < a.F && a.status[j] == ST_RUNNING;
     for (int64_t u = gw; u < static_cast<int64_t>(a.A.n) * a.G; u += nwarps) {
       const int32_t i = static_cast<int32_t>(u / a.G);
       if (run) {
@@ -273,6 +304,7 @@ __global__ void __launch_bounds__(512) k_sw_init(SweepArgs a) {
   double tot[4];
   if (!sweep_grid_sum<4>(a, part, sh, a.tickets + TK_INIT, tot)) return;
   for (int jj = threadIdx.x; jj < a.F && jj == (int)threadIdx.x; jj += blockDim.x) {
+    if (a.status[jj] != ST_RUNNING) continue;  // frozen by a restart of other frequencies
     const double bn = sqrt(tot[0]);
     a.bnorm[jj] = bn;
     int status = ST_RUNNING;
@@ -487,13 +519,7 @@ __global__ void __launch_bounds__(512) k_sw_tail(SweepArgs a) {
   const double wj = a.w[j], w2 = wj * wj;
   for (int64_t u = gw; u < static_cast<int64_t>(a.A.n) * a.G; u += nwarps) {
     const int32_t i = static_cast<int32_t>(u / a.G);
-    const int64_t k0 = __ldg(a.A.rowptr + i), k1 = __ldg(a.A.rowptr + i + 1);
-    double2 acc = make_double2(0.0, 0.0);
-    for (int64_t k = k0; k < k1; ++k) {
-      const int32_t c = __ldg(a.A.colind + k);
-      const double2 av = make_double2(fma(-w2, __ldg(a.A.M + k), __ldg(a.A.K + k)), wj * __ldg(a.A.B + k));
-      acc = cfma(av, a.x[static_cast<size_t>(c) * a.Fp + j], acc);
-    }
+    const double2 acc = sweep_row(a.A, i, j, wj, w2, a.x, a.Fp);
     if (j < a.F)
       part[0] = cabs2_acc(csub(a.b[a.b_ld ? static_cast<size_t>(i) * a.b_ld + j : static_cast<size_t>(i)], acc),
                           part[0]);
@@ -556,11 +582,13 @@ struct helm_sweep_s {
   double2* vec = nullptr;         // 7 vectors [n][Fcap]
   double2* scal = nullptr;        // 4 [Fcap]
   double* dscal = nullptr;        // 3 [Fcap] + w [Fcap]
-  int32_t* iscal = nullptr;       // 3 [Fcap] + groups [Fcap / 32]
+  int32_t* iscal = nullptr;       // 3 [Fcap] + groups [Fcap / 32] + restart flags [Fcap]
   SolverState* state = nullptr;
   double* partials = nullptr;
   size_t partials_cap = 0;
   unsigned int* tickets = nullptr;
+  double* wapply = nullptr;       // frequencies of helm_sweep_spmv
+  int32_t wapply_cap = 0;
   int warps_per_block = 8;        // autotuned
   bool tuned = false;
   std::mutex mu;
@@ -589,7 +617,7 @@ helm_status sweep_alloc(helm_sweep S, int32_t Fp, size_t blocks) {
     HELM_CUDA_TRY(cudaMalloc(&S->vec, 7 * nf * sizeof(double2)));
     HELM_CUDA_TRY(cudaMalloc(&S->scal, 4 * static_cast<size_t>(Fp) * sizeof(double2)));
     HELM_CUDA_TRY(cudaMalloc(&S->dscal, 4 * static_cast<size_t>(Fp) * sizeof(double)));
-    HELM_CUDA_TRY(cudaMalloc(&S->iscal, (3 * static_cast<size_t>(Fp) + Fp / 32) * sizeof(int32_t)));
+    HELM_CUDA_TRY(cudaMalloc(&S->iscal, (4 * static_cast<size_t>(Fp) + Fp / 32) * sizeof(int32_t)));
     S->Fcap = Fp;
     if (S->graph.exec) {
       cudaGraphExecDestroy(S->graph.exec);
@@ -762,7 +790,7 @@ helm_status autotune(helm_sweep S, int32_t F, int32_t Fp, cudaStream_t s) {
     if (result != HELM_OK) break;
     SweepArgs a = make_args(S, F, Fp, nullptr, 0);
     // every group active, every frequency running, p = 0 (timing only)
-    k_sw_configure<<<1, 256, 0, s>>>(a, 0.0, 1, 0, 0.0);
+    k_sw_configure<<<1, 256, 0, s>>>(a, 0.0, 1, 0, 0.0, 1, nullptr);
     cudaMemsetAsync(a.p, 0, static_cast<size_t>(S->n) * Fp * sizeof(double2), s);
     k_sw_spmv_probe<<<sh.grid, sh.threads, 0, s>>>(a);
     cudaEventRecord(e0, s);
@@ -843,6 +871,7 @@ helm_status helm_sweep_destroy(helm_sweep S) {
   cudaFree(S->state);
   cudaFree(S->partials);
   cudaFree(S->tickets);
+  cudaFree(S->wapply);
   (void)cudaGetLastError();
   if (prev >= 0) cudaSetDevice(prev);
   delete S;
@@ -905,30 +934,49 @@ helm_status helm_sweep_solve(helm_sweep S, int32_t nfreq, const double* h_omega,
       }
     }
   }
-  k_sw_configure<<<1, 256, 0, s>>>(a, opts.tol, opts.maxit, opts.use_x0, opts.deadline_s);
-  HELM_CUDA_TRY(cudaGetLastError());
-  if (S->graph.exec && !bcopy) {
-    HELM_CUDA_TRY(cudaGraphLaunch(S->graph.exec, s));
-  } else {
-    SolverState hs;
-    k_sw_init<<<sh.grid, sh.threads, sh.smem, s>>>(a);
-    for (;;) {
-      for (int k = 0; k < 8; ++k) enqueue_sweep_body(a, sh, s);
-      HELM_CUDA_TRY(cudaGetLastError());
-      HELM_CUDA_TRY(cudaMemcpyAsync(&hs, a.st, sizeof(hs), cudaMemcpyDeviceToHost, s));
-      HELM_CUDA_TRY(cudaStreamSynchronize(s));
-      if (hs.status != ST_RUNNING) break;
+  // restart flags of the frequencies that run again from their x
+  int32_t* d_restart = S->iscal + 3 * static_cast<size_t>(Fp) + Fp / 32;
+  std::vector<int32_t> status(Fp), iters(Fp), restart(Fp, 0), restarts(nfreq, 0);
+  std::vector<double> relres(Fp), relres_true(Fp);
+  for (int32_t fresh = 1, use_x0 = opts.use_x0 ? 1 : 0;; fresh = 0, use_x0 = 1) {
+    k_sw_configure<<<1, 256, 0, s>>>(a, opts.tol, opts.maxit, use_x0, opts.deadline_s, fresh, d_restart);
+    HELM_CUDA_TRY(cudaGetLastError());
+    if (S->graph.exec && !bcopy) {
+      HELM_CUDA_TRY(cudaGraphLaunch(S->graph.exec, s));
+    } else {
+      SolverState hs;
+      k_sw_init<<<sh.grid, sh.threads, sh.smem, s>>>(a);
+      for (;;) {
+        for (int k = 0; k < 8; ++k) enqueue_sweep_body(a, sh, s);
+        HELM_CUDA_TRY(cudaGetLastError());
+        HELM_CUDA_TRY(cudaMemcpyAsync(&hs, a.st, sizeof(hs), cudaMemcpyDeviceToHost, s));
+        HELM_CUDA_TRY(cudaStreamSynchronize(s));
+        if (hs.status != ST_RUNNING) break;
+      }
+      k_sw_tail<<<sh.grid, sh.threads, sh.smem, s>>>(a);
     }
-    k_sw_tail<<<sh.grid, sh.threads, sh.smem, s>>>(a);
+    HELM_CUDA_TRY(cudaMemcpyAsync(status.data(), a.status, Fp * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    HELM_CUDA_TRY(cudaMemcpyAsync(iters.data(), a.iters, Fp * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    HELM_CUDA_TRY(cudaMemcpyAsync(relres.data(), a.relres, Fp * sizeof(double), cudaMemcpyDeviceToHost, s));
+    HELM_CUDA_TRY(
+        cudaMemcpyAsync(relres_true.data(), a.relres_true, Fp * sizeof(double), cudaMemcpyDeviceToHost, s));
+    HELM_CUDA_TRY(cudaStreamSynchronize(s));
+    // a frequency whose recurrence met tol while its true residual did not
+    // restarts from its x (iterations permitting), as the single solve does
+    bool any = false;
+    for (int j = 0; j < Fp; ++j) {
+      restart[j] = j < nfreq && status[j] == HELM_OK && relres_true[j] > opts.tol && iters[j] < opts.maxit;
+      if (restart[j]) {
+        any = true;
+        restarts[j] += 1;
+      }
+    }
+    if (!any) break;
+    HELM_CUDA_TRY(cudaMemcpyAsync(d_restart, restart.data(), Fp * sizeof(int32_t), cudaMemcpyHostToDevice, s));
   }
   k_sw_copy<<<vec_grid_for(static_cast<int64_t>(S->n) * nfreq), 256, 0, s>>>(S->n, nfreq, Fp, a.x, Fp,
                                                                            static_cast<double2*>(d_X), ldx);
-  std::vector<int32_t> status(Fp), iters(Fp);
-  std::vector<double> relres(Fp), relres_true(Fp);
-  HELM_CUDA_TRY(cudaMemcpyAsync(status.data(), a.status, Fp * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-  HELM_CUDA_TRY(cudaMemcpyAsync(iters.data(), a.iters, Fp * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-  HELM_CUDA_TRY(cudaMemcpyAsync(relres.data(), a.relres, Fp * sizeof(double), cudaMemcpyDeviceToHost, s));
-  HELM_CUDA_TRY(cudaMemcpyAsync(relres_true.data(), a.relres_true, Fp * sizeof(double), cudaMemcpyDeviceToHost, s));
+  HELM_CUDA_TRY(cudaGetLastError());
   if (bcopy) cudaFreeAsync(bcopy, s);
   HELM_CUDA_TRY(cudaStreamSynchronize(s));
   helm_status worst = HELM_OK;
@@ -937,7 +985,7 @@ helm_status helm_sweep_solve(helm_sweep S, int32_t nfreq, const double* h_omega,
     if (sj == HELM_OK && !(relres_true[j] <= opts.tol)) sj = HELM_ERR_NOT_CONVERGED;
     if (h_infos) {
       h_infos[j].iters = iters[j];
-      h_infos[j].restarts = 0;
+      h_infos[j].restarts = restarts[j];
       h_infos[j].relres_recur = relres[j];
       h_infos[j].relres_true = relres_true[j];
       h_infos[j].status = sj;
@@ -946,6 +994,34 @@ helm_status helm_sweep_solve(helm_sweep S, int32_t nfreq, const double* h_omega,
     if (sj != HELM_OK && worst == HELM_OK) worst = sj;
   }
   return worst;
+}
+
+helm_status helm_sweep_spmv(helm_sweep S, int32_t nfreq, const double* h_omega, const void* d_X, int32_t ldx,
+                            void* d_Y, int32_t ldy, helm_stream_t stream) {
+  if (!S || nfreq < 1 || nfreq > kMaxF || !h_omega || ldx < nfreq || ldy < nfreq) return HELM_ERR_INVALID;
+  if (S->n == 0) return HELM_OK;
+  if (!d_X || !d_Y || d_X == d_Y || !aligned(d_X, 16) || !aligned(d_Y, 16)) return HELM_ERR_INVALID;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> lk(S->mu);
+  const int32_t Fp = (nfreq + 31) / 32 * 32;
+  if (S->wapply_cap < Fp) {
+    cudaFree(S->wapply);
+    S->wapply = nullptr;
+    S->wapply_cap = 0;
+    HELM_CUDA_TRY(cudaMalloc(&S->wapply, Fp * sizeof(double)));
+    S->wapply_cap = Fp;
+  }
+  // the frequencies are copied from a pageable host buffer: the copy is
+  // complete when cudaMemcpyAsync returns, so h_omega may be reused at once
+  HELM_CUDA_TRY(cudaMemcpyAsync(S->wapply, h_omega, nfreq * sizeof(double), cudaMemcpyHostToDevice, s));
+  const SweepDev A{S->n, S->nnz, S->rowptr, S->colind, S->K, S->M, S->B, S->bzero_blk};
+  const int G = Fp / 32;
+  const int64_t warps = static_cast<int64_t>(S->n) * G;
+  const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((warps + 7) / 8, static_cast<int64_t>(S->num_sms) * 8)));
+  k_sw_apply<<<grid, 256, 0, s>>>(A, nfreq, G, S->wapply, static_cast<const double2*>(d_X), ldx,
+                                  static_cast<double2*>(d_Y), ldy);
+  HELM_CUDA_TRY(cudaGetLastError());
+  return HELM_OK;
 }
 
 }  // extern "C"

@@ -110,3 +110,40 @@ def test_mixed_warm_start():
     assert info["status"] == "ok", info
     assert np.linalg.norm(x.cpu().numpy() - xs) <= 1e-9 * np.linalg.norm(xs)
     A.close()
+
+
+@pytest.mark.parametrize("name", ["cavity120", "cavity200"])
+def test_mixed_full_size_to_1e10(name):
+    """The full-size cavities (376,431 and 1,644,381 unknowns) to 1e-10 with
+    the default inner tolerance: status ok, the FP64 true residual recomputed
+    on the host (scipy, from the generator's matrix) at most 1e-10 and equal
+    to the reported one, and the solution gate against a tight FP64 solve
+    (1e-12): ||x_mixed - x_tight|| <= max(1e-8, 2 ||x_fp64 - x_tight||) with
+    x_fp64 the FP64 solve at the same 1e-10.  The error of the mixed solution
+    against the FP64 one is printed."""
+    import scipy.sparse as sp
+    cfg = g.CONFIGS[name]
+    p = g.assemble(cfg)
+    vals = g.helmholtz_values(p, cfg.F)
+    b = g.source(p)
+    A = helm.CsrMatrix.from_host(p.rowptr, p.colind, vals, device=DEV)
+    bd = _dev(b)
+    x32, i32 = helm.solve(A, bd, tol=1e-10, maxit=400000, precision=helm.HELM_PREC_MIXED, deadline_s=400.0)
+    assert i32["status"] == "ok", i32
+    x64, i64 = helm.solve(A, bd, tol=1e-10, maxit=300000, deadline_s=400.0)
+    assert i64["status"] == "ok", i64
+    xt, it = helm.solve(A, bd, tol=1e-12, maxit=400000, deadline_s=400.0)
+    assert it["status"] == "ok", it
+    A.close()
+    Ah = sp.csr_matrix((vals, p.colind, p.rowptr), shape=(p.n, p.n))
+    xm = x32.cpu().numpy()
+    r = float(np.linalg.norm(b - Ah @ xm) / np.linalg.norm(b))
+    assert r <= 1e-10 * (1 + 1e-6) and abs(r - i32["relres_true"]) <= 1e-3 * r
+    xt = xt.cpu().numpy()
+    nt = np.linalg.norm(xt)
+    e_m = np.linalg.norm(xm - xt) / nt
+    e_f = np.linalg.norm(x64.cpu().numpy() - xt) / nt
+    e_mf = np.linalg.norm(xm - x64.cpu().numpy()) / np.linalg.norm(x64.cpu().numpy())
+    print(f"{name} mixed: {i32['iters']} complex64 iterations in {i32['restarts']} refinement steps; FP64 "
+          f"{i64['iters']} iterations; error vs tight {e_m:.2e} (FP64 at 1e-10: {e_f:.2e}); vs FP64 {e_mf:.2e}")
+    assert e_m <= max(1e-8, 2 * e_f), (e_m, e_f)

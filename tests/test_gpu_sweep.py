@@ -57,29 +57,118 @@ def test_sweep_small_vs_oracle(dims, freqs, shared_b):
     S.close()
 
 
-def test_sweep60_against_single_solves():
-    """60x30x25 cavity, 64 frequencies 100-1000 Hz: each frequency against the
-    oracle-assembled A_j through the single-frequency GPU solver (same gate),
-    and its true residual recomputed by the oracle."""
+def test_sweep60_against_oracle():
+    """60x30x25 cavity, 64 frequencies 100-1000 Hz at 1e-8 (the benchmark's
+    sweep).  Every frequency: status ok and the true residual, recomputed with
+    the oracle's SpMV on the oracle-assembled A_j, at most tol.  Five
+    frequencies spread over the band, the hardest (1000 Hz) among them,
+    against the oracle's BiCGStab on A_j: ||x_gpu - x_tight|| / ||x_tight||
+    <= max(1e-8, 2 ||x_oracle - x_tight|| / ||x_tight||), x_tight the
+    oracle at 1e-13.  The oracle runs on host threads meanwhile."""
+    from concurrent.futures import ThreadPoolExecutor
     cfg = g.CONFIGS["sweep60"]
     p = g.assemble(cfg)
     b = g.source(p)
     w = [g.omega(f) for f in cfg.freqs]
-    S = helm.Sweep(p.rowptr, p.colind, p.K, p.Mc, p.Bc, device=DEV)
-    X, infos = S.solve(w, torch.as_tensor(b, device=DEV), tol=1e-8, maxit=30000)
-    Xh = X.cpu().numpy()
-    iters = [i["iters"] for i in infos]
-    print(f"sweep60 iterations per frequency: min {min(iters)} max {max(iters)} total {sum(iters)}")
-    for j in range(0, 64, 9):
+    picks = [0, 16, 32, 48, 63]
+
+    def oracle_solve(job):
+        j, tol = job
         vals = oracle.helmholtz_values(p.K, p.Mc, p.Bc, w[j])
-        assert infos[j]["status"] == "ok", (j, infos[j])
-        assert _relres(p, vals, b, Xh[:, j]) <= 1e-8 * (1 + 1e-6)
-        A = helm.CsrMatrix.from_host(p.rowptr, p.colind, vals, device=DEV)
-        x1, i1 = helm.solve(A, torch.as_tensor(b, device=DEV), tol=1e-12, maxit=60000)
-        x_t = x1.cpu().numpy()
-        err = np.linalg.norm(Xh[:, j] - x_t) / np.linalg.norm(x_t)
-        assert err <= 1e-6, (j, err)       # 1e-8 residual on an indefinite system
-        A.close()
+        x, info = oracle.bicgstab(p.rowptr, p.colind, vals, b, tol=tol, maxit=60000)
+        assert info["status"] == "ok", (j, tol, info)
+        return x
+
+    with ThreadPoolExecutor(max_workers=len(picks) * 2) as ex:
+        futs = {(j, tol): ex.submit(oracle_solve, (j, tol)) for j in picks for tol in (1e-8, 1e-13)}
+        S = helm.Sweep(p.rowptr, p.colind, p.K, p.Mc, p.Bc, device=DEV)
+        X, infos = S.solve(w, torch.as_tensor(b, device=DEV), tol=cfg.tol, maxit=30000)
+        Xh = X.cpu().numpy()
+        S.close()
+        iters = [i["iters"] for i in infos]
+        print(f"sweep60 iterations per frequency: min {min(iters)} max {max(iters)} total {sum(iters)}, "
+              f"restarts {sum(i['restarts'] for i in infos)}")
+        for j in range(len(w)):
+            vals = oracle.helmholtz_values(p.K, p.Mc, p.Bc, w[j])
+            assert infos[j]["status"] == "ok", (j, infos[j])
+            r = _relres(p, vals, b, Xh[:, j])
+            assert r <= cfg.tol * (1 + 1e-6) and abs(r - infos[j]["relres_true"]) <= 1e-3 * r, (j, r, infos[j])
+        for j in picks:
+            x_o, x_t = futs[(j, 1e-8)].result(), futs[(j, 1e-13)].result()
+            nt = np.linalg.norm(x_t)
+            e_g = np.linalg.norm(Xh[:, j] - x_t) / nt
+            e_o = np.linalg.norm(x_o - x_t) / nt
+            print(f"  F = {cfg.freqs[j]:.1f} Hz: gpu error {e_g:.2e}, oracle error {e_o:.2e}, iters {iters[j]}")
+            assert e_g <= max(1e-8, 2 * e_o), (j, e_g, e_o)
+
+
+def test_sweep_operator_entries_and_product():
+    """The sweep forms A_j = K - w_j^2 M + i w_j B on the fly.  Applied to
+    unit vectors e_c, its product (helm_sweep_spmv, the solver's own row sum)
+    returns column c of A_j: every stored entry equals the oracle's assembly
+    to the rounding of its terms, 2^-52 (|K| + w^2 |M| + w |B|) (an fma
+    against a multiply and a subtract), and every other entry is exactly
+    zero.  Columns at an interior node, on the impedance face (complex
+    entries) and next to the Dirichlet plane.  A random X against the
+    oracle's SpMV of the explicitly assembled A_j, 1e-13 sum |a||x| per row."""
+    cfg = g.CONFIGS["sweep60"]
+    p = g.assemble(cfg)
+    w = [g.omega(f) for f in cfg.freqs]
+    F = len(w)
+    nx, ny, nz = cfg.nx + 1, cfg.ny + 1, cfg.nz + 1
+    node = lambda i, j, k: i + nx * (j + ny * k)  # noqa: E731
+    cols = [node(30, 15, 12), node(17, 9, nz - 1), node(41, 22, 1), node(0, 0, nz - 1)]
+    S = helm.Sweep(p.rowptr, p.colind, p.K, p.Mc, p.Bc, device=DEV)
+    for c in cols:
+        X = np.zeros((p.n, F), complex)
+        X[c, :] = 1.0
+        Y = S.matvec(w, torch.as_tensor(X, device=DEV)).cpu().numpy()
+        k0, k1 = p.rowptr[c], p.rowptr[c + 1]
+        ci = p.colind[k0:k1]
+        off = np.ones(p.n, bool)
+        off[ci] = False
+        for j in range(F):
+            a = oracle.helmholtz_values(p.K, p.Mc, p.Bc, w[j])[k0:k1]
+            bound = 2.0 ** -52 * (np.abs(p.K[k0:k1]) + w[j] ** 2 * np.abs(p.Mc[k0:k1]) + w[j] * np.abs(p.Bc[k0:k1]))
+            assert np.all(np.abs(Y[ci, j] - a) <= bound), (c, j, np.max(np.abs(Y[ci, j] - a) / bound))
+            assert np.all(Y[off, j] == 0)
+    Xr = np.stack([g.complex_vector(p.n, 40 + j) for j in range(F)], axis=1)
+    Y = S.matvec(w, torch.as_tensor(Xr, device=DEV)).cpu().numpy()
+    for j in range(0, F, 7):
+        vals = oracle.helmholtz_values(p.K, p.Mc, p.Bc, w[j])
+        yr = oracle.spmv(p.rowptr, p.colind, vals, Xr[:, j])
+        ab = oracle.spmv(p.rowptr, p.colind, np.abs(vals), np.abs(Xr[:, j])).real
+        assert np.all(np.abs(Y[:, j] - yr) <= 1e-13 * ab + 1e-300)
+    S.close()
+
+
+def test_sweep_restarts_a_frequency_whose_true_residual_misses_tol():
+    """At a tolerance near rounding level the recurrence of some frequencies
+    meets tol before their true residual does; those restart from their x
+    while the others stay frozen, and each frequency reports ok only with its
+    true residual (recomputed by the oracle) at most tol."""
+    cfg = g.tiny_config(8, 6, 5, h=0.1, seed=2)
+    p = g.assemble(cfg)
+    freqs = [300.0, 500.0, 700.0, 900.0]
+    w = [g.omega(f) for f in freqs]
+    b = g.source(p) + 0.1 * g.complex_vector(p.n, 4) * (~p.dirichlet)
+    S = helm.Sweep(p.rowptr, p.colind, p.K, p.Mc, p.Bc, device=DEV)
+    restarted = 0
+    for tol in (1e-13, 1e-15):
+        X, infos = S.solve(w, torch.as_tensor(b, device=DEV), tol=tol, maxit=3000)
+        Xh = X.cpu().numpy()
+        for j in range(len(w)):
+            vals = oracle.helmholtz_values(p.K, p.Mc, p.Bc, w[j])
+            r = _relres(p, vals, b, Xh[:, j])
+            # at rounding level the residual itself carries ~1 % rounding
+            # (b - A x cancels): GPU and oracle agree to 5 %
+            assert abs(r - infos[j]["relres_true"]) <= 0.05 * r, (j, tol, r, infos[j])
+            if infos[j]["status"] == "ok":
+                assert infos[j]["relres_true"] <= tol and r <= 1.05 * tol, (j, tol, r, infos[j])
+            else:
+                assert infos[j]["status"] == "not_converged" and infos[j]["relres_true"] > tol
+            restarted += infos[j]["restarts"]
+    assert restarted >= 1
     S.close()
 
 
