@@ -149,6 +149,15 @@ def real_row_mask(p, vals):
     return ~blk_complex[np.arange(p.n) // 32]
 
 
+def workload_config(p, cfg, ws):
+    """The `config` of the JSON line (the same for both arms)."""
+    return {"workload": f"{WORKLOAD}: Q1 Helmholtz box 120x60x50, n={p.n}, nnz={p.nnz}, F={cfg.F:.1f} Hz, "
+                        f"BiCGStab to rel. residual {cfg.tol:g}, complex128",
+            "n": p.n, "nnz": p.nnz, "tol": cfg.tol, "parallelism": f"replicas x{ws}",
+            "l2": "inputs larger than L2 (matrix 207 MB vs 129 MB L2); Krylov vectors L2-resident "
+                  "inside a solve by design"}
+
+
 def build_problem(cfg):
     p = helmgen.assemble(cfg)
     vals = helmgen.helmholtz_values(p, cfg.F)
@@ -295,11 +304,7 @@ def run_gpu(args):
         "metric": METRIC, "value": round(value, 4), "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{WORKLOAD}: Q1 Helmholtz box 120x60x50, n={p.n}, nnz={p.nnz}, F={cfg.F:.1f} Hz, "
-                               f"BiCGStab to rel. residual {cfg.tol:g}, complex128",
-                   "n": p.n, "nnz": p.nnz, "tol": cfg.tol, "parallelism": f"replicas x{ws}",
-                   "l2": "inputs larger than L2 (matrix 207 MB vs 129 MB L2); Krylov vectors L2-resident "
-                         "inside a solve by design"},
+        "config": workload_config(p, cfg, ws),
         "iters_per_solve": iters, "converged": ok, "relres_true_host": relres_host,
         "spmv_ms": round(spmv_ms, 5), "spmv_hbm_gbs": round(spmv_gbs, 1),
         "spmv_hbm_frac": round(spmv_gbs / peaks.get("hbm_gbs", 6800.0), 4),
@@ -309,10 +314,15 @@ def run_gpu(args):
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }
-    if rank == 0:
-        line["cpu_baseline"] = cpu_baseline(p, vals, b, iters[0] if iters else 1, args)
-        print(json.dumps(line), flush=True)
     A.close()
+    if rank == 0:
+        base = cpu_baseline(p, vals, b, iters[0] if iters else 1, args)
+        if "value" not in base["cpu_baseline"]:
+            base["cpu_baseline"] = base["cpu_baseline_1core"]
+        line.update(base)
+        if args.extensions == "on":
+            line["extensions"] = extension_summary(dev, args)
+        print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -320,23 +330,157 @@ def run_gpu(args):
 
 # ---------------------------------------------------------------- CPU oracle
 
-def oracle_iteration_time(p, vals, b, iters: int):
-    """Seconds per BiCGStab iteration of the CPU oracle, from a capped run."""
+def oracle_iteration_time(p, vals, b, iters: int, openmp: bool = False):
+    """Seconds per BiCGStab iteration of the CPU oracle, from a capped run
+    (openmp: its all-core build)."""
     import oracle
-    oracle.build()
+    oracle.build(openmp=openmp)
+    oracle.bicgstab(p.rowptr, p.colind, vals, b, tol=1e-30, maxit=1, openmp=openmp)  # load, page in
     t0 = time.perf_counter()
-    _, info = oracle.bicgstab(p.rowptr, p.colind, vals, b, tol=1e-30, maxit=iters)
+    _, info = oracle.bicgstab(p.rowptr, p.colind, vals, b, tol=1e-30, maxit=iters, openmp=openmp)
     dt = time.perf_counter() - t0
     return dt / max(info["iters"], 1), info["iters"], dt
 
 
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
 def cpu_baseline(p, vals, b, iters_per_solve: int, args):
+    """The oracle on the host cores: all of them (its -fopenmp build of the
+    same source, as `cpu_baseline`) and one (the sequential build, as
+    `cpu_baseline_1core`), each on a sample of iterations of the full system
+    scaled by the GPU solve's iteration count."""
     sample_iters = args.cpu_sample_iters
-    t_it, done, dt = oracle_iteration_time(p, vals, b, sample_iters)
-    solves_per_s = 1.0 / (t_it * iters_per_solve)
-    return {"value": solves_per_s, "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": f"{done} BiCGStab iterations of the oracle on the full {WORKLOAD} system "
-                      f"({dt:.1f} s); solves/s = 1 / (s per iteration x {iters_per_solve} iterations per solve)"}
+    out = {}
+    for key, omp in (("cpu_baseline", True), ("cpu_baseline_1core", False)):
+        try:
+            t_it, done, dt = oracle_iteration_time(p, vals, b, sample_iters, openmp=omp)
+        except Exception as e:  # no OpenMP runtime on the host: the 1-core figure stands alone
+            out[key] = {"unavailable": f"{type(e).__name__}: {e}"[:200]}
+            continue
+        cores = host_cores() if omp else 1
+        out[key] = {"value": 1.0 / (t_it * iters_per_solve), "unit": "solves/s", "cores": cores, "kind": "oracle",
+                    "sample": f"{done} BiCGStab iterations of the oracle ({'-fopenmp build, ' if omp else ''}"
+                              f"{cores} thread{'s' if cores > 1 else ''}) on the full {WORKLOAD} system ({dt:.1f} s); "
+                              f"solves/s = 1 / (s per iteration x {iters_per_solve} iterations per solve)"}
+    return out
+
+
+def extension_summary(dev, args):
+    """One pass of each of the other workloads, for the default line: the
+    20x20x20 box (config 1, solves/s), the 64-frequency sweep on the 60x30x25
+    cavity (config 4: batched against 64 single-frequency solves), mixed
+    precision against FP64 on the 200x100x80 cavity at 1e-10 (config 3) and
+    the adjoint gradient on the 80x40x32 cavity (config 5: backward against
+    forward).  Wall-clock seconds around synchronised GPU work."""
+    import torch
+
+    import paper_2112_11880_gb300 as helm
+    from paper_2112_11880_gb300 import autograd as hgrad
+    out = {}
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return r, time.perf_counter() - t0
+
+    # config 1
+    cfg = helmgen.CONFIGS["box20"]
+    p, vals, bh = build_problem(cfg)
+    A = helm.CsrMatrix.from_host(p.rowptr, p.colind, vals, device=dev)
+    b = torch.as_tensor(bh, device=dev)
+    x = torch.empty_like(b)
+    o = helm.default_opts(tol=cfg.tol, maxit=100000)
+    for _ in range(2):
+        helm.helm_bicgstab_solve(A.handle, b, x, o)
+    reps = 10
+    infos, dt = timed(lambda: [helm.helm_bicgstab_solve(A.handle, b, x, o) for _ in range(reps)])
+    out["box20"] = {"solves_per_s": round(reps / dt, 3), "iters": infos[-1]["iters"],
+                    "relres_true": infos[-1]["relres_true"], "status": infos[-1]["status"]}
+    A.close()
+
+    # config 4
+    cfg = helmgen.CONFIGS["sweep60"]
+    p = helmgen.assemble(cfg)
+    b = torch.as_tensor(helmgen.source(p), device=dev)
+    w = [helmgen.omega(f) for f in cfg.freqs]
+    S = helm.Sweep(p.rowptr, p.colind, p.K, p.Mc, p.Bc, device=dev)
+    S.solve(w, b, tol=cfg.tol, maxit=50000)  # warm-up (and tile autotuning)
+    (X, infos), t_sweep = timed(lambda: S.solve(w, b, tol=cfg.tol, maxit=50000))
+    S.close()
+    t_single, it_single, ok_single = 0.0, 0, True
+    for F in cfg.freqs:
+        A = helm.CsrMatrix.from_host(p.rowptr, p.colind, helmgen.helmholtz_values(p, F), device=dev)
+        x = torch.empty_like(b)
+        o = helm.default_opts(tol=cfg.tol, maxit=50000)
+        helm.helm_bicgstab_solve(A.handle, b, x, o)
+        info, dt = timed(lambda: helm.helm_bicgstab_solve(A.handle, b, x, o))
+        t_single += dt
+        it_single += info["iters"]
+        ok_single &= info["status"] == "ok"
+        A.close()
+    out["sweep60"] = {"frequencies": len(w), "tol": cfg.tol,
+                      "batched_freq_solves_per_s": round(len(w) / t_sweep, 3),
+                      "single_freq_solves_per_s": round(len(w) / t_single, 3),
+                      "speedup": round(t_single / t_sweep, 3), "batched_s": round(t_sweep, 3),
+                      "single_s": round(t_single, 3), "converged": all(i["status"] == "ok" for i in infos) and ok_single,
+                      "worst_relres_true": max(i["relres_true"] for i in infos),
+                      "iters_batched_total": sum(i["iters"] for i in infos), "iters_single_total": it_single}
+
+    # config 3
+    cfg = helmgen.CONFIGS["cavity200"]
+    p, vals, bh = build_problem(cfg)
+    A = helm.CsrMatrix.from_host(p.rowptr, p.colind, vals, device=dev)
+    b = torch.as_tensor(bh, device=dev)
+    x64, x32 = torch.empty_like(b), torch.empty_like(b)
+    i64, t64 = timed(lambda: helm.helm_bicgstab_solve(A.handle, b, x64, helm.default_opts(
+        tol=cfg.tol, maxit=args.mixed_maxit, deadline_s=600.0)))
+    i32, t32 = timed(lambda: helm.helm_bicgstab_solve(A.handle, b, x32, helm.default_opts(
+        tol=cfg.tol, maxit=args.mixed_maxit, precision=helm.HELM_PREC_MIXED, deadline_s=600.0)))
+    err = float(torch.linalg.vector_norm(x32 - x64) / torch.linalg.vector_norm(x64))
+    out["cavity200_mixed"] = {"tol": cfg.tol, "fp64_s": round(t64, 3), "mixed_s": round(t32, 3),
+                              "speedup": round(t64 / t32, 3), "fp64_iters": i64["iters"],
+                              "mixed_inner_iters": i32["iters"], "mixed_steps": i32["restarts"],
+                              "status": [i64["status"], i32["status"]],
+                              "relres_true": [i64["relres_true"], i32["relres_true"]],
+                              "rel_err_mixed_vs_fp64": err}
+    A.close()
+    del x64, x32
+
+    # config 5
+    cfg = helmgen.CONFIGS["adjoint80"]
+    p = helmgen.assemble(cfg)
+    m = helmgen.element_nnz_map(p)
+    se, spair = helmgen.slot_elements(p, m)
+    _, Me, Bf = helmgen.element_matrices(cfg.h)
+    fem = hgrad.HelmholtzFEM(p.rowptr, p.colind, p.K, se, spair, m, Me, Bf, helmgen.top_elements(cfg),
+                             helmgen.omega(cfg.F), dev)
+    rec = torch.as_tensor(helmgen.receivers(p, 64, seed=1), device=dev)
+    b = torch.as_tensor(helmgen.source(p), device=dev)
+    opts = helm.default_opts(tol=cfg.tol, maxit=100000)
+    with torch.no_grad():
+        d = hgrad.solve_sound_speed(torch.as_tensor(helmgen.sound_speed(cfg, seed=2), device=dev), b, fem, opts)[rec]
+
+    def fwd_bwd():
+        c = torch.as_tensor(p.c, device=dev).requires_grad_(True)
+        u = hgrad.solve_sound_speed(c, b, fem, opts)
+        e = u[rec] - d
+        torch.sum(e.real ** 2 + e.imag ** 2).backward()
+        return c.grad
+
+    fwd_bwd()
+    _, t_grad = timed(fwd_bwd)
+    with torch.no_grad():
+        _, t_fwd = timed(lambda: hgrad.solve_sound_speed(torch.as_tensor(p.c, device=dev), b, fem, opts))
+    out["adjoint80"] = {"params": cfg.n_elem, "forward_s": round(t_fwd, 4), "forward_backward_s": round(t_grad, 4),
+                        "backward_over_forward": round((t_grad - t_fwd) / t_fwd, 3)}
+    return out
 
 
 def run_reference(args):
@@ -359,8 +503,7 @@ def run_reference(args):
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_it * args.ref_step_iters * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": f"{WORKLOAD}: Q1 Helmholtz box 120x60x50, n={p.n}, nnz={p.nnz}, "
-                                   f"BiCGStab to rel. residual {cfg.tol:g}, complex128", "n": p.n, "nnz": p.nnz},
+            "config": workload_config(p, cfg, ws),
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -620,6 +763,9 @@ def main():
                     help="spmv: only the complex128 SpMV loop on the same matrix (profiling target); "
                          "vectors: the BLAS-1 operations alone at the paper's vector lengths")
     ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--extensions", default="on", choices=["on", "off"],
+                    help="on: add one pass of each other workload (box20, sweep60, cavity200 mixed, adjoint80) "
+                         "to the default line as the 'extensions' key")
     ap.add_argument("--launch", default="graph", choices=["graph", "host"],
                     help="host: drive the iteration loop from the host (same kernels; for profilers that "
                          "cannot see inside conditional graphs)")
@@ -638,9 +784,11 @@ def main():
         run_gpu(args)
 
 
-# Iterations of one cavity120 BiCGStab solve to 1e-8 (GPU count, used to
-# scale the oracle's per-iteration time when only a sample is timed).
-REF_ITERS_PER_SOLVE = 20000
+# Iterations of one cavity120 BiCGStab solve to 1e-8, as the GPU solve takes
+# them (measured on GB300 with the shipped build), used to scale the
+# oracle's per-iteration time when only a sample is timed.  Any change of a
+# reduction's summation order moves the count by a few per cent.
+REF_ITERS_PER_SOLVE = 19653
 
 if __name__ == "__main__":
     main()

@@ -30,23 +30,31 @@ _lib = None
 STATUS = {0: "ok", 1: "invalid", 4: "not_converged", 5: "breakdown", 7: "nonfinite"}
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with g++ -O2 (no fast-math) if it is missing or stale."""
-    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
-    if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
-        return _LIB_PATH
-    tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    subprocess.check_call(["g++", "-std=c++17", "-O2", "-fPIC", "-shared", "-o", tmp, _SRC])
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+_OMP_PATH = os.path.join(_HERE, "_build", "libhelm_oracle_omp.so")
+_omp_lib = None
 
 
-def _load():
-    global _lib
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle with g++ -O2 (no fast-math) if it is missing or stale.
+    openmp: the all-core build of the same source for the benchmark's CPU
+    baseline (-fopenmp; the tests use the sequential build only)."""
+    path = _OMP_PATH if openmp else _LIB_PATH
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    if (not force and os.path.exists(path)
+            and os.path.getmtime(path) >= os.path.getmtime(_SRC)):
+        return path
+    tmp = path + f".tmp{os.getpid()}"
+    subprocess.check_call(["g++", "-std=c++17", "-O2", "-fPIC", "-shared"] + (["-fopenmp"] if openmp else [])
+                          + ["-o", tmp, _SRC])
+    os.replace(tmp, path)
+    return path
+
+
+def _load(openmp: bool = False):
+    global _lib, _omp_lib
     with _lock:
-        if _lib is None:
-            lib = ctypes.CDLL(build())
+        if (_omp_lib if openmp else _lib) is None:
+            lib = ctypes.CDLL(build(openmp=openmp))
             P = ctypes.c_void_p
             lib.oracle_spmv.argtypes = [ctypes.c_int32, P, P, P, P, P]
             lib.oracle_spmv.restype = None
@@ -62,8 +70,11 @@ def _load():
             lib.oracle_bicgstabl.argtypes = [ctypes.c_int32, P, P, P, P, P, ctypes.c_int, ctypes.c_double,
                                              ctypes.c_int32, ctypes.c_int, P, P, P]
             lib.oracle_bicgstabl.restype = ctypes.c_int
-            _lib = lib
-    return _lib
+            if openmp:
+                _omp_lib = lib
+            else:
+                _lib = lib
+    return _omp_lib if openmp else _lib
 
 
 def _c(a, dtype):
@@ -102,9 +113,10 @@ def dznrm2(x) -> float:
     return float(lib.oracle_dznrm2(xx.size, px))
 
 
-def bicgstab(rowptr, colind, vals, b, tol=1e-8, maxit=20000, x0=None):
-    """Textbook BiCGStab; returns (x, info dict)."""
-    return _krylov("oracle_bicgstab", rowptr, colind, vals, b, tol, maxit, x0)
+def bicgstab(rowptr, colind, vals, b, tol=1e-8, maxit=20000, x0=None, openmp=False):
+    """Textbook BiCGStab; returns (x, info dict).  openmp: run the all-core
+    build (benchmark baseline only)."""
+    return _krylov("oracle_bicgstab", rowptr, colind, vals, b, tol, maxit, x0, openmp=openmp)
 
 
 def tfqmr(rowptr, colind, vals, b, tol=1e-8, maxit=20000, x0=None):
@@ -117,8 +129,8 @@ def bicgstabl(rowptr, colind, vals, b, ell=2, tol=1e-8, maxit=20000, x0=None):
     return _krylov("oracle_bicgstabl", rowptr, colind, vals, b, tol, maxit, x0, ell=ell)
 
 
-def _krylov(fname, rowptr, colind, vals, b, tol, maxit, x0, ell=None):
-    lib = _load()
+def _krylov(fname, rowptr, colind, vals, b, tol, maxit, x0, ell=None, openmp=False):
+    lib = _load(openmp)
     n = len(rowptr) - 1
     rp, prp = _c(rowptr, np.int32)
     ci, pci = _c(colind, np.int32)
