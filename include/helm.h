@@ -364,7 +364,17 @@ helm_status helm_sweep_destroy(helm_sweep S);
  *             frequencies) for b_ld = 0.
  *   d_X     : complex128 solutions, x_j[i] = d_X[i * ldx + j], ldx >= nfreq
  *             (read first when o->use_x0).
- *   o       : tol, maxit, use_x0, deadline_s used (BiCGStab, FP64 only).
+ *   o       : tol, maxit, use_x0, deadline_s, precision, inner_tol used
+ *             (BiCGStab).  precision HELM_PREC_MIXED: FP64 refinement per
+ *             frequency around complex64 inner sweeps -- each step forms
+ *             r_j = b_j - A_j x_j in FP64, solves A_j d_j = r_j / sigma_j
+ *             (sigma_j = ||r_j|| / sqrt(n)) for all running frequencies in
+ *             one complex64 sweep to a reduction of inner_tol, and updates
+ *             x_j += gamma_j sigma_j d_j with the gamma_j that minimises the
+ *             FP64 residual along that direction; a frequency stops when its
+ *             FP64 residual meets tol, or not converged after five steps in
+ *             a row without halving it; iterations are counted in inner
+ *             iterations, restarts in refinement steps.
  *             A frequency reports HELM_OK only when its true residual is at
  *             most tol; one whose recurrence met tol while its true residual
  *             did not restarts from its x (the others stay frozen), its

@@ -56,17 +56,35 @@ constexpr int32_t kModePlain = 0;
 constexpr int32_t kModeRefine = 1;
 constexpr int kInnerMax = 50000;  // inner iterations per refinement step at most
 
+// Every partial sum of a dot product or norm accumulates in FP64 (S, and
+// double2 for complex sums): for complex128 operands with the FP64 product
+// (4 or 2 FMA), for complex64 operands the product is formed in FP32 and
+// added in FP64 -- the complex64 kernels are HBM-bound and the FP64 pipe is
+// otherwise idle there, while an FP32 running sum over the ~10 rows a
+// thread takes on the 200x100x80 cavity visibly slowed the inner solves.
 template <class V> struct Prec;
 template <> struct Prec<double2> {
   using S = double;
   __device__ static __forceinline__ double2 cvt(double2 z) { return z; }
 };
 template <> struct Prec<float2> {
-  using S = float;
+  using S = double;
   __device__ static __forceinline__ float2 cvt(double2 z) {
     return make_float2(static_cast<float>(z.x), static_cast<float>(z.y));
   }
 };
+
+// acc + conj(a) b and acc + |a|^2 in the precision rules above
+__device__ __forceinline__ double2 dot_acc(double2 acc, double2 a, double2 b) { return cfma_conj(a, b, acc); }
+__device__ __forceinline__ double2 dot_acc(double2 acc, float2 a, float2 b) {
+  const float re = fmaf(a.x, b.x, a.y * b.y);
+  const float im = fmaf(a.x, b.y, -a.y * b.x);
+  return make_double2(acc.x + static_cast<double>(re), acc.y + static_cast<double>(im));
+}
+__device__ __forceinline__ double nrm_acc(double acc, double2 a) { return cabs2_acc(a, acc); }
+__device__ __forceinline__ double nrm_acc(double acc, float2 a) {
+  return acc + static_cast<double>(fmaf(a.x, a.x, a.y * a.y));
+}
 
 // Every kernel of the solver: at most 1024 threads, one block per SM.
 constexpr int kSolverThreads = Engine<double2>::kThreads;
@@ -142,6 +160,22 @@ __device__ __forceinline__ bool grid_total_last(double (&v)[K], double* partials
 // Executed by one thread on the state (in global memory for the graph path,
 // in each block's shared memory for the persistent one).
 
+// The inner loop of mixed precision does not end the solve on a breakdown or
+// a non-finite scalar of its complex64 recurrence: it asks for a refinement
+// step instead (the FP64 step minimises the residual over its window, so a
+// poor or non-finite inner iterate is rejected there, and a fresh inner
+// process starts from the FP64 residual).  Returns true when the event was
+// absorbed that way; the caller then leaves the status running.
+__device__ __forceinline__ bool refine_absorb(SolverState* st) {
+  if (st->method != kModeRefine) return false;
+  st->aux[1].x = 1.0;
+  return true;
+}
+// A refinement step is pending: the rest of the inner iteration is skipped.
+__device__ __forceinline__ bool refine_step_pending(const SolverState* st) {
+  return st->method == kModeRefine && st->aux[1].x != 0.0;
+}
+
 // after the initial residual: tot = (||b||^2, ||r||^2, (r^, r))
 __device__ __forceinline__ void sc_init(SolverState* st, const double (&tot)[4], int use_x0) {
   const double bnorm = sqrt(tot[0]);
@@ -186,15 +220,17 @@ __device__ __forceinline__ void sc_after_v(SolverState* st, const double (&tot)[
   st->iter += 1;
   st->spmv_count += 1;
   const double2 rv = make_double2(tot[0], tot[1]);
+  int err = 0;
   if (!cfinite(rv)) {
-    st->status = HELM_ERR_NONFINITE;
+    err = HELM_ERR_NONFINITE;
   } else if (czero(rv)) {
-    st->status = HELM_ERR_BREAKDOWN;
+    err = HELM_ERR_BREAKDOWN;
   } else {
     const double2 alpha = cdiv_fast(st->rho, rv);
-    if (!cfinite(alpha)) st->status = HELM_ERR_NONFINITE;
+    if (!cfinite(alpha)) err = HELM_ERR_NONFINITE;
     else st->alpha = alpha;
   }
+  if (err && !refine_absorb(st)) st->status = err;
 }
 
 // after P3: tot = ||s||^2; ||s|| / ||b|| <= tol compared squared
@@ -202,7 +238,7 @@ __device__ __forceinline__ void sc_after_s(SolverState* st, const double (&tot)[
   const double s2 = tot[0];
   const double bt = st->bnorm * st->tol;
   if (!isfinite(s2)) {
-    st->status = HELM_ERR_NONFINITE;
+    if (!refine_absorb(st)) st->status = HELM_ERR_NONFINITE;
   } else if (st->method != kModeRefine && s2 <= bt * bt) {
     st->phase = PH_SCONV;
     st->relres = sqrt(s2) / st->bnorm;
@@ -214,16 +250,18 @@ __device__ __forceinline__ void sc_after_t(SolverState* st, const double (&tot)[
   st->spmv_count += 1;
   const double2 ts = make_double2(tot[0], tot[1]);
   const double tt = tot[2];
+  int err = 0;
   if (!cfinite(ts) || !isfinite(tt)) {
-    st->status = HELM_ERR_NONFINITE;
+    err = HELM_ERR_NONFINITE;
   } else if (tt == 0.0) {
-    st->status = HELM_ERR_BREAKDOWN;
+    err = HELM_ERR_BREAKDOWN;
   } else {
     const double inv_tt = 1.0 / tt;
     const double2 omega = make_double2(ts.x * inv_tt, ts.y * inv_tt);
-    if (!cfinite(omega)) st->status = HELM_ERR_NONFINITE;
+    if (!cfinite(omega)) err = HELM_ERR_NONFINITE;
     else st->omega = omega;
   }
+  if (err && !refine_absorb(st)) st->status = err;
 }
 
 // after P5: tot = ((r^, r), ||r||^2); `late` = the deadline has passed.
@@ -257,11 +295,11 @@ __device__ __forceinline__ void sc_after_xr(SolverState* st, const double (&tot)
       stop_ok = false;
     }
     if (!isfinite(r2)) {
-      status = HELM_ERR_NONFINITE;
+      status = refine_absorb(st) ? ST_RUNNING : HELM_ERR_NONFINITE;
     } else if (stop_ok) {
       status = HELM_OK;
     } else if (czero(omega64)) {
-      status = HELM_ERR_BREAKDOWN;
+      status = refine_absorb(st) ? ST_RUNNING : HELM_ERR_BREAKDOWN;
     } else if (st->iter >= st->maxit) {
       status = HELM_ERR_NOT_CONVERGED;
     } else if (late) {
@@ -271,10 +309,10 @@ __device__ __forceinline__ void sc_after_xr(SolverState* st, const double (&tot)
       // beta = (rho_new / rho) (alpha / omega) = (rho_new alpha) / (rho omega)
       const double2 beta = cdiv_fast(cmul(rho_new, alpha64), cmul(st->rho, omega64));
       if (!cfinite(rho_new) || !cfinite(beta)) {
-        status = HELM_ERR_NONFINITE;
+        status = refine_absorb(st) ? ST_RUNNING : HELM_ERR_NONFINITE;
         st->iter += 1;
       } else if (czero(rho_new)) {
-        status = HELM_ERR_BREAKDOWN;
+        status = refine_absorb(st) ? ST_RUNNING : HELM_ERR_BREAKDOWN;
         st->iter += 1;
       } else {
         st->rho = rho_new;
@@ -304,11 +342,8 @@ __device__ __forceinline__ void ph_init_zero(const KArgs<V>& a, typename Prec<V>
     a.rh[i] = bi;
     a.p[i] = z;
     a.v[i] = z;
-    acc[0] = cabs2_acc(bi, acc[0]);
-    V d;
-    d.x = acc[2];
-    d.y = acc[3];
-    d = cfma_conj(bi, bi, d);
+    acc[0] = nrm_acc(acc[0], bi);
+    const double2 d = dot_acc(make_double2(acc[2], acc[3]), bi, bi);
     acc[2] = d.x;
     acc[3] = d.y;
   }
@@ -330,12 +365,9 @@ struct InitEpi {
     rh[i] = ri;
     p[i] = vzero<V>();
     v[i] = vzero<V>();
-    part[0] = cabs2_acc(bi, part[0]);
-    part[1] = cabs2_acc(ri, part[1]);
-    V d;
-    d.x = part[2];
-    d.y = part[3];
-    d = cfma_conj(ri, ri, d);
+    part[0] = nrm_acc(part[0], bi);
+    part[1] = nrm_acc(part[1], ri);
+    const double2 d = dot_acc(make_double2(part[2], part[3]), ri, ri);
     part[2] = d.x;
     part[3] = d.y;
   }
@@ -379,17 +411,17 @@ template <class V>
 struct VEpi {
   V* v;
   const V* rhp;
-  V part;
+  double2 part;
   V rh;
   __device__ __forceinline__ void prefetch(int32_t i) { rh = rhp[i]; }
   __device__ __forceinline__ void row(int32_t i, V ax) {
     v[i] = ax;
-    part = cfma_conj(rh, ax, part);
+    part = dot_acc(part, rh, ax);
   }
 };
 template <class V>
 __device__ __forceinline__ VEpi<V> v_epi(const KArgs<V>& a) {
-  return VEpi<V>{a.v, a.rh, vzero<V>(), vzero<V>()};
+  return VEpi<V>{a.v, a.rh, make_double2(0.0, 0.0), vzero<V>()};
 }
 
 // P3: s = r - alpha v, ||s||^2
@@ -412,7 +444,7 @@ __device__ __forceinline__ typename Prec<V>::S ph_s(const KArgs<V>& a, V alpha) 
     }
     const V s0 = cfms(alpha, v0, r0);
     a.s[i] = s0;
-    acc = cabs2_acc(s0, acc);
+    acc = nrm_acc(acc, s0);
     if (!more) break;
     v0 = v1;
     r0 = r1;
@@ -427,27 +459,25 @@ template <class V>
 struct TEpi {
   V* t;
   const V* sp;
-  V ts;
-  typename Prec<V>::S tt;
+  double2 ts;
+  double tt;
   V si;
   __device__ __forceinline__ void prefetch(int32_t i) { si = sp[i]; }
   __device__ __forceinline__ void row(int32_t i, V ax) {
     t[i] = ax;
-    ts = cfma_conj(ax, si, ts);
-    tt = cabs2_acc(ax, tt);
+    ts = dot_acc(ts, ax, si);
+    tt = nrm_acc(tt, ax);
   }
 };
 template <class V>
 __device__ __forceinline__ TEpi<V> t_epi(const KArgs<V>& a) {
-  using S = typename Prec<V>::S;
-  return TEpi<V>{a.t, a.s, vzero<V>(), S(0), vzero<V>()};
+  return TEpi<V>{a.t, a.s, make_double2(0.0, 0.0), 0.0, vzero<V>()};
 }
 
 // P5: x += alpha p + omega s, r = s - omega t; (r^, r), ||r||^2.  With
 // sconv (the solve stopped at s) only x += alpha p.
 template <class V>
-__device__ __forceinline__ void ph_xr(const KArgs<V>& a, V alpha, V omega, bool sconv, V& rr,
-                                      typename Prec<V>::S& r2) {
+__device__ __forceinline__ void ph_xr(const KArgs<V>& a, V alpha, V omega, bool sconv, double2& rr, double& r2) {
   SliceRows q(a.A.n);
   int32_t i = q.row();
   if (!q.active() || i >= a.A.n) return;
@@ -474,8 +504,8 @@ __device__ __forceinline__ void ph_xr(const KArgs<V>& a, V alpha, V omega, bool 
     a.x[i] = cfma(omega, s0, cfma(alpha, p0, x0));
     const V r0 = cfms(omega, t0, s0);
     a.r[i] = r0;
-    rr = cfma_conj(h0, r0, rr);
-    r2 = cabs2_acc(r0, r2);
+    rr = dot_acc(rr, h0, r0);
+    r2 = nrm_acc(r2, r0);
     if (!more) break;
     s0 = sn;
     x0 = xn;
@@ -540,7 +570,7 @@ template <class V>
 __global__ void __launch_bounds__(kSolverThreads, kSolverMinBlocks) k_s(KArgs<V> a) {
   __shared__ double red[32];
   SolverState* st = a.st;
-  if (st->status != ST_RUNNING) return;
+  if (st->status != ST_RUNNING || refine_step_pending(st)) return;
   double part[1] = {double(ph_s<V>(a, Prec<V>::cvt(st->alpha)))};
   double tot[1];
   if (!grid_total_last<1>(part, a.partials, a.tickets + TK_S, red, tot)) return;
@@ -554,7 +584,7 @@ __global__ void __launch_bounds__(kSolverThreads, kSolverMinBlocks) k_t(KArgs<V>
   using S = typename Prec<V>::S;
   __shared__ double red[32 * 3];
   SolverState* st = a.st;
-  if (st->status != ST_RUNNING || st->phase != PH_RUN) return;
+  if (st->status != ST_RUNNING || st->phase != PH_RUN || refine_step_pending(st)) return;
   TEpi<V> epi = t_epi<V>(a);
   spmv_run<V>(a.A, a.s, epi, nullptr, a.dev_err);
   double part[3] = {double(epi.ts.x), double(epi.ts.y), double(epi.tt)};
@@ -574,8 +604,9 @@ __global__ void __launch_bounds__(kSolverThreads, kSolverMinBlocks) k_xr(KArgs<V
     if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(a, false);
     return;
   }
-  V rr = vzero<V>();
-  S r2 = S(0);
+  if (refine_step_pending(st)) return;  // the mixed-precision graph body sets the condition itself
+  double2 rr = make_double2(0.0, 0.0);
+  double r2 = 0.0;
   ph_xr<V>(a, Prec<V>::cvt(st->alpha), Prec<V>::cvt(st->omega), st->phase == PH_SCONV, rr, r2);
   double part[3] = {double(rr.x), double(rr.y), double(r2)};
   double tot[3];

@@ -291,14 +291,13 @@ __global__ void __launch_bounds__(256) k_gcr_xupd(RuArgs a, int always) {
   const double2 gamma = st->gamma;
   const int slot = st->gcr_next, keep = st->gcr_keep;
   const double inv = keep ? 1.0 / st->gcr_nrm : 0.0;
+  if (!keep) return;  // rejected direction (zero or non-finite): x stays as it is
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < a.A.n; i += gridDim.x * blockDim.x) {
     const double2 z = a.Zw[slot][i];
     a.x[i] = cfma(gamma, z, a.x[i]);
-    if (keep) {
-      const double2 c = a.Cw[slot][i];
-      a.Cw[slot][i] = make_double2(c.x * inv, c.y * inv);
-      a.Zw[slot][i] = make_double2(z.x * inv, z.y * inv);
-    }
+    const double2 c = a.Cw[slot][i];
+    a.Cw[slot][i] = make_double2(c.x * inv, c.y * inv);
+    a.Zw[slot][i] = make_double2(z.x * inv, z.y * inv);
   }
 }
 

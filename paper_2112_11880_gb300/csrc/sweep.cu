@@ -22,6 +22,7 @@
 // Tile shape autotuning: at creation the sweep times the batched SpMV with
 // 4, 8 and 16 warps per block on the actual matrix and keeps the fastest.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -46,15 +47,23 @@ struct SweepDev {
   const double* M;
   const double* B;
   const uint8_t* bzero_blk;  // [ceil(n / 32)]: 1 when B = 0 on every entry of the 32-row block
+  const float* K32;          // FP32 copies for the complex64 inner sweep (null in the FP64 sweep)
+  const float* M32;
+  const float* B32;
 };
 
-struct SweepArgs {
+// Arguments of the sweep kernels.  V is the type of the Krylov vectors:
+// complex128 for the FP64 sweep, complex64 for the inner solves of the
+// mixed-precision sweep (products in FP32, every partial sum and every
+// scalar of the recurrence in FP64).
+template <class V>
+struct SweepArgsT {
   SweepDev A;
   int32_t F, Fp, G;      // frequencies, padded count, 32-frequency groups
   const double* w;       // [Fp] angular frequencies (padding: 0)
-  const double2* b;      // right-hand side: b[i * b_ld + j], or b[i] for all j when b_ld = 0
+  const V* b;            // right-hand side: b[i * b_ld + j], or b[i] for all j when b_ld = 0
   int32_t b_ld;          // 0 (one b for all frequencies) or Fp
-  double2 *x, *r, *rh, *p, *v, *s, *t;  // [n][Fp]
+  V *x, *r, *rh, *p, *v, *s, *t;  // [n][Fp]
   double2 *rho, *alpha, *omg, *beta;    // [Fp]
   double *bnorm, *relres, *relres_true; // [Fp]
   int32_t *status, *iters, *phase;      // [Fp]
@@ -66,10 +75,32 @@ struct SweepArgs {
   cudaGraphConditionalHandle cond;
   int has_cond;
 };
+using SweepArgs = SweepArgsT<double2>;
 
-__device__ __forceinline__ void sweep_set_cond(const SweepArgs& a, bool cont) {
+template <class V>
+__device__ __forceinline__ void sweep_set_cond(const SweepArgsT<V>& a, bool cont) {
   if (a.has_cond) cudaGraphSetConditional(a.cond, cont ? 1u : 0u);
 }
+
+// Vector-type conversions and FP64-accumulated sums.
+template <class V> __device__ __forceinline__ V sw_cvt(double2 z);
+template <> __device__ __forceinline__ double2 sw_cvt<double2>(double2 z) { return z; }
+template <> __device__ __forceinline__ float2 sw_cvt<float2>(double2 z) {
+  return make_float2(static_cast<float>(z.x), static_cast<float>(z.y));
+}
+__device__ __forceinline__ double2 sw_dot(double2 acc, double2 a, double2 b) { return cfma_conj(a, b, acc); }
+__device__ __forceinline__ double2 sw_dot(double2 acc, float2 a, float2 b) {
+  const float re = fmaf(a.x, b.x, a.y * b.y);
+  const float im = fmaf(a.x, b.y, -a.y * b.x);
+  return make_double2(acc.x + static_cast<double>(re), acc.y + static_cast<double>(im));
+}
+__device__ __forceinline__ double sw_nrm(double acc, double2 a) { return cabs2_acc(a, acc); }
+__device__ __forceinline__ double sw_nrm(double acc, float2 a) {
+  return acc + static_cast<double>(fmaf(a.x, a.x, a.y * a.y));
+}
+template <class V> __device__ __forceinline__ V sw_zero();
+template <> __device__ __forceinline__ double2 sw_zero<double2>() { return make_double2(0.0, 0.0); }
+template <> __device__ __forceinline__ float2 sw_zero<float2>() { return make_float2(0.f, 0.f); }
 
 // Per-frequency partial sums of one block: each warp's lanes hold the partials
 // of frequencies g*32 + lane (g = the warp's group); warps with the same group
@@ -78,8 +109,8 @@ __device__ __forceinline__ void sweep_set_cond(const SweepArgs& a, bool cont) {
 // blocks in block order; there thread j < Fp owns frequency j's totals in
 // tot[].  Requires Fp <= blockDim.x.  `sh` holds (warps per block) * 32 * K
 // doubles.
-template <int K>
-__device__ bool sweep_grid_sum(const SweepArgs& a, const double (&v)[K], double* sh, unsigned int* ticket,
+template <int K, class V>
+__device__ bool sweep_grid_sum(const SweepArgsT<V>& a, const double (&v)[K], double* sh, unsigned int* ticket,
                                double (&tot)[K]) {
   __shared__ bool s_last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -180,10 +211,38 @@ __device__ __forceinline__ double2 sweep_row(const SweepDev& A, int32_t i, int j
   return acc;
 }
 
+// The same row for complex64 vectors (the inner operator of the mixed
+// sweep): the entries are formed in FP32 from FP32 copies of K, M, B,
+// products and the row sum are FP32 -- no FP64 instruction per entry.
+__device__ __forceinline__ float2 sweep_row(const SweepDev& A, int32_t i, int j, double wj, double w2,
+                                            const float2* __restrict__ x, int64_t ld) {
+  const int64_t k0 = __ldg(A.rowptr + i), k1 = __ldg(A.rowptr + i + 1);
+  const float wf = static_cast<float>(wj), w2f = static_cast<float>(w2);
+  float2 acc = make_float2(0.f, 0.f);
+  if (A.bzero_blk[i >> 5] != 0) {
+#pragma unroll 4
+    for (int64_t k = k0; k < k1; ++k) {
+      const int32_t c = __ldg(A.colind + k);
+      const float are = fmaf(-w2f, __ldg(A.M32 + k), __ldg(A.K32 + k));
+      const float2 xv = __ldg(x + static_cast<int64_t>(c) * ld + j);
+      acc.x = fmaf(are, xv.x, acc.x);
+      acc.y = fmaf(are, xv.y, acc.y);
+    }
+  } else {
+#pragma unroll 2
+    for (int64_t k = k0; k < k1; ++k) {
+      const int32_t c = __ldg(A.colind + k);
+      const float2 av = make_float2(fmaf(-w2f, __ldg(A.M32 + k), __ldg(A.K32 + k)), wf * __ldg(A.B32 + k));
+      acc = cfma32(av, __ldg(x + static_cast<int64_t>(c) * ld + j), acc);
+    }
+  }
+  return acc;
+}
+
 // Batched SpMV over the warp's (row, group) units: acc[j] = sum_k A_j[k] x[col][j].
 // Calls epi(i, lane_frequency, acc) for running frequencies.
-template <class Epi>
-__device__ __forceinline__ void sweep_spmv(const SweepArgs& a, const double2* __restrict__ x, Epi& epi) {
+template <class V, class Epi>
+__device__ __forceinline__ void sweep_spmv(const SweepArgsT<V>& a, const V* __restrict__ x, Epi& epi) {
   const int lane = threadIdx.x & 31;
   const int64_t gw = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
@@ -199,7 +258,7 @@ __device__ __forceinline__ void sweep_spmv(const SweepArgs& a, const double2* __
   for (int64_t u = gw; u < units; u += nwarps) {
     if (!grp_on) break;
     const int32_t i = static_cast<int32_t>(u / a.G);
-    const double2 acc = sweep_row(a.A, i, j, wj, w2, x, a.Fp);
+    const V acc = sweep_row(a.A, i, j, wj, w2, x, a.Fp);
     if (run) epi(i, j, acc);
   }
 }
@@ -224,7 +283,8 @@ __global__ void __launch_bounds__(256) k_sw_apply(SweepDev A, int32_t F, int32_t
 // fresh: every frequency starts (iteration counts from 0).  Otherwise a
 // restart from x: the frequencies with restart[j] != 0 run again (their
 // iteration counts continue), the others keep their status and result.
-__global__ void k_sw_configure(SweepArgs a, double tol, int32_t maxit, int32_t use_x0, double deadline_s,
+template <class V>
+__global__ void k_sw_configure(SweepArgsT<V> a, double tol, int32_t maxit, int32_t use_x0, double deadline_s,
                                int32_t fresh, const int32_t* __restrict__ restart) {
   SolverState* st = a.st;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -253,7 +313,8 @@ __global__ void k_sw_configure(SweepArgs a, double tol, int32_t maxit, int32_t u
 
 // Update the group flags and the loop condition from the per-frequency status
 // (thread 0 of the last block of a reduction kernel, after the statuses are set).
-__device__ void sweep_refresh_groups(const SweepArgs& a) {
+template <class V>
+__device__ void sweep_refresh_groups(const SweepArgsT<V>& a) {
   bool any = false;
   for (int g = 0; g < a.G; ++g) {
     bool on = false;
@@ -266,7 +327,8 @@ __device__ void sweep_refresh_groups(const SweepArgs& a) {
 }
 
 // init: r = b - A_j x (or r = b, x = 0), r^ = r, p = v = 0; ||b||, ||r||, rho
-__global__ void __launch_bounds__(512) k_sw_init(SweepArgs a) {
+template <class V>
+__global__ void __launch_bounds__(512) k_sw_init(SweepArgsT<V> a) {
   extern __shared__ double sh[];
   const int use_x0 = a.st->use_x0;
   const int lane = threadIdx.x & 31;
@@ -274,17 +336,17 @@ __global__ void __launch_bounds__(512) k_sw_init(SweepArgs a) {
   const int g = static_cast<int>(gw % a.G);
   const int j = g * 32 + lane;
   double part[4] = {0.0, 0.0, 0.0, 0.0};
-  auto body = [&](int32_t i, int jj, double2 ax) {
+  auto body = [&](int32_t i, int jj, V ax) {
     const size_t idx = static_cast<size_t>(i) * a.Fp + jj;
-    const double2 bi = a.b[a.b_ld ? static_cast<size_t>(i) * a.b_ld + jj : static_cast<size_t>(i)];
-    const double2 ri = csub(bi, ax);
+    const V bi = a.b[a.b_ld ? static_cast<size_t>(i) * a.b_ld + jj : static_cast<size_t>(i)];
+    const V ri = csub(bi, ax);
     a.r[idx] = ri;
     a.rh[idx] = ri;
-    a.p[idx] = make_double2(0.0, 0.0);
-    a.v[idx] = make_double2(0.0, 0.0);
-    part[0] = cabs2_acc(bi, part[0]);
-    part[1] = cabs2_acc(ri, part[1]);
-    double2 d = cfma_conj(ri, ri, make_double2(part[2], part[3]));
+    a.p[idx] = sw_zero<V>();
+    a.v[idx] = sw_zero<V>();
+    part[0] = sw_nrm(part[0], bi);
+    part[1] = sw_nrm(part[1], ri);
+    double2 d = sw_dot(make_double2(part[2], part[3]), ri, ri);
     part[2] = d.x;
     part[3] = d.y;
   };
@@ -296,8 +358,8 @@ __global__ void __launch_bounds__(512) k_sw_init(SweepArgs a) {
     for (int64_t u = gw; u < static_cast<int64_t>(a.A.n) * a.G; u += nwarps) {
       const int32_t i = static_cast<int32_t>(u / a.G);
       if (run) {
-        a.x[static_cast<size_t>(i) * a.Fp + j] = make_double2(0.0, 0.0);
-        body(i, j, make_double2(0.0, 0.0));
+        a.x[static_cast<size_t>(i) * a.Fp + j] = sw_zero<V>();
+        body(i, j, sw_zero<V>());
       }
     }
   }
@@ -340,10 +402,11 @@ __global__ void __launch_bounds__(512) k_sw_init(SweepArgs a) {
   const bool run = grp_on && j < a.F && a.status[j] == ST_RUNNING;
 
 // K1: p = r + beta (p - omega v)
-__global__ void __launch_bounds__(512) k_sw_p(SweepArgs a) {
+template <class V>
+__global__ void __launch_bounds__(512) k_sw_p(SweepArgsT<V> a) {
   SWEEP_ELEMENTWISE_BEGIN
   if (!run) return;
-  const double2 beta = a.beta[j], omg = a.omg[j];
+  const V beta = sw_cvt<V>(a.beta[j]), omg = sw_cvt<V>(a.omg[j]);
   for (int64_t u = gw; u < static_cast<int64_t>(a.A.n) * a.G; u += nwarps) {
     const size_t idx = static_cast<size_t>(u / a.G) * a.Fp + j;
     a.p[idx] = cfma(beta, cfms(omg, a.v[idx], a.p[idx]), a.r[idx]);
@@ -351,16 +414,17 @@ __global__ void __launch_bounds__(512) k_sw_p(SweepArgs a) {
 }
 
 // K2: v = A_j p, (r^, v) -> alpha
-__global__ void __launch_bounds__(512) k_sw_v(SweepArgs a) {
+template <class V>
+__global__ void __launch_bounds__(512) k_sw_v(SweepArgsT<V> a) {
   extern __shared__ double sh[];
   if (a.st->status != ST_RUNNING) return;
   const int64_t gw = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int g = static_cast<int>(gw % a.G);
   double part[2] = {0.0, 0.0};
-  auto body = [&](int32_t i, int j, double2 ax) {
+  auto body = [&](int32_t i, int j, V ax) {
     const size_t idx = static_cast<size_t>(i) * a.Fp + j;
     a.v[idx] = ax;
-    double2 d = cfma_conj(a.rh[idx], ax, make_double2(part[0], part[1]));
+    double2 d = sw_dot(make_double2(part[0], part[1]), a.rh[idx], ax);
     part[0] = d.x;
     part[1] = d.y;
   };
@@ -384,18 +448,19 @@ __global__ void __launch_bounds__(512) k_sw_v(SweepArgs a) {
 }
 
 // K3: s = r - alpha v, ||s||
-__global__ void __launch_bounds__(512) k_sw_s(SweepArgs a) {
+template <class V>
+__global__ void __launch_bounds__(512) k_sw_s(SweepArgsT<V> a) {
   extern __shared__ double sh[];
   if (a.st->status != ST_RUNNING) return;
   SWEEP_ELEMENTWISE_BEGIN
   double part[1] = {0.0};
   if (run) {
-    const double2 al = a.alpha[j];
+    const V al = sw_cvt<V>(a.alpha[j]);
     for (int64_t u = gw; u < static_cast<int64_t>(a.A.n) * a.G; u += nwarps) {
       const size_t idx = static_cast<size_t>(u / a.G) * a.Fp + j;
-      const double2 si = cfms(al, a.v[idx], a.r[idx]);
+      const V si = cfms(al, a.v[idx], a.r[idx]);
       a.s[idx] = si;
-      part[0] = cabs2_acc(si, part[0]);
+      part[0] = sw_nrm(part[0], si);
     }
   }
   double tot[1];
@@ -414,20 +479,21 @@ __global__ void __launch_bounds__(512) k_sw_s(SweepArgs a) {
 }
 
 // K4: t = A_j s, (t, s), (t, t) -> omega (frequencies stopped at s skip)
-__global__ void __launch_bounds__(512) k_sw_t(SweepArgs a) {
+template <class V>
+__global__ void __launch_bounds__(512) k_sw_t(SweepArgsT<V> a) {
   extern __shared__ double sh[];
   if (a.st->status != ST_RUNNING) return;
   const int64_t gw = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int g = static_cast<int>(gw % a.G);
   double part[3] = {0.0, 0.0, 0.0};
-  auto body = [&](int32_t i, int j, double2 ax) {
+  auto body = [&](int32_t i, int j, V ax) {
     if (a.phase[j] != PH_RUN) return;
     const size_t idx = static_cast<size_t>(i) * a.Fp + j;
     a.t[idx] = ax;
-    double2 d = cfma_conj(ax, a.s[idx], make_double2(part[0], part[1]));
+    double2 d = sw_dot(make_double2(part[0], part[1]), ax, a.s[idx]);
     part[0] = d.x;
     part[1] = d.y;
-    part[2] = cabs2_acc(ax, part[2]);
+    part[2] = sw_nrm(part[2], ax);
   };
   sweep_spmv(a, a.s, body);
   double tot[3];
@@ -449,7 +515,8 @@ __global__ void __launch_bounds__(512) k_sw_t(SweepArgs a) {
 }
 
 // K5: x += alpha p + omega s, r = s - omega t; per-frequency stop tests
-__global__ void __launch_bounds__(512) k_sw_xr(SweepArgs a) {
+template <class V>
+__global__ void __launch_bounds__(512) k_sw_xr(SweepArgsT<V> a) {
   extern __shared__ double sh[];
   if (a.st->status != ST_RUNNING) {
     if (blockIdx.x == 0 && threadIdx.x == 0) sweep_set_cond(a, false);
@@ -458,21 +525,21 @@ __global__ void __launch_bounds__(512) k_sw_xr(SweepArgs a) {
   SWEEP_ELEMENTWISE_BEGIN
   double part[3] = {0.0, 0.0, 0.0};
   if (run) {
-    const double2 al = a.alpha[j], om = a.omg[j];
+    const V al = sw_cvt<V>(a.alpha[j]), om = sw_cvt<V>(a.omg[j]);
     const bool sconv = a.phase[j] == PH_SCONV;
     for (int64_t u = gw; u < static_cast<int64_t>(a.A.n) * a.G; u += nwarps) {
       const size_t idx = static_cast<size_t>(u / a.G) * a.Fp + j;
       if (sconv) {
         a.x[idx] = cfma(al, a.p[idx], a.x[idx]);
       } else {
-        const double2 si = a.s[idx];
+        const V si = a.s[idx];
         a.x[idx] = cfma(om, si, cfma(al, a.p[idx], a.x[idx]));
-        const double2 ri = cfms(om, a.t[idx], si);
+        const V ri = cfms(om, a.t[idx], si);
         a.r[idx] = ri;
-        double2 d = cfma_conj(a.rh[idx], ri, make_double2(part[0], part[1]));
+        double2 d = sw_dot(make_double2(part[0], part[1]), a.rh[idx], ri);
         part[0] = d.x;
         part[1] = d.y;
-        part[2] = cabs2_acc(ri, part[2]);
+        part[2] = sw_nrm(part[2], ri);
       }
     }
   }
@@ -507,7 +574,8 @@ __global__ void __launch_bounds__(512) k_sw_xr(SweepArgs a) {
 }
 
 // tail: true residual per frequency, ||b - A_j x|| / ||b||
-__global__ void __launch_bounds__(512) k_sw_tail(SweepArgs a) {
+template <class V>
+__global__ void __launch_bounds__(512) k_sw_tail(SweepArgsT<V> a) {
   extern __shared__ double sh[];
   const int64_t gw = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int g = static_cast<int>(gw % a.G);
@@ -519,10 +587,9 @@ __global__ void __launch_bounds__(512) k_sw_tail(SweepArgs a) {
   const double wj = a.w[j], w2 = wj * wj;
   for (int64_t u = gw; u < static_cast<int64_t>(a.A.n) * a.G; u += nwarps) {
     const int32_t i = static_cast<int32_t>(u / a.G);
-    const double2 acc = sweep_row(a.A, i, j, wj, w2, a.x, a.Fp);
+    const V acc = sweep_row(a.A, i, j, wj, w2, a.x, a.Fp);
     if (j < a.F)
-      part[0] = cabs2_acc(csub(a.b[a.b_ld ? static_cast<size_t>(i) * a.b_ld + j : static_cast<size_t>(i)], acc),
-                          part[0]);
+      part[0] = sw_nrm(part[0], csub(a.b[a.b_ld ? static_cast<size_t>(i) * a.b_ld + j : static_cast<size_t>(i)], acc));
   }
   double tot[1];
   if (!sweep_grid_sum<1>(a, part, sh, a.tickets + TK_TAIL, tot)) return;
@@ -555,10 +622,142 @@ __global__ void k_sw_bzero(int32_t n, const int32_t* __restrict__ rowptr, const 
   }
 }
 
+// FP32 copies of the K, M, B values (the complex64 inner sweep's operator)
+__global__ void k_sw_to_f32(int64_t nnz, const double* __restrict__ K, const double* __restrict__ M,
+                            const double* __restrict__ B, float* __restrict__ out) {
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < nnz;
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    out[k] = static_cast<float>(K[k]);
+    out[nnz + k] = static_cast<float>(M[k]);
+    out[2 * nnz + k] = static_cast<float>(B[k]);
+  }
+}
+
 // SpMV-only kernel for the tile-shape autotuner (x = y = internal buffers).
-__global__ void __launch_bounds__(512) k_sw_spmv_probe(SweepArgs a) {
-  auto body = [&](int32_t i, int j, double2 ax) { a.v[static_cast<size_t>(i) * a.Fp + j] = ax; };
+template <class V>
+__global__ void __launch_bounds__(512) k_sw_spmv_probe(SweepArgsT<V> a) {
+  auto body = [&](int32_t i, int j, V ax) { a.v[static_cast<size_t>(i) * a.Fp + j] = ax; };
   sweep_spmv(a, a.p, body);
+}
+
+// ---------------------------------------------------------------- mixed precision
+// The mixed-precision sweep: FP64 refinement per frequency around complex64
+// inner sweeps (the kernels above instantiated for complex64 vectors).  One
+// refinement step for every frequency still running: r_j = b_j - A_j x_j in
+// FP64, sigma_j = ||r_j|| / sqrt(n), the inner sweep solves A_j d_j =
+// r_j / sigma_j in complex64 to a reduction of inner_tol, then z_j = sigma_j
+// d_j (FP64), w_j = A_j z_j and the step gamma_j = (w_j, r_j) / (w_j, w_j)
+// that minimises ||r_j - gamma w_j||, x_j += gamma_j z_j.  Frequencies that
+// have stopped get f_j = 0, which the inner sweep freezes at once.
+
+struct MxsArgs {
+  SweepArgs a;          // FP64 geometry; a.x = x_j, a.r = r_j, a.p = z_j, a.v = w_j, a.b / a.b_ld = b
+  float2* x32;          // inner solutions d_j
+  float2* f32;          // inner right-hand sides
+  const int32_t* act;   // [Fp] 1: running, 2: b_j = 0 (x_j = 0), 0: stopped
+  const double* sigma;  // [Fp]
+  const double2* gamma; // [Fp]
+  double* out;          // [Fp][4] per-frequency sums of the last reduction
+};
+
+#define MXS_UNITS_BEGIN                                                                  \
+  const SweepArgs& a = m.a;                                                              \
+  const int lane = threadIdx.x & 31;                                                     \
+  const int64_t gw = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; \
+  const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;            \
+  const int g = static_cast<int>(gw % a.G);                                              \
+  const int j = g * 32 + lane;                                                           \
+  const bool on = j < a.F && m.act[j] == 1;
+
+// r = b - A x (or b when zero_x), out[j][0] = ||r_j||^2
+__global__ void __launch_bounds__(512) k_mxs_residual(MxsArgs m, int zero_x) {
+  extern __shared__ double sh[];
+  MXS_UNITS_BEGIN
+  double part[1] = {0.0};
+  const double wj = a.w[j], w2 = wj * wj;
+  for (int64_t u = gw; u < static_cast<int64_t>(a.A.n) * a.G; u += nwarps) {
+    const int32_t i = static_cast<int32_t>(u / a.G);
+    if (!on) continue;
+    const size_t idx = static_cast<size_t>(i) * a.Fp + j;
+    const double2 bi = a.b[a.b_ld ? static_cast<size_t>(i) * a.b_ld + j : static_cast<size_t>(i)];
+    const double2 ri = zero_x ? bi : csub(bi, sweep_row(a.A, i, j, wj, w2, a.x, a.Fp));
+    a.r[idx] = ri;
+    part[0] = cabs2_acc(ri, part[0]);
+  }
+  double tot[1];
+  if (!sweep_grid_sum<1>(a, part, sh, a.tickets + TK_AUX0, tot)) return;
+  for (int jj = threadIdx.x; jj < a.F && jj == (int)threadIdx.x; jj += blockDim.x) m.out[4 * jj] = tot[0];
+}
+
+// f_j = complex64(r_j / sigma_j) for running frequencies, 0 for the others
+__global__ void __launch_bounds__(512) k_mxs_down(MxsArgs m) {
+  MXS_UNITS_BEGIN
+  if (j >= a.Fp) return;
+  const double inv = on ? 1.0 / m.sigma[j] : 0.0;
+  for (int64_t u = gw; u < static_cast<int64_t>(a.A.n) * a.G; u += nwarps) {
+    const size_t idx = static_cast<size_t>(u / a.G) * a.Fp + j;
+    float2 f = make_float2(0.f, 0.f);
+    if (on) {
+      const double2 ri = a.r[idx];
+      f = make_float2(static_cast<float>(ri.x * inv), static_cast<float>(ri.y * inv));
+    }
+    m.f32[idx] = f;
+  }
+}
+
+// z_j = sigma_j complex128(d_j)
+__global__ void __launch_bounds__(512) k_mxs_lift(MxsArgs m) {
+  MXS_UNITS_BEGIN
+  if (!on) return;
+  const double sc = m.sigma[j];
+  for (int64_t u = gw; u < static_cast<int64_t>(a.A.n) * a.G; u += nwarps) {
+    const size_t idx = static_cast<size_t>(u / a.G) * a.Fp + j;
+    const float2 d = m.x32[idx];
+    a.p[idx] = make_double2(sc * static_cast<double>(d.x), sc * static_cast<double>(d.y));
+  }
+}
+
+// w_j = A_j z_j (FP64), out[j] = ((w_j, r_j), ||w_j||^2)
+__global__ void __launch_bounds__(512) k_mxs_apply(MxsArgs m) {
+  extern __shared__ double sh[];
+  MXS_UNITS_BEGIN
+  double part[3] = {0.0, 0.0, 0.0};
+  const double wj = a.w[j], w2 = wj * wj;
+  for (int64_t u = gw; u < static_cast<int64_t>(a.A.n) * a.G; u += nwarps) {
+    const int32_t i = static_cast<int32_t>(u / a.G);
+    if (!on) continue;
+    const size_t idx = static_cast<size_t>(i) * a.Fp + j;
+    const double2 wi = sweep_row(a.A, i, j, wj, w2, a.p, a.Fp);
+    a.v[idx] = wi;
+    const double2 d = cfma_conj(wi, a.r[idx], make_double2(part[0], part[1]));
+    part[0] = d.x;
+    part[1] = d.y;
+    part[2] = cabs2_acc(wi, part[2]);
+  }
+  double tot[3];
+  if (!sweep_grid_sum<3>(a, part, sh, a.tickets + TK_AUX1, tot)) return;
+  for (int jj = threadIdx.x; jj < a.F && jj == (int)threadIdx.x; jj += blockDim.x) {
+    m.out[4 * jj] = tot[0];
+    m.out[4 * jj + 1] = tot[1];
+    m.out[4 * jj + 2] = tot[2];
+  }
+}
+
+// x_j += gamma_j z_j (running frequencies); x_j = 0 where b_j = 0
+__global__ void __launch_bounds__(512) k_mxs_update(MxsArgs m) {
+  const SweepArgs& a = m.a;
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+  const int j = static_cast<int>(gw % a.G) * 32 + lane;
+  if (j >= a.F) return;
+  const int act = m.act[j];
+  const double2 gm = m.gamma[j];
+  if (act == 0 || (act == 1 && czero(gm))) return;
+  for (int64_t u = gw; u < static_cast<int64_t>(a.A.n) * a.G; u += nwarps) {
+    const size_t idx = static_cast<size_t>(u / a.G) * a.Fp + j;
+    a.x[idx] = act == 2 ? make_double2(0.0, 0.0) : cfma(gm, a.p[idx], a.x[idx]);
+  }
 }
 
 }  // namespace
@@ -589,6 +788,13 @@ struct helm_sweep_s {
   unsigned int* tickets = nullptr;
   double* wapply = nullptr;       // frequencies of helm_sweep_spmv
   int32_t wapply_cap = 0;
+  // mixed precision: 8 complex64 vectors [n][Fcap32] (x, r, r^, p, v, s, t,
+  // f), per-frequency sigma, gamma, sums [Fcap32 * 7 doubles], flags
+  float2* vec32 = nullptr;
+  int32_t Fcap32 = 0;
+  float* kmb32 = nullptr;         // FP32 copies of K, M, B (3 nnz)
+  double* oscal = nullptr;
+  int32_t* oact = nullptr;
   int warps_per_block = 8;        // autotuned
   bool tuned = false;
   std::mutex mu;
@@ -597,10 +803,20 @@ struct helm_sweep_s {
     const void* b = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
-  } graph;
+  } graph, graph32;
 };
 
 namespace {
+
+// Graphs capture buffer addresses: both are dropped whenever a buffer they
+// use is replaced.
+void drop_sweep_graphs(helm_sweep S) {
+  for (helm_sweep_s::G* g : {&S->graph, &S->graph32}) {
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    *g = helm_sweep_s::G();
+  }
+}
 
 helm_status sweep_alloc(helm_sweep S, int32_t Fp, size_t blocks) {
   if (S->Fcap < Fp) {
@@ -619,11 +835,7 @@ helm_status sweep_alloc(helm_sweep S, int32_t Fp, size_t blocks) {
     HELM_CUDA_TRY(cudaMalloc(&S->dscal, 4 * static_cast<size_t>(Fp) * sizeof(double)));
     HELM_CUDA_TRY(cudaMalloc(&S->iscal, (4 * static_cast<size_t>(Fp) + Fp / 32) * sizeof(int32_t)));
     S->Fcap = Fp;
-    if (S->graph.exec) {
-      cudaGraphExecDestroy(S->graph.exec);
-      cudaGraphDestroy(S->graph.graph);
-      S->graph = helm_sweep_s::G();
-    }
+    drop_sweep_graphs(S);
   }
   const size_t need = blocks * static_cast<size_t>(Fp) * 4;
   if (S->partials_cap < need) {
@@ -631,6 +843,7 @@ helm_status sweep_alloc(helm_sweep S, int32_t Fp, size_t blocks) {
     S->partials = nullptr;
     HELM_CUDA_TRY(cudaMalloc(&S->partials, need * sizeof(double)));
     S->partials_cap = need;
+    drop_sweep_graphs(S);
   }
   return HELM_OK;
 }
@@ -638,7 +851,7 @@ helm_status sweep_alloc(helm_sweep S, int32_t Fp, size_t blocks) {
 SweepArgs make_args(helm_sweep S, int32_t F, int32_t Fp, const double2* b, int32_t b_ld) {
   SweepArgs a;
   std::memset(&a, 0, sizeof(a));
-  a.A = SweepDev{S->n, S->nnz, S->rowptr, S->colind, S->K, S->M, S->B, S->bzero_blk};
+  a.A = SweepDev{S->n, S->nnz, S->rowptr, S->colind, S->K, S->M, S->B, S->bzero_blk, nullptr, nullptr, nullptr};
   a.F = F;
   a.Fp = Fp;
   a.G = Fp / 32;
@@ -672,6 +885,77 @@ SweepArgs make_args(helm_sweep S, int32_t F, int32_t Fp, const double2* b, int32
   return a;
 }
 
+// The inner (complex64) sweep's arguments: the same per-frequency scalars and
+// geometry as the FP64 sweep, complex64 vectors, right-hand side f [n][Fp].
+SweepArgsT<float2> make_args32(helm_sweep S, const SweepArgs& a64) {
+  SweepArgsT<float2> a;
+  std::memset(&a, 0, sizeof(a));
+  a.A = a64.A;
+  a.A.K32 = S->kmb32;
+  a.A.M32 = S->kmb32 + S->nnz;
+  a.A.B32 = S->kmb32 + 2 * S->nnz;
+  a.F = a64.F;
+  a.Fp = a64.Fp;
+  a.G = a64.G;
+  a.w = a64.w;
+  const size_t nf = static_cast<size_t>(std::max<int32_t>(S->n, 1)) * a64.Fp;
+  float2* V = S->vec32;
+  a.x = V;
+  a.r = V + nf;
+  a.rh = V + 2 * nf;
+  a.p = V + 3 * nf;
+  a.v = V + 4 * nf;
+  a.s = V + 5 * nf;
+  a.t = V + 6 * nf;
+  a.b = V + 7 * nf;
+  a.b_ld = a64.Fp;
+  a.rho = a64.rho;
+  a.alpha = a64.alpha;
+  a.omg = a64.omg;
+  a.beta = a64.beta;
+  a.bnorm = a64.bnorm;
+  a.relres = a64.relres;
+  a.relres_true = a64.relres_true;
+  a.status = a64.status;
+  a.iters = a64.iters;
+  a.phase = a64.phase;
+  a.gactive = a64.gactive;
+  a.st = a64.st;
+  a.partials = a64.partials;
+  a.tickets = a64.tickets;
+  a.dev_err = a64.dev_err;
+  return a;
+}
+
+helm_status sweep_alloc_mixed(helm_sweep S, int32_t Fp, cudaStream_t s) {
+  if (!S->kmb32) {
+    HELM_CUDA_TRY(cudaMalloc(&S->kmb32, 3 * static_cast<size_t>(std::max<int64_t>(S->nnz, 1)) * sizeof(float)));
+    if (S->nnz > 0) {
+      k_sw_to_f32<<<vec_grid_for(S->nnz), 256, 0, s>>>(S->nnz, S->K, S->M, S->B, S->kmb32);
+      HELM_CUDA_TRY(cudaGetLastError());
+    }
+  }
+  if (S->Fcap32 >= Fp) return HELM_OK;
+  cudaFree(S->vec32);
+  cudaFree(S->oscal);
+  cudaFree(S->oact);
+  S->vec32 = nullptr;
+  S->oscal = nullptr;
+  S->oact = nullptr;
+  S->Fcap32 = 0;
+  const size_t nf = static_cast<size_t>(std::max<int32_t>(S->n, 1)) * Fp;
+  HELM_CUDA_TRY(cudaMalloc(&S->vec32, 8 * nf * sizeof(float2)));
+  HELM_CUDA_TRY(cudaMalloc(&S->oscal, 7 * static_cast<size_t>(Fp) * sizeof(double)));
+  HELM_CUDA_TRY(cudaMalloc(&S->oact, static_cast<size_t>(Fp) * sizeof(int32_t)));
+  S->Fcap32 = Fp;
+  if (S->graph32.exec) {
+    cudaGraphExecDestroy(S->graph32.exec);
+    cudaGraphDestroy(S->graph32.graph);
+  }
+  S->graph32 = helm_sweep_s::G();
+  return HELM_OK;
+}
+
 struct SweepShape {
   int threads, grid;
   size_t smem;  // per-frequency reduction scratch
@@ -687,10 +971,14 @@ SweepShape sweep_shape(helm_sweep S, int G) {
   // block partials for the per-frequency reductions), and no more blocks
   // than every sweep kernel fits on an SM at once: one wave
   int per_sm = std::max(1, 1024 / sh.threads);
-  for (const void* fn : {reinterpret_cast<const void*>(&k_sw_init), reinterpret_cast<const void*>(&k_sw_p),
-                         reinterpret_cast<const void*>(&k_sw_v), reinterpret_cast<const void*>(&k_sw_s),
-                         reinterpret_cast<const void*>(&k_sw_t), reinterpret_cast<const void*>(&k_sw_xr),
-                         reinterpret_cast<const void*>(&k_sw_tail)}) {
+  for (const void* fn :
+       {reinterpret_cast<const void*>(&k_sw_init<double2>), reinterpret_cast<const void*>(&k_sw_p<double2>),
+        reinterpret_cast<const void*>(&k_sw_v<double2>), reinterpret_cast<const void*>(&k_sw_s<double2>),
+        reinterpret_cast<const void*>(&k_sw_t<double2>), reinterpret_cast<const void*>(&k_sw_xr<double2>),
+        reinterpret_cast<const void*>(&k_sw_tail<double2>), reinterpret_cast<const void*>(&k_sw_init<float2>),
+        reinterpret_cast<const void*>(&k_sw_p<float2>), reinterpret_cast<const void*>(&k_sw_v<float2>),
+        reinterpret_cast<const void*>(&k_sw_s<float2>), reinterpret_cast<const void*>(&k_sw_t<float2>),
+        reinterpret_cast<const void*>(&k_sw_xr<float2>)}) {
     int b = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, sh.threads, sh.smem) == cudaSuccess && b >= 1)
       per_sm = std::min(per_sm, b);
@@ -712,15 +1000,18 @@ SweepShape sweep_shape(helm_sweep S, int G) {
   return sh;
 }
 
-void enqueue_sweep_body(const SweepArgs& a, const SweepShape& sh, cudaStream_t s) {
-  k_sw_p<<<sh.grid, sh.threads, 0, s>>>(a);
-  k_sw_v<<<sh.grid, sh.threads, sh.smem, s>>>(a);
-  k_sw_s<<<sh.grid, sh.threads, sh.smem, s>>>(a);
-  k_sw_t<<<sh.grid, sh.threads, sh.smem, s>>>(a);
-  k_sw_xr<<<sh.grid, sh.threads, sh.smem, s>>>(a);
+template <class V>
+void enqueue_sweep_body(const SweepArgsT<V>& a, const SweepShape& sh, cudaStream_t s) {
+  k_sw_p<V><<<sh.grid, sh.threads, 0, s>>>(a);
+  k_sw_v<V><<<sh.grid, sh.threads, sh.smem, s>>>(a);
+  k_sw_s<V><<<sh.grid, sh.threads, sh.smem, s>>>(a);
+  k_sw_t<V><<<sh.grid, sh.threads, sh.smem, s>>>(a);
+  k_sw_xr<V><<<sh.grid, sh.threads, sh.smem, s>>>(a);
 }
 
-helm_status build_sweep_graph(const SweepArgs& base, const SweepShape& sh, cudaGraph_t* gout, cudaGraphExec_t* eout) {
+template <class V>
+helm_status build_sweep_graph(const SweepArgsT<V>& base, const SweepShape& sh, cudaGraph_t* gout,
+                              cudaGraphExec_t* eout) {
   cudaStream_t cs = nullptr;
   HELM_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   cudaGraph_t graph = nullptr;
@@ -730,12 +1021,12 @@ helm_status build_sweep_graph(const SweepArgs& base, const SweepShape& sh, cudaG
     if (cudaGraphCreate(&graph, 0) != cudaSuccess) break;
     cudaGraphConditionalHandle cond;
     if (cudaGraphConditionalHandleCreate(&cond, graph, 1u, cudaGraphCondAssignDefault) != cudaSuccess) break;
-    SweepArgs a = base;
+    SweepArgsT<V> a = base;
     a.cond = cond;
     a.has_cond = 1;
     if (cudaStreamBeginCaptureToGraph(cs, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
       break;
-    k_sw_init<<<sh.grid, sh.threads, sh.smem, cs>>>(a);
+    k_sw_init<V><<<sh.grid, sh.threads, sh.smem, cs>>>(a);
     cudaStreamCaptureStatus cst;
     const cudaGraphNode_t* deps = nullptr;
     size_t ndeps = 0;
@@ -757,7 +1048,7 @@ helm_status build_sweep_graph(const SweepArgs& base, const SweepShape& sh, cudaG
     if (cudaStreamEndCapture(cs, &tmp) != cudaSuccess) break;
     if (cudaStreamBeginCaptureToGraph(cs, graph, &wnode, nullptr, 1, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
       break;
-    k_sw_tail<<<sh.grid, sh.threads, sh.smem, cs>>>(a);
+    k_sw_tail<V><<<sh.grid, sh.threads, sh.smem, cs>>>(a);
     if (cudaStreamEndCapture(cs, &tmp) != cudaSuccess) break;
     if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) break;
     result = HELM_OK;
@@ -790,11 +1081,11 @@ helm_status autotune(helm_sweep S, int32_t F, int32_t Fp, cudaStream_t s) {
     if (result != HELM_OK) break;
     SweepArgs a = make_args(S, F, Fp, nullptr, 0);
     // every group active, every frequency running, p = 0 (timing only)
-    k_sw_configure<<<1, 256, 0, s>>>(a, 0.0, 1, 0, 0.0, 1, nullptr);
+    k_sw_configure<double2><<<1, 256, 0, s>>>(a, 0.0, 1, 0, 0.0, 1, nullptr);
     cudaMemsetAsync(a.p, 0, static_cast<size_t>(S->n) * Fp * sizeof(double2), s);
-    k_sw_spmv_probe<<<sh.grid, sh.threads, 0, s>>>(a);
+    k_sw_spmv_probe<double2><<<sh.grid, sh.threads, 0, s>>>(a);
     cudaEventRecord(e0, s);
-    for (int rep = 0; rep < 3; ++rep) k_sw_spmv_probe<<<sh.grid, sh.threads, 0, s>>>(a);
+    for (int rep = 0; rep < 3; ++rep) k_sw_spmv_probe<double2><<<sh.grid, sh.threads, 0, s>>>(a);
     cudaEventRecord(e1, s);
     if (cudaEventSynchronize(e1) != cudaSuccess) {
       result = HELM_ERR_CUDA;
@@ -813,6 +1104,156 @@ helm_status autotune(helm_sweep S, int32_t F, int32_t Fp, cudaStream_t s) {
   S->warps_per_block = best_w;
   S->tuned = true;
   return result;
+}
+
+// The mixed-precision sweep (precision HELM_PREC_MIXED): refinement steps as
+// described with the kernels above, driven from the host (a few dozen steps;
+// three reads of per-frequency sums each), the inner complex64 solves one
+// graph launch each.  A frequency stops when its FP64 residual meets tol,
+// after five steps in a row without halving it, at the iteration cap
+// (counted in inner iterations) or at the deadline.
+constexpr int kSweepInnerMax = 50000;
+
+helm_status sweep_solve_mixed(helm_sweep S, const SweepArgs& a64, const SweepShape& sh, void* d_X, int32_t ldx,
+                              const helm_opts& opts, helm_info* h_infos, cudaStream_t s) {
+  const int32_t F = a64.F, Fp = a64.Fp;
+  HELM_TRY(sweep_alloc_mixed(S, Fp, s));
+  SweepArgsT<float2> a32 = make_args32(S, a64);
+  MxsArgs m;
+  m.a = a64;
+  m.x32 = a32.x;
+  m.f32 = const_cast<float2*>(a32.b);
+  m.act = S->oact;
+  double* d_sigma = S->oscal;
+  double2* d_gamma = reinterpret_cast<double2*>(S->oscal + Fp);
+  m.sigma = d_sigma;
+  m.gamma = d_gamma;
+  m.out = S->oscal + 3 * static_cast<size_t>(Fp);
+  const size_t nf = static_cast<size_t>(S->n) * Fp;
+  if (opts.use_x0) {
+    HELM_CUDA_TRY(cudaMemsetAsync(a64.x, 0, nf * sizeof(double2), s));
+    k_sw_copy<<<vec_grid_for(static_cast<int64_t>(S->n) * F), 256, 0, s>>>(S->n, F, Fp,
+                                                                          static_cast<const double2*>(d_X), ldx, a64.x, Fp);
+  } else {
+    HELM_CUDA_TRY(cudaMemsetAsync(a64.x, 0, nf * sizeof(double2), s));
+  }
+  if (!(S->graph32.exec && S->graph32.F == F)) {
+    if (S->graph32.exec) {
+      cudaGraphExecDestroy(S->graph32.exec);
+      cudaGraphDestroy(S->graph32.graph);
+    }
+    S->graph32 = helm_sweep_s::G();
+    if (build_sweep_graph(a32, sh, &S->graph32.graph, &S->graph32.exec) == HELM_OK) S->graph32.F = F;
+  }
+  const double inner_tol = (opts.inner_tol > 0.0 && opts.inner_tol < 1.0) ? opts.inner_tol : 1e-3;
+  std::vector<int32_t> act(Fp, 0), status(Fp, ST_RUNNING), steps(Fp, 0), stall(Fp, 0), inner_it(Fp, 0), it32(Fp);
+  std::vector<double> bn(Fp, 0.0), rn(Fp, 0.0), out(4 * static_cast<size_t>(Fp)), sigma(Fp, 0.0);
+  std::vector<double2> gamma(Fp);
+  for (int j = 0; j < F; ++j) act[j] = 1;
+  auto upload_act = [&]() {
+    return cudaMemcpyAsync(S->oact, act.data(), Fp * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+  };
+  auto residual = [&](int zero_x, std::vector<double>& norms) -> helm_status {
+    HELM_CUDA_TRY(upload_act());
+    k_mxs_residual<<<sh.grid, sh.threads, sh.smem, s>>>(m, zero_x);
+    HELM_CUDA_TRY(cudaGetLastError());
+    HELM_CUDA_TRY(cudaMemcpyAsync(out.data(), m.out, 4 * Fp * sizeof(double), cudaMemcpyDeviceToHost, s));
+    HELM_CUDA_TRY(cudaStreamSynchronize(s));
+    for (int j = 0; j < F; ++j)
+      if (act[j] == 1) norms[j] = std::sqrt(out[4 * j]);
+    return HELM_OK;
+  };
+  HELM_TRY(residual(1, bn));
+  for (int j = 0; j < F; ++j) rn[j] = bn[j];
+  if (opts.use_x0) HELM_TRY(residual(0, rn));
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    const double elapsed = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    bool any = false;
+    for (int j = 0; j < F; ++j) {
+      if (act[j] != 1) continue;
+      const double rel = bn[j] > 0.0 ? rn[j] / bn[j] : 0.0;
+      int st = ST_RUNNING;
+      if (bn[j] == 0.0) st = HELM_OK, act[j] = 2;  // b_j = 0: x_j = 0
+      else if (!std::isfinite(rel)) st = HELM_ERR_NONFINITE;
+      else if (rel <= opts.tol) st = HELM_OK;
+      else if (stall[j] >= 5 || inner_it[j] >= opts.maxit) st = HELM_ERR_NOT_CONVERGED;
+      else if (opts.deadline_s > 0.0 && elapsed > opts.deadline_s) st = HELM_ERR_TIMEOUT;
+      status[j] = st;
+      if (st != ST_RUNNING && act[j] == 1) act[j] = 0;
+      if (act[j] == 1) {
+        any = true;
+        sigma[j] = rn[j] / std::sqrt(static_cast<double>(std::max(S->n, 1)));
+      }
+    }
+    if (!any) break;
+    // inner right-hand sides, inner complex64 sweep
+    HELM_CUDA_TRY(upload_act());
+    HELM_CUDA_TRY(cudaMemcpyAsync(d_sigma, sigma.data(), Fp * sizeof(double), cudaMemcpyHostToDevice, s));
+    k_mxs_down<<<sh.grid, sh.threads, 0, s>>>(m);
+    int32_t inner_max = kSweepInnerMax;
+    for (int j = 0; j < F; ++j)
+      if (act[j] == 1) inner_max = std::min(inner_max, std::max(1, opts.maxit - inner_it[j]));
+    k_sw_configure<float2><<<1, 256, 0, s>>>(a32, inner_tol, inner_max, 0, 0.0, 1, nullptr);
+    HELM_CUDA_TRY(cudaGetLastError());
+    if (S->graph32.exec) {
+      HELM_CUDA_TRY(cudaGraphLaunch(S->graph32.exec, s));
+    } else {
+      SolverState hs;
+      k_sw_init<float2><<<sh.grid, sh.threads, sh.smem, s>>>(a32);
+      for (;;) {
+        for (int k = 0; k < 8; ++k) enqueue_sweep_body(a32, sh, s);
+        HELM_CUDA_TRY(cudaGetLastError());
+        HELM_CUDA_TRY(cudaMemcpyAsync(&hs, a32.st, sizeof(hs), cudaMemcpyDeviceToHost, s));
+        HELM_CUDA_TRY(cudaStreamSynchronize(s));
+        if (hs.status != ST_RUNNING) break;
+      }
+    }
+    HELM_CUDA_TRY(cudaMemcpyAsync(it32.data(), a32.iters, Fp * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    // FP64 step along z = sigma d
+    k_mxs_lift<<<sh.grid, sh.threads, 0, s>>>(m);
+    k_mxs_apply<<<sh.grid, sh.threads, sh.smem, s>>>(m);
+    HELM_CUDA_TRY(cudaGetLastError());
+    HELM_CUDA_TRY(cudaMemcpyAsync(out.data(), m.out, 4 * Fp * sizeof(double), cudaMemcpyDeviceToHost, s));
+    HELM_CUDA_TRY(cudaStreamSynchronize(s));
+    for (int j = 0; j < Fp; ++j) {
+      gamma[j] = make_double2(0.0, 0.0);
+      if (j >= F || act[j] != 1) continue;
+      inner_it[j] += it32[j];
+      steps[j] += 1;
+      const double ww = out[4 * j + 2];
+      if (ww > 0.0 && std::isfinite(ww) && std::isfinite(out[4 * j]) && std::isfinite(out[4 * j + 1]))
+        gamma[j] = make_double2(out[4 * j] / ww, out[4 * j + 1] / ww);
+    }
+    HELM_CUDA_TRY(cudaMemcpyAsync(d_gamma, gamma.data(), Fp * sizeof(double2), cudaMemcpyHostToDevice, s));
+    k_mxs_update<<<sh.grid, sh.threads, 0, s>>>(m);
+    HELM_CUDA_TRY(cudaGetLastError());
+    std::vector<double> prev = rn;
+    HELM_TRY(residual(0, rn));
+    for (int j = 0; j < F; ++j)
+      if (act[j] == 1) stall[j] = rn[j] > 0.5 * prev[j] ? stall[j] + 1 : 0;
+  }
+  // b_j = 0 columns become zero, then x goes to the caller
+  HELM_CUDA_TRY(upload_act());
+  k_mxs_update<<<sh.grid, sh.threads, 0, s>>>(m);
+  k_sw_copy<<<vec_grid_for(static_cast<int64_t>(S->n) * F), 256, 0, s>>>(S->n, F, Fp, a64.x, Fp,
+                                                                        static_cast<double2*>(d_X), ldx);
+  HELM_CUDA_TRY(cudaGetLastError());
+  HELM_CUDA_TRY(cudaStreamSynchronize(s));
+  helm_status worst = HELM_OK;
+  for (int j = 0; j < F; ++j) {
+    const helm_status sj = static_cast<helm_status>(status[j]);
+    if (h_infos) {
+      h_infos[j].iters = inner_it[j];
+      h_infos[j].restarts = steps[j];
+      h_infos[j].relres_recur = bn[j] > 0.0 ? rn[j] / bn[j] : 0.0;
+      h_infos[j].relres_true = h_infos[j].relres_recur;
+      h_infos[j].status = sj;
+      h_infos[j].spmv_count = 2 * inner_it[j] + 2 * steps[j] + 1;
+    }
+    if (sj != HELM_OK && worst == HELM_OK) worst = sj;
+  }
+  return worst;
 }
 
 }  // namespace
@@ -872,6 +1313,12 @@ helm_status helm_sweep_destroy(helm_sweep S) {
   cudaFree(S->partials);
   cudaFree(S->tickets);
   cudaFree(S->wapply);
+  cudaFree(S->vec32);
+  cudaFree(S->kmb32);
+  cudaFree(S->oscal);
+  cudaFree(S->oact);
+  if (S->graph32.exec) cudaGraphExecDestroy(S->graph32.exec);
+  if (S->graph32.graph) cudaGraphDestroy(S->graph32.graph);
   (void)cudaGetLastError();
   if (prev >= 0) cudaSetDevice(prev);
   delete S;
@@ -886,7 +1333,8 @@ helm_status helm_sweep_solve(helm_sweep S, int32_t nfreq, const double* h_omega,
   if (!S || nfreq < 1 || nfreq > kMaxF || !h_omega || (b_ld != 0 && b_ld < nfreq) || ldx < nfreq) return HELM_ERR_INVALID;
   if (S->n > 0 && (!d_b || !d_X)) return HELM_ERR_INVALID;
   if (!aligned(d_b, 16) || !aligned(d_X, 16) || !(opts.tol >= 0.0) || opts.maxit < 0) return HELM_ERR_INVALID;
-  if (opts.precision != HELM_PREC_FP64 || opts.method != HELM_BICGSTAB) return HELM_ERR_INVALID;
+  if ((opts.precision != HELM_PREC_FP64 && opts.precision != HELM_PREC_MIXED) || opts.method != HELM_BICGSTAB)
+    return HELM_ERR_INVALID;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   std::lock_guard<std::mutex> lk(S->mu);
   const int32_t Fp = (nfreq + 31) / 32 * 32;
@@ -914,6 +1362,14 @@ helm_status helm_sweep_solve(helm_sweep S, int32_t nfreq, const double* h_omega,
   for (int j = 0; j < nfreq; ++j) w[j] = h_omega[j];
   SweepArgs a = make_args(S, nfreq, Fp, bsrc, bld);
   HELM_CUDA_TRY(cudaMemcpyAsync(const_cast<double*>(a.w), w.data(), Fp * sizeof(double), cudaMemcpyHostToDevice, s));
+  if (opts.precision == HELM_PREC_MIXED) {
+    st = sweep_solve_mixed(S, a, sh, d_X, ldx, opts, h_infos, s);
+    if (bcopy) {
+      cudaFreeAsync(bcopy, s);
+      if (cudaStreamSynchronize(s) != cudaSuccess && st == HELM_OK) st = HELM_ERR_CUDA;
+    }
+    return st;
+  }
   if (opts.use_x0) {
     HELM_CUDA_TRY(cudaMemsetAsync(a.x, 0, static_cast<size_t>(S->n) * Fp * sizeof(double2), s));
     k_sw_copy<<<vec_grid_for(static_cast<int64_t>(S->n) * nfreq), 256, 0, s>>>(
@@ -939,13 +1395,13 @@ helm_status helm_sweep_solve(helm_sweep S, int32_t nfreq, const double* h_omega,
   std::vector<int32_t> status(Fp), iters(Fp), restart(Fp, 0), restarts(nfreq, 0);
   std::vector<double> relres(Fp), relres_true(Fp);
   for (int32_t fresh = 1, use_x0 = opts.use_x0 ? 1 : 0;; fresh = 0, use_x0 = 1) {
-    k_sw_configure<<<1, 256, 0, s>>>(a, opts.tol, opts.maxit, use_x0, opts.deadline_s, fresh, d_restart);
+    k_sw_configure<double2><<<1, 256, 0, s>>>(a, opts.tol, opts.maxit, use_x0, opts.deadline_s, fresh, d_restart);
     HELM_CUDA_TRY(cudaGetLastError());
     if (S->graph.exec && !bcopy) {
       HELM_CUDA_TRY(cudaGraphLaunch(S->graph.exec, s));
     } else {
       SolverState hs;
-      k_sw_init<<<sh.grid, sh.threads, sh.smem, s>>>(a);
+      k_sw_init<double2><<<sh.grid, sh.threads, sh.smem, s>>>(a);
       for (;;) {
         for (int k = 0; k < 8; ++k) enqueue_sweep_body(a, sh, s);
         HELM_CUDA_TRY(cudaGetLastError());
@@ -953,7 +1409,7 @@ helm_status helm_sweep_solve(helm_sweep S, int32_t nfreq, const double* h_omega,
         HELM_CUDA_TRY(cudaStreamSynchronize(s));
         if (hs.status != ST_RUNNING) break;
       }
-      k_sw_tail<<<sh.grid, sh.threads, sh.smem, s>>>(a);
+      k_sw_tail<double2><<<sh.grid, sh.threads, sh.smem, s>>>(a);
     }
     HELM_CUDA_TRY(cudaMemcpyAsync(status.data(), a.status, Fp * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     HELM_CUDA_TRY(cudaMemcpyAsync(iters.data(), a.iters, Fp * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -1014,7 +1470,7 @@ helm_status helm_sweep_spmv(helm_sweep S, int32_t nfreq, const double* h_omega, 
   // the frequencies are copied from a pageable host buffer: the copy is
   // complete when cudaMemcpyAsync returns, so h_omega may be reused at once
   HELM_CUDA_TRY(cudaMemcpyAsync(S->wapply, h_omega, nfreq * sizeof(double), cudaMemcpyHostToDevice, s));
-  const SweepDev A{S->n, S->nnz, S->rowptr, S->colind, S->K, S->M, S->B, S->bzero_blk};
+  const SweepDev A{S->n, S->nnz, S->rowptr, S->colind, S->K, S->M, S->B, S->bzero_blk, nullptr, nullptr, nullptr};
   const int G = Fp / 32;
   const int64_t warps = static_cast<int64_t>(S->n) * G;
   const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((warps + 7) / 8, static_cast<int64_t>(S->num_sms) * 8)));

@@ -59,7 +59,7 @@ def test_sweep_small_vs_oracle(dims, freqs, shared_b):
 
 def test_sweep60_against_oracle():
     """60x30x25 cavity, 64 frequencies 100-1000 Hz at 1e-8 (the benchmark's
-    sweep).  Every frequency: status ok and the true residual, recomputed with
+    sweep), FP64 and complex64-inner.  Every frequency: status ok and the true residual, recomputed with
     the oracle's SpMV on the oracle-assembled A_j, at most tol.  Five
     frequencies spread over the band, the hardest (1000 Hz) among them,
     against the oracle's BiCGStab on A_j: ||x_gpu - x_tight|| / ||x_tight||
@@ -93,13 +93,74 @@ def test_sweep60_against_oracle():
             assert infos[j]["status"] == "ok", (j, infos[j])
             r = _relres(p, vals, b, Xh[:, j])
             assert r <= cfg.tol * (1 + 1e-6) and abs(r - infos[j]["relres_true"]) <= 1e-3 * r, (j, r, infos[j])
+        # the complex64-inner (mixed-precision) sweep of the same system
+        S = helm.Sweep(p.rowptr, p.colind, p.K, p.Mc, p.Bc, device=DEV)
+        Xm, infm = S.solve(w, torch.as_tensor(b, device=DEV), tol=cfg.tol, maxit=200000,
+                           precision=helm.HELM_PREC_MIXED)
+        Xmh = Xm.cpu().numpy()
+        S.close()
+        print(f"sweep60 mixed: inner iterations total {sum(i['iters'] for i in infm)}, refinement steps "
+              f"{sum(i['restarts'] for i in infm)}")
+        for j in range(len(w)):
+            vals = oracle.helmholtz_values(p.K, p.Mc, p.Bc, w[j])
+            assert infm[j]["status"] == "ok", (j, infm[j])
+            r = _relres(p, vals, b, Xmh[:, j])
+            assert r <= cfg.tol * (1 + 1e-6) and abs(r - infm[j]["relres_true"]) <= 1e-3 * r, (j, r, infm[j])
         for j in picks:
             x_o, x_t = futs[(j, 1e-8)].result(), futs[(j, 1e-13)].result()
             nt = np.linalg.norm(x_t)
-            e_g = np.linalg.norm(Xh[:, j] - x_t) / nt
             e_o = np.linalg.norm(x_o - x_t) / nt
-            print(f"  F = {cfg.freqs[j]:.1f} Hz: gpu error {e_g:.2e}, oracle error {e_o:.2e}, iters {iters[j]}")
-            assert e_g <= max(1e-8, 2 * e_o), (j, e_g, e_o)
+            # the FP64 sweep runs the oracle's method: within 2x of its error.  The
+            # mixed sweep reaches the same residual by minimal-residual refinement
+            # steps, whose residual A^-1 amplifies differently from a BiCGStab
+            # iterate's: its error gate is 4x (the residual gate above is exact)
+            for tag, XX, ii, fac in (("fp64", Xh, iters, 2.0), ("mixed", Xmh, [i["iters"] for i in infm], 4.0)):
+                e_g = np.linalg.norm(XX[:, j] - x_t) / nt
+                print(f"  F = {cfg.freqs[j]:.1f} Hz {tag}: gpu error {e_g:.2e}, oracle error {e_o:.2e}, iters {ii[j]}")
+                assert e_g <= max(1e-8, fac * e_o), (tag, j, e_g, e_o)
+
+
+@pytest.mark.parametrize("dims,freqs,shared_b", [
+    ((4, 3, 3), [150.0, 420.0, 800.0], True),
+    ((6, 5, 4), list(np.linspace(100.0, 1000.0, 40)), False),
+])
+def test_sweep_mixed_small_vs_oracle(dims, freqs, shared_b):
+    """The complex64-inner sweep to 1e-10 on small meshes: every frequency's
+    FP64 residual, recomputed with the oracle's SpMV on the oracle-assembled
+    A_j, at most tol, and the solution gate against dense LU and the
+    oracle's own solve at the same tolerance."""
+    cfg = g.tiny_config(*dims, h=0.1, seed=6)
+    p = g.assemble(cfg)
+    F = len(freqs)
+    w = [g.omega(f) for f in freqs]
+    if shared_b:
+        b = g.source(p) + 0.2 * g.complex_vector(p.n, 3) * (~p.dirichlet)
+        bt = torch.as_tensor(b, device=DEV)
+        bs = [b] * F
+    else:
+        B = np.stack([g.complex_vector(p.n, 10 + j) * (~p.dirichlet) for j in range(F)], axis=1)
+        bt = torch.as_tensor(B, device=DEV).contiguous()
+        bs = [B[:, j] for j in range(F)]
+    S = helm.Sweep(p.rowptr, p.colind, p.K, p.Mc, p.Bc, device=DEV)
+    X, infos = S.solve(w, bt, tol=1e-10, maxit=50000, precision=helm.HELM_PREC_MIXED)
+    Xh = X.cpu().numpy()
+    for j in range(F):
+        vals = oracle.helmholtz_values(p.K, p.Mc, p.Bc, w[j])
+        assert infos[j]["status"] == "ok", (j, infos[j])
+        r = _relres(p, vals, bs[j], Xh[:, j])
+        assert r <= 1e-10 * (1 + 1e-6) and abs(r - infos[j]["relres_true"]) <= 1e-3 * r + 1e-15
+        xs = oracle.dense_solve(p.rowptr, p.colind, vals, bs[j])
+        xo, _ = oracle.bicgstab(p.rowptr, p.colind, vals, bs[j], tol=1e-10, maxit=20000)
+        e_g = np.linalg.norm(Xh[:, j] - xs) / np.linalg.norm(xs)
+        e_o = np.linalg.norm(xo - xs) / np.linalg.norm(xs)
+        assert e_g <= max(1e-8, 2 * e_o), (j, e_g, e_o)
+    # b = 0 for one frequency column: x = 0 there, ok
+    if not shared_b:
+        B[:, 0] = 0.0
+        X, infos = S.solve(w, torch.as_tensor(B, device=DEV).contiguous(), tol=1e-10, maxit=50000,
+                           precision=helm.HELM_PREC_MIXED)
+        assert infos[0]["status"] == "ok" and torch.all(X[:, 0] == 0)
+    S.close()
 
 
 def test_sweep_operator_entries_and_product():
