@@ -14,6 +14,7 @@ ranks over the slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import math
@@ -551,14 +552,19 @@ def run_spmv_only(args):
 # Vector lengths of the paper's BLAS-1 measurements (Section 3, Tables 2-7):
 # the order of Audi3D-4 and three larger sizes.
 VECTOR_SIZES = (648_849, 2_000_000, 9_000_000, 14_000_000)
+# Nominal FP64 rate of a GB300 (1.25 TFLOP/s): FP64 fused multiply-adds per second.
+FP64_DFMA_PER_S = 0.625e12
 
 
 def run_vectors(args):
     """The BLAS-1 operations of Section 3 alone, through the C ABI, on
     complex128 vectors of the paper's lengths: assign (y = x, Table 2), scal
-    (y = beta y, Table 3), axpy (y = alpha x + y, Table 4), zdotc (Tables 5-6)
-    and the 2-norm (Table 7).  Every launch is timed alone with CUDA events
-    after a 256 MB write that evicts the vectors from L2; the median launch
+    (y = beta y, Table 3), axpy (y = alpha x + y, Table 4), zdotc (Tables 5-6,
+    also through helm_dot_noalloc, whose scratch is a fixed array instead of
+    the stream-ordered allocator) and the 2-norm (Table 7).  Every launch is
+    timed alone with CUDA events after a 256 MB READ that evicts the vectors
+    from L2 and leaves only clean lines behind (a write would leave dirty
+    lines whose write-back lands inside the timed launch); the median launch
     gives GB/s on the algorithmic bytes (each vector read or written once).
     One JSON line per length."""
     import torch
@@ -570,39 +576,52 @@ def run_vectors(args):
     torch.cuda.set_device(dev)
     peaks, peak_src = load_peaks()
     peak = float(peaks["hbm_gbs"])
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB, above L2
+    flush = torch.ones(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB, above L2
+    flush_out = torch.zeros((), dtype=torch.float32, device=dev)
     out_c = torch.zeros(1, dtype=torch.complex128, device=dev)
+    lib = helm.load_library()
+    stream = torch.cuda.current_stream().cuda_stream
     out_r = torch.zeros(1, dtype=torch.float64, device=dev)
     for n in VECTOR_SIZES:
         x = torch.as_tensor(helmgen.complex_vector(n, 4), device=dev)
         y = torch.as_tensor(helmgen.complex_vector(n, 5), device=dev)
-        # name -> (call, algorithmic bytes); |beta| = 1 in scal keeps y's scale
+        # name -> (call, algorithmic bytes, FP64 instructions per element);
+        # |beta| = 1 in scal keeps y's scale
         ops = {
-            "assign": (lambda: helm.helm_axpby(1.0, x, 0.0, y), 32 * n),
-            "scal": (lambda: helm.helm_axpby(0.0, None, 0.6 + 0.8j, y), 32 * n),
-            "axpy": (lambda: helm.helm_axpby(0.3 - 0.1j, x, 1.0, y), 48 * n),
-            "zdotc": (lambda: helm.helm_dot(x, y, out_c), 32 * n),
-            "nrm2": (lambda: helm.helm_nrm2(x, out_r), 16 * n),
+            "assign": (lambda: helm.helm_axpby(1.0, x, 0.0, y), 32 * n, 0),
+            "scal": (lambda: helm.helm_axpby(0.0, None, 0.6 + 0.8j, y), 32 * n, 4),
+            "axpy": (lambda: helm.helm_axpby(0.3 - 0.1j, x, 1.0, y), 48 * n, 4),
+            "zdotc": (lambda: helm.helm_dot(x, y, out_c), 32 * n, 4),
+            "zdotc_noalloc": (lambda: lib.helm_dot_noalloc(
+                ctypes.c_int64(n), helm.HELM_C128, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                1, ctypes.c_void_p(out_c.data_ptr()), ctypes.c_void_p(stream)), 32 * n, 4),
+            "nrm2": (lambda: helm.helm_nrm2(x, out_r), 16 * n, 2),
         }
         res = {}
-        for name, (fn, nbytes) in ops.items():
+        for name, (fn, nbytes, fp64_per) in ops.items():
             for _ in range(args.warmup):
                 fn()
             ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                   for _ in range(args.reps)]
             torch.cuda.synchronize()
             for e0, e1 in ev:
-                flush.zero_()
+                torch.sum(flush, dim=0, out=flush_out)
                 e0.record()
                 fn()
                 e1.record()
             torch.cuda.synchronize()
             us = statistics.median(e0.elapsed_time(e1) for e0, e1 in ev) * 1e3
             gbs = nbytes / us / 1e3
-            res[name] = {"us": round(us, 2), "gbs": round(gbs, 1), "frac": round(gbs / peak, 3)}
+            # the roof is the slower of the two pipes the op needs: HBM for its
+            # bytes, the FP64 pipe (nominal FP64_DFMA_PER_S) for its products
+            roof_us = max(nbytes / peak / 1e3, fp64_per * n / FP64_DFMA_PER_S * 1e6)
+            res[name] = {"us": round(us, 2), "gbs": round(gbs, 1), "frac": round(gbs / peak, 3),
+                         "fp64_per_elem": fp64_per, "bound": "fp64" if fp64_per * n / FP64_DFMA_PER_S * 1e6 >
+                         nbytes / peak / 1e3 else "hbm", "roof_us": round(roof_us, 2),
+                         "frac_of_roof": round(roof_us / us, 3)}
         print(json.dumps({"mode": "vectors", "n": n, "dtype": "c128", "ops": res, "peak_gbs": peak,
                           "peak_source": peak_src, "reps": args.reps, "warmup": args.warmup,
-                          "l2": "256 MB write before every launch"}), flush=True)
+                          "l2": "256 MB read before every launch"}), flush=True)
         del x, y
 
 

@@ -137,9 +137,10 @@ helm_status helm_dot(int64_t n, helm_dtype dt, const void* d_x, const void* d_y,
  *   stream-ordered allocator.
  *   Maximum size: n < 2^31; larger n returns HELM_ERR_INVALID.  The grid never
  *   exceeds 4096 blocks, so every n below the maximum fits the array.
- *   Set-up: the first call on a device (with that device current) looks up
- *   the array's device address with cudaGetSymbolAddress and caches it; make
- *   that first call before any stream capture.  A failed lookup returns
+ *   Address: every call looks up the array's device address on the current
+ *   device with cudaGetSymbolAddress (a host-side lookup; the first call on a
+ *   device may also load the library's device code).  Nothing is cached, so
+ *   a device reset needs nothing special.  A failed lookup returns
  *   HELM_ERR_CUDA.
  *   Sharing: all calls on a device share the one array and it keeps the last
  *   call's contents; nothing in it needs to start at zero (every slot read is
@@ -163,7 +164,8 @@ helm_status helm_nrm2(int64_t n, helm_dtype dt, const void* d_x, double* d_out,
  * beta = 1; ZSCAL, Table 3, is alpha = 0 with y scaled by beta; ZASSIGN,
  * Table 2, is alpha = 1, beta = 0).
  *   alpha, beta : host complex128 (double[2]).
- *   d_x         : complex[n]; may equal d_y.  Not read when alpha == 0.
+ *   d_x         : complex[n]; may equal d_y, must not otherwise overlap it.
+ *                 Not read when alpha == 0.
  *   d_y         : complex[n]; not read when beta == 0.
  * Asynchronous.
  */
@@ -195,8 +197,14 @@ typedef enum {
                                  cooperative kernel whose phases are separated
                                  by grid barriers; the same arithmetic as the
                                  graph, bit for bit.  Every barrier wait gives
-                                 up after 2 s (HELM_ERR_CUDA).  HELM_ERR_CUDA
-                                 if the device cannot launch it */
+                                 up after 2 s: the block sets a device error
+                                 flag of the handle, every block leaves the
+                                 kernel, and the solve returns HELM_ERR_CUDA.
+                                 Every solve clears that flag when it starts,
+                                 so a later solve on the handle is unaffected;
+                                 helm_spmv has no waits and never sets it.
+                                 HELM_ERR_CUDA also if the device cannot
+                                 launch the kernel */
   HELM_LAUNCH_HOST = 3        /* host-driven loop of the same kernels, state
                                  polled every 16 iterations (profiling: tools
                                  that cannot see inside conditional graphs) */

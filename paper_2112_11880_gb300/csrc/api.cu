@@ -186,6 +186,14 @@ __global__ void k_csr_check(int32_t n, int64_t nnz, const int32_t* __restrict__ 
   if (bad) atomicOr(&out[1], 1);
 }
 
+// The BLAS-1 kernels below walk the vectors with a grid-stride loop and take
+// four strides per trip: all loads of the trip are issued before the first
+// product, so every thread keeps four (axpby: eight) 16-byte loads in flight
+// instead of one or two.  A thread still adds its elements i, i+T, i+2T, ...
+// (T threads in the grid) in that order, so the sums are the same bits as a
+// one-stride loop over the same grid.
+constexpr int kVecIlp = 4;
+
 // One block-sized partial of (x, y) per block; complex64 inputs accumulate
 // products in FP32 per thread (few terms each) and everything above in FP64.
 template <class V, bool CONJ>
@@ -193,7 +201,21 @@ __global__ void __launch_bounds__(256) k_dot_partial(int64_t n, const V* __restr
                                                      const V* __restrict__ y, double* partials) {
   __shared__ double red[32 * 2];
   V acc = vzero<V>();
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t T = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (; i + (kVecIlp - 1) * T < n; i += kVecIlp * T) {
+    V a[kVecIlp], b[kVecIlp];
+#pragma unroll
+    for (int k = 0; k < kVecIlp; ++k) a[k] = ld_stream(x + i + k * T);
+#pragma unroll
+    for (int k = 0; k < kVecIlp; ++k) b[k] = ld_stream(y + i + k * T);
+#pragma unroll
+    for (int k = 0; k < kVecIlp; ++k) {
+      if (CONJ) a[k].y = -a[k].y;
+      acc = mac(a[k], b[k], acc);
+    }
+  }
+  for (; i < n; i += T) {
     V a = ld_stream(x + i);
     if (CONJ) a.y = -a.y;
     acc = mac(a, ld_stream(y + i), acc);
@@ -209,23 +231,26 @@ __global__ void __launch_bounds__(256) k_dot_partial(int64_t n, const V* __restr
 template <class V>
 __global__ void __launch_bounds__(256) k_nrm2_partial(int64_t n, const V* __restrict__ x, double* partials) {
   __shared__ double red[32];
-  double acc = 0.0;
-  if (sizeof(V) == sizeof(double2)) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-      const V a = ld_stream(x + i);
-      acc = fma((double)a.x, (double)a.x, acc);
-      acc = fma((double)a.y, (double)a.y, acc);
+  using S = decltype(V().x);  // FP64 sums for complex128, FP32 per thread for complex64
+  S acc = S(0);
+  const int64_t T = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (; i + (kVecIlp - 1) * T < n; i += kVecIlp * T) {
+    V a[kVecIlp];
+#pragma unroll
+    for (int k = 0; k < kVecIlp; ++k) a[k] = ld_stream(x + i + k * T);
+#pragma unroll
+    for (int k = 0; k < kVecIlp; ++k) {
+      acc = fma(a[k].x, a[k].x, acc);
+      acc = fma(a[k].y, a[k].y, acc);
     }
-  } else {
-    float accf = 0.f;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-      const V a = ld_stream(x + i);
-      accf = fmaf((float)a.x, (float)a.x, accf);
-      accf = fmaf((float)a.y, (float)a.y, accf);
-    }
-    acc = accf;
   }
-  double v[1] = {acc};
+  for (; i < n; i += T) {
+    const V a = ld_stream(x + i);
+    acc = fma(a.x, a.x, acc);
+    acc = fma(a.y, a.y, acc);
+  }
+  double v[1] = {static_cast<double>(acc)};
   block_sum<1>(v, red);
   if (threadIdx.x == 0) partials[blockIdx.x] = v[0];
 }
@@ -249,14 +274,63 @@ __global__ void __launch_bounds__(256) k_sum_partials(int nparts, const double* 
   }
 }
 
+// y = alpha x + beta y with the kinds of the two scalars fixed at compile
+// time (0: zero, 1: one, 2: real, 3: complex), so that a kernel does only the
+// products its scalars need: assignment (alpha = 1, beta = 0) is a copy, a real
+// scalar costs 2 real products an element, a complex one 4.  On this GPU a
+// complex128 axpy with complex alpha is as much FP64-pipe work as memory
+// traffic, so the products skipped here are time saved.  The values are those
+// of the full complex formula (a zero imaginary part adds exact zeros).
+template <class V, int XA, int YB>
+__device__ __forceinline__ V axpby_elem(V alpha, V xi, V beta, V yi) {
+  V r = vzero<V>();
+  if (YB == 1) r = yi;
+  if (YB == 2) r = V{beta.x * yi.x, beta.x * yi.y};
+  if (YB == 3) r = cmul(beta, yi);
+  if (XA == 1) r = YB == 0 ? xi : V{r.x + xi.x, r.y + xi.y};
+  if (XA == 2) r = V{fma(alpha.x, xi.x, r.x), fma(alpha.x, xi.y, r.y)};
+  if (XA == 3) r = mac(alpha, xi, r);
+  return r;
+}
+
+template <class V, int XA, int YB>
+__global__ void __launch_bounds__(256) k_axpby(int64_t n, V alpha, const V* x, V beta, V* y) {
+  const int64_t T = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (; i + (kVecIlp - 1) * T < n; i += kVecIlp * T) {
+    V xs[kVecIlp], ys[kVecIlp];
+#pragma unroll
+    for (int k = 0; k < kVecIlp; ++k) {
+      xs[k] = XA ? ld_stream(x + i + k * T) : vzero<V>();
+      ys[k] = YB ? ld_stream(y + i + k * T) : vzero<V>();
+    }
+#pragma unroll
+    for (int k = 0; k < kVecIlp; ++k) __stcs(y + i + k * T, axpby_elem<V, XA, YB>(alpha, xs[k], beta, ys[k]));
+  }
+  for (; i < n; i += T) {
+    const V xi = XA ? ld_stream(x + i) : vzero<V>();
+    const V yi = YB ? ld_stream(y + i) : vzero<V>();
+    __stcs(y + i, axpby_elem<V, XA, YB>(alpha, xi, beta, yi));
+  }
+}
+
+template <class V, int XA>
+void launch_axpby_yb(int yb, int grid, cudaStream_t s, int64_t n, V alpha, const V* x, V beta, V* y) {
+  switch (yb) {
+    case 0: k_axpby<V, XA, 0><<<grid, 256, 0, s>>>(n, alpha, x, beta, y); break;
+    case 1: k_axpby<V, XA, 1><<<grid, 256, 0, s>>>(n, alpha, x, beta, y); break;
+    case 2: k_axpby<V, XA, 2><<<grid, 256, 0, s>>>(n, alpha, x, beta, y); break;
+    default: k_axpby<V, XA, 3><<<grid, 256, 0, s>>>(n, alpha, x, beta, y); break;
+  }
+}
+
 template <class V>
-__global__ void __launch_bounds__(256) k_axpby(int64_t n, V alpha, const V* x, V beta, V* y, int mode) {
-  // mode bit 0: alpha != 0 (read x); bit 1: beta != 0 (read y); bit 2: beta == 1
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    V r = vzero<V>();
-    if (mode & 2) r = (mode & 4) ? y[i] : cmul(beta, y[i]);
-    if (mode & 1) r = mac(alpha, x[i], r);
-    y[i] = r;
+void launch_axpby(int xa, int yb, int grid, cudaStream_t s, int64_t n, V alpha, const V* x, V beta, V* y) {
+  switch (xa) {
+    case 0: launch_axpby_yb<V, 0>(yb, grid, s, n, alpha, x, beta, y); break;
+    case 1: launch_axpby_yb<V, 1>(yb, grid, s, n, alpha, x, beta, y); break;
+    case 2: launch_axpby_yb<V, 2>(yb, grid, s, n, alpha, x, beta, y); break;
+    default: launch_axpby_yb<V, 3>(yb, grid, s, n, alpha, x, beta, y); break;
   }
 }
 
@@ -834,15 +908,17 @@ helm_status helm_axpby(int64_t n, helm_dtype dt, const double* alpha, const void
   if (!d_y || (!is_zero(alpha) && !d_x)) return HELM_ERR_INVALID;
   const size_t esz = dt == HELM_C128 ? 16 : 8;
   if (!aligned(d_x, esz) || !aligned(d_y, esz)) return HELM_ERR_INVALID;
-  const int mode = (is_zero(alpha) ? 0 : 1) | (is_zero(beta) ? 0 : 2) | (is_one(beta) ? 4 : 0);
+  auto kind = [](const double* z) { return is_zero(z) ? 0 : is_one(z) ? 1 : z[1] == 0.0 ? 2 : 3; };
+  const int xa = kind(alpha), yb = kind(beta);
+  if (xa == 0 && yb == 1) return HELM_OK;  // y = y
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int grid = vec_grid_for(n);
   if (dt == HELM_C128)
-    k_axpby<double2><<<grid, 256, 0, s>>>(n, make_double2(alpha[0], alpha[1]), (const double2*)d_x,
-                                          make_double2(beta[0], beta[1]), (double2*)d_y, mode);
+    launch_axpby<double2>(xa, yb, grid, s, n, make_double2(alpha[0], alpha[1]), (const double2*)d_x,
+                          make_double2(beta[0], beta[1]), (double2*)d_y);
   else
-    k_axpby<float2><<<grid, 256, 0, s>>>(n, make_float2((float)alpha[0], (float)alpha[1]), (const float2*)d_x,
-                                         make_float2((float)beta[0], (float)beta[1]), (float2*)d_y, mode);
+    launch_axpby<float2>(xa, yb, grid, s, n, make_float2((float)alpha[0], (float)alpha[1]), (const float2*)d_x,
+                         make_float2((float)beta[0], (float)beta[1]), (float2*)d_y);
   HELM_CUDA_TRY(cudaGetLastError());
   return HELM_OK;
 }

@@ -13,10 +13,10 @@
 // The array g_dot_scratch below is a file-scope __device__ variable: every GPU
 // that loads libhelm holds one copy of it (64 KiB) until the process exits.
 // In host code its name is only a host-side stand-in, not a device address, so
-// the entry point looks up the real device address with cudaGetSymbolAddress
-// once per device (with that device current) and passes it to the kernels.
-#include <mutex>
-
+// every call looks up the real device address on the current device with
+// cudaGetSymbolAddress and passes it to the kernels.  Nothing is cached: after
+// a device reset the library's device code is loaded again (possibly at a new
+// address), and the next call sees that address.
 #include "common.cuh"
 #include "internal.hpp"
 #include "spmv.cuh"
@@ -29,10 +29,6 @@ namespace {
 constexpr int kNoallocMaxBlocks = 4096;
 constexpr int kNoallocThreads = 256;
 static __device__ __align__(256) double g_dot_scratch[2 * kNoallocMaxBlocks];
-
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mu;
-double* g_scratch_addr[kMaxDevices] = {nullptr};
 
 template <class V, bool CONJ>
 __global__ void __launch_bounds__(kNoallocThreads) k_dot_partial_na(int64_t n, const V* __restrict__ x,
@@ -67,24 +63,14 @@ __global__ void __launch_bounds__(kNoallocThreads) k_dot_final_na(int nparts, co
   }
 }
 
-// Device address of g_dot_scratch on the current device (looked up once).
+// Device address of g_dot_scratch on the current device.
 helm_status scratch_address(double** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) {
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_dot_scratch) != cudaSuccess || p == nullptr) {
     (void)cudaGetLastError();
     return HELM_ERR_CUDA;
   }
-  if (dev < 0 || dev >= kMaxDevices) return HELM_ERR_INVALID;
-  std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_dot_scratch) != cudaSuccess || p == nullptr) {
-      (void)cudaGetLastError();
-      return HELM_ERR_CUDA;
-    }
-    g_scratch_addr[dev] = static_cast<double*>(p);
-  }
-  *out = g_scratch_addr[dev];
+  *out = static_cast<double*>(p);
   return HELM_OK;
 }
 

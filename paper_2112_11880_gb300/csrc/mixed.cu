@@ -551,6 +551,7 @@ helm_status solve_mixed(helm_csr A, const double2* b, double2* x, const helm_opt
 
   // an explicit graph request does not fall back to the host-driven loop
   if (!g && o.launch == HELM_LAUNCH_GRAPH) return HELM_ERR_CUDA;
+  HELM_CUDA_TRY(cudaMemsetAsync(A->dev_err, 0, sizeof(unsigned int), s));
   k_configure<<<1, 1, 0, s>>>(A->state, o.tol, o.maxit, o.use_x0 ? 1 : 0, o.deadline_s, 1);
   k_mx_configure<<<1, 1, 0, s>>>(A->state, o.inner_tol);
   HELM_CUDA_TRY(cudaGetLastError());

@@ -474,6 +474,7 @@ helm_status tfqmr_fp64(helm_csr A, const double2* b, double2* x, const helm_opts
   SolverState* hs = A->state_host;
   unsigned int herr = 0;
   int32_t use_x0 = o.use_x0 ? 1 : 0, fresh = 1;
+  HELM_CUDA_TRY(cudaMemsetAsync(A->dev_err, 0, sizeof(unsigned int), s));
   for (;;) {
     k_configure<<<1, 1, 0, s>>>(A->state, o.tol, o.maxit, use_x0, o.deadline_s, fresh);
     HELM_CUDA_TRY(cudaGetLastError());

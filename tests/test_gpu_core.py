@@ -162,7 +162,11 @@ def test_dot_c64():
     assert abs(d - ref) <= (per_thread + 2) * 2 * U32 * np.sum(np.abs(x) * np.abs(y))
 
 
-@pytest.mark.parametrize("alpha,beta", [(2 - 1j, 0.5 + 0.5j), (0.0, 3.0), (1.5, 0.0), (1j, 1.0), (0.0, 0.0)])
+AXPBY_CASES = [(2 - 1j, 0.5 + 0.5j), (0.0, 3.0), (1.5, 0.0), (1j, 1.0), (0.0, 0.0), (1.0, 0.0), (0.0, 1.0),
+               (0.7, 1.0), (1.0, -2.5), (1.0, 1.0), (0.0, 0.6 + 0.8j), (-0.3, 0.5 - 2j), (1.0, 1j)]
+
+
+@pytest.mark.parametrize("alpha,beta", AXPBY_CASES)
 def test_axpby(alpha, beta):
     n = 100_003
     x = g.complex_vector(n, 17)
@@ -172,6 +176,29 @@ def test_axpby(alpha, beta):
     ref = alpha * x + beta * y
     scale = abs(alpha) * np.abs(x) + abs(beta) * np.abs(y)
     assert np.all(np.abs(yd.cpu().numpy() - ref) <= 4e-16 * scale + 1e-300)
+
+
+@pytest.mark.parametrize("alpha,beta", AXPBY_CASES[:6] + [(0.7, 1.0), (1.0, -2.5)])
+def test_axpby_complex64_and_aliased(alpha, beta):
+    """complex64 vectors (FP32 products: at most 4 roundings of 2^-24 each
+    relative to |alpha||x| + |beta||y|), and x equal to y (y = (alpha + beta) y
+    element by element)."""
+    n = 70_001
+    x = g.complex_vector(n, 27).astype(np.complex64)
+    y = g.complex_vector(n, 28).astype(np.complex64)
+    yd = _dev(y.copy())
+    helm.helm_axpby(alpha, _dev(x), beta, yd)
+    a32, b32 = complex(np.complex64(alpha)), complex(np.complex64(beta))
+    xe, ye = x.astype(np.complex128), y.astype(np.complex128)
+    ref = a32 * xe + b32 * ye
+    scale = abs(a32) * np.abs(xe) + abs(b32) * np.abs(ye)
+    assert np.all(np.abs(yd.cpu().numpy().astype(np.complex128) - ref) <= 4 * 2.0 ** -24 * scale + 1e-38)
+    z = g.complex_vector(n, 29)
+    zd = _dev(z.copy())
+    helm.helm_axpby(alpha, zd, beta, zd)
+    ref = alpha * z + beta * z
+    scale = (abs(alpha) + abs(beta)) * np.abs(z)
+    assert np.all(np.abs(zd.cpu().numpy() - ref) <= 4e-16 * scale + 1e-300)
 
 
 def test_invalid_arguments_rejected():
