@@ -417,6 +417,8 @@ def extension_summary(dev, args):
     S.solve(w, b, tol=cfg.tol, maxit=200000, precision=helm.HELM_PREC_MIXED, inner_tol=0.01)
     (Xm, infm), t_mixed = timed(lambda: S.solve(w, b, tol=cfg.tol, maxit=200000, precision=helm.HELM_PREC_MIXED,
                                                 inner_tol=0.01))
+    S.solve(w, b, tol=cfg.tol, maxit=50000, method=helm.HELM_TFQMR)
+    (Xq, infq), t_tfqmr = timed(lambda: S.solve(w, b, tol=cfg.tol, maxit=50000, method=helm.HELM_TFQMR))
     S.close()
     t_single, it_single, ok_single = 0.0, 0, True
     for F in cfg.freqs:
@@ -441,7 +443,13 @@ def extension_summary(dev, args):
                                 "vs_fp64_batched": round(t_sweep / t_mixed, 3),
                                 "converged": all(i["status"] == "ok" for i in infm),
                                 "worst_relres_true": max(i["relres_true"] for i in infm),
-                                "inner_iters_total": sum(i["iters"] for i in infm)}}
+                                "inner_iters_total": sum(i["iters"] for i in infm)},
+                      "tfqmr": {"s": round(t_tfqmr, 3), "freq_solves_per_s": round(len(w) / t_tfqmr, 3),
+                                "vs_bicgstab_batched": round(t_sweep / t_tfqmr, 3),
+                                "converged": all(i["status"] == "ok" for i in infq),
+                                "worst_relres_true": max(i["relres_true"] for i in infq),
+                                "iters_total": sum(i["iters"] for i in infq),
+                                "restarts": sum(i["restarts"] for i in infq)}}
 
     # config 3
     cfg = helmgen.CONFIGS["cavity200"]

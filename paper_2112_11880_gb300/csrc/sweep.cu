@@ -1,6 +1,7 @@
-// Batched frequency sweep: BiCGStab for F frequencies on one sparsity pattern,
-// A_j = K - w_j^2 M + i w_j B formed on the fly (the Helmholtz operator of
-// Section 1 at wavenumbers k = w_j / c, with the impedance term).
+// Batched frequency sweep: BiCGStab or TFQMR (Section 4's solvers) for F
+// frequencies on one sparsity pattern, A_j = K - w_j^2 M + i w_j B formed on
+// the fly (the Helmholtz operator of Section 1 at wavenumbers k = w_j / c,
+// with the impedance term); BiCGStab also with complex64 inner solves.
 //
 // Layout: every Krylov vector is node-major, frequency-minor: V[i * Fp + j],
 // Fp = F rounded up to a multiple of 32.  A warp owns one row and 32
@@ -68,6 +69,13 @@ struct SweepArgsT {
   double *bnorm, *relres, *relres_true; // [Fp]
   int32_t *status, *iters, *phase;      // [Fp]
   int32_t* gactive;                     // [G]: a frequency of the group is running
+  // batched TFQMR only (null otherwise): A un and d [n][Fp]; gamma and
+  // (theta, tau) [Fp]; the true-residual check flags per frequency, per group
+  // and for the whole sweep; the iteration at which each frequency's
+  // current (re)start began
+  V *q1, *q2;
+  double2 *gam, *tt;
+  int32_t *chk, *gcheck, *anychk, *start;
   SolverState* st;                      // tol, maxit, deadline, use_x0
   double* partials;                     // [blocks][Fp][K]
   unsigned int* tickets;
@@ -597,6 +605,344 @@ __global__ void __launch_bounds__(512) k_sw_tail(SweepArgsT<V> a) {
     a.relres_true[jj] = a.bnorm[jj] > 0.0 ? sqrt(tot[0]) / a.bnorm[jj] : 0.0;
 }
 
+// ---------------------------------------------------------------- batched TFQMR
+//
+// The TFQMR of the single solve (Freund 1993; Saad 2003, Algorithm 7.8, two
+// half-steps and two products with A_j per iteration) for every frequency at
+// once, on the same row walk, reductions and freezing as the batched
+// BiCGStab above.  The sweep's vectors take the TFQMR roles r0 = rh, w = r,
+// u = p, un = s, v = v, Au = t, A un = q1, d = q2; eta lives in omg.  When a
+// half-step's quasi-residual bound tau sqrt(m + 2) falls below tol ||b_j||,
+// the frequency's true residual ||b_j - A_j x_j|| is computed after the odd
+// half-step (only the 32-frequency groups with such a frequency make that
+// product); a frequency whose bound is below tol but whose true residual is
+// not stops with ST_RESTART and the host starts it again from its x.
+
+// After a half-step of frequency j: theta = ||w|| / tau, c = 1 / sqrt(1 + theta^2),
+// tau = tau theta c, eta = c^2 alpha; the bound raises the check flag.
+__device__ void swq_half(const SweepArgs& a, int j, double ww, int m) {
+  const double tau0 = a.tt[j].y;
+  const double theta = sqrt(ww) / tau0;
+  const double c = 1.0 / sqrt(1.0 + theta * theta);
+  const double tau = tau0 * theta * c;
+  const double2 al = a.alpha[j];
+  const double2 eta = make_double2(c * c * al.x, c * c * al.y);
+  if (!isfinite(theta) || !isfinite(tau) || !cfinite(eta)) {
+    a.status[j] = HELM_ERR_NONFINITE;
+    return;
+  }
+  a.tt[j] = make_double2(theta, tau);
+  a.omg[j] = eta;
+  const double bt = a.st->tol * a.bnorm[j];
+  if (tau * tau * static_cast<double>(m + 2) <= bt * bt) a.chk[j] = 1;
+  a.relres[j] = tau * sqrt(static_cast<double>(m + 2)) / a.bnorm[j];
+}
+
+// gamma = (theta^2 / alpha) eta for the next d update
+__device__ __forceinline__ void swq_gamma(const SweepArgs& a, int j) {
+  const double th = a.tt[j].x;
+  a.gam[j] = cmul(cdiv(make_double2(th * th, 0.0), a.alpha[j]), a.omg[j]);
+}
+
+// init A: r0 = b - A_j x (or b, x = 0); w = u = r0; d = 0; ||b||, ||r0||, rho = (r0, r0)
+__global__ void __launch_bounds__(512) k_swq_init_a(SweepArgs a) {
+  extern __shared__ double sh[];
+  const int use_x0 = a.st->use_x0;
+  SWEEP_ELEMENTWISE_BEGIN
+  double part[4] = {0.0, 0.0, 0.0, 0.0};
+  auto body = [&](int32_t i, int jj, double2 ax) {
+    const size_t idx = static_cast<size_t>(i) * a.Fp + jj;
+    const double2 bi = a.b[a.b_ld ? static_cast<size_t>(i) * a.b_ld + jj : static_cast<size_t>(i)];
+    const double2 ri = csub(bi, ax);
+    a.rh[idx] = ri;
+    a.r[idx] = ri;
+    a.p[idx] = ri;
+    a.q2[idx] = make_double2(0.0, 0.0);
+    part[0] = sw_nrm(part[0], bi);
+    part[1] = sw_nrm(part[1], ri);
+    const double2 d = sw_dot(make_double2(part[2], part[3]), ri, ri);
+    part[2] = d.x;
+    part[3] = d.y;
+  };
+  if (use_x0) {
+    sweep_spmv(a, a.x, body);
+  } else if (run) {
+    for (int64_t u = gw; u < static_cast<int64_t>(a.A.n) * a.G; u += nwarps) {
+      const int32_t i = static_cast<int32_t>(u / a.G);
+      a.x[static_cast<size_t>(i) * a.Fp + j] = make_double2(0.0, 0.0);
+      body(i, j, make_double2(0.0, 0.0));
+    }
+  }
+  double tot[4];
+  if (!sweep_grid_sum<4>(a, part, sh, a.tickets + TK_INIT, tot)) return;
+  for (int jj = threadIdx.x; jj < a.F && jj == (int)threadIdx.x; jj += blockDim.x) {
+    if (a.status[jj] != ST_RUNNING) continue;  // frozen by a restart of other frequencies
+    const double bn = sqrt(tot[0]);
+    a.bnorm[jj] = bn;
+    a.chk[jj] = 0;
+    a.start[jj] = a.iters[jj];
+    int status = ST_RUNNING;
+    if (!isfinite(bn)) {
+      status = HELM_ERR_NONFINITE;
+    } else if (bn == 0.0) {
+      status = HELM_OK;
+    } else {
+      const double rn = sqrt(tot[1]);
+      a.relres[jj] = rn / bn;
+      if (!isfinite(rn)) status = HELM_ERR_NONFINITE;
+      else if (rn <= a.st->tol * bn) status = HELM_OK;
+      else if (a.st->maxit <= 0) status = HELM_ERR_NOT_CONVERGED;
+      a.rho[jj] = make_double2(tot[2], tot[3]);
+      a.tt[jj] = make_double2(0.0, rn);  // theta = 0, tau = ||r0||
+      a.omg[jj] = make_double2(0.0, 0.0);
+      a.gam[jj] = make_double2(0.0, 0.0);
+    }
+    a.status[jj] = status;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int g2 = 0; g2 < a.G; ++g2) a.gcheck[g2] = 0;
+    *a.anychk = 0;
+    sweep_refresh_groups(a);
+  }
+}
+
+// init B: v = A_j u, Au = v, sigma = (r0, v) -> alpha
+__global__ void __launch_bounds__(512) k_swq_init_b(SweepArgs a) {
+  extern __shared__ double sh[];
+  if (a.st->status != ST_RUNNING) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) sweep_set_cond(a, false);
+    return;
+  }
+  double part[2] = {0.0, 0.0};
+  auto body = [&](int32_t i, int j, double2 ax) {
+    const size_t idx = static_cast<size_t>(i) * a.Fp + j;
+    a.v[idx] = ax;
+    a.t[idx] = ax;
+    const double2 d = sw_dot(make_double2(part[0], part[1]), a.rh[idx], ax);
+    part[0] = d.x;
+    part[1] = d.y;
+  };
+  sweep_spmv(a, a.p, body);
+  double tot[2];
+  if (!sweep_grid_sum<2>(a, part, sh, a.tickets + TK_V, tot)) return;
+  for (int j = threadIdx.x; j < a.F && j == (int)threadIdx.x; j += blockDim.x) {
+    if (a.status[j] != ST_RUNNING) continue;
+    const double2 sigma = make_double2(tot[0], tot[1]), rho = a.rho[j];
+    if (!cfinite(sigma) || !cfinite(rho)) a.status[j] = HELM_ERR_NONFINITE;
+    else if (czero(sigma) || czero(rho)) { a.status[j] = HELM_ERR_BREAKDOWN; a.iters[j] += 1; }
+    else {
+      const double2 al = cdiv(rho, sigma);
+      if (!cfinite(al)) a.status[j] = HELM_ERR_NONFINITE;
+      else a.alpha[j] = al;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) sweep_refresh_groups(a);
+}
+
+// T1, even half-step: un = u - alpha v, w -= alpha Au, d = u + gamma d, ||w||^2
+__global__ void __launch_bounds__(512) k_swq_even(SweepArgs a) {
+  extern __shared__ double sh[];
+  if (a.st->status != ST_RUNNING) return;
+  SWEEP_ELEMENTWISE_BEGIN
+  double part[1] = {0.0};
+  if (run) {
+    const double2 al = a.alpha[j], ga = a.gam[j];
+    for (int64_t u = gw; u < static_cast<int64_t>(a.A.n) * a.G; u += nwarps) {
+      const size_t idx = static_cast<size_t>(u / a.G) * a.Fp + j;
+      const double2 ui = a.p[idx];
+      a.s[idx] = cfms(al, a.v[idx], ui);
+      const double2 wi = cfms(al, a.t[idx], a.r[idx]);
+      a.r[idx] = wi;
+      a.q2[idx] = cfma(ga, a.q2[idx], ui);
+      part[0] = sw_nrm(part[0], wi);
+    }
+  }
+  double tot[1];
+  if (!sweep_grid_sum<1>(a, part, sh, a.tickets + TK_S, tot)) return;
+  for (int jj = threadIdx.x; jj < a.F && jj == (int)threadIdx.x; jj += blockDim.x) {
+    if (a.status[jj] != ST_RUNNING) continue;
+    a.iters[jj] += 1;
+    swq_half(a, jj, tot[0], 2 * (a.iters[jj] - 1 - a.start[jj]));
+    if (a.status[jj] == ST_RUNNING) swq_gamma(a, jj);  // the odd half-step's d update (same alpha)
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) sweep_refresh_groups(a);
+}
+
+// T2: A un; x += eta d (the even half-step's x update)
+__global__ void __launch_bounds__(512) k_swq_spmv_un(SweepArgs a) {
+  if (a.st->status != ST_RUNNING) return;
+  const int64_t gw = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int jl = static_cast<int>(gw % a.G) * 32 + (threadIdx.x & 31);
+  const double2 eta = a.omg[jl];
+  auto body = [&](int32_t i, int j, double2 ax) {
+    const size_t idx = static_cast<size_t>(i) * a.Fp + j;
+    a.q1[idx] = ax;
+    a.x[idx] = cfma(eta, a.q2[idx], a.x[idx]);
+  };
+  sweep_spmv(a, a.s, body);
+}
+
+// T3, odd half-step: w -= alpha A un, d = un + gamma d, ||w||^2, (r0, w) -> rho, beta
+__global__ void __launch_bounds__(512) k_swq_odd(SweepArgs a) {
+  extern __shared__ double sh[];
+  if (a.st->status != ST_RUNNING) return;
+  SWEEP_ELEMENTWISE_BEGIN
+  double part[3] = {0.0, 0.0, 0.0};
+  if (run) {
+    const double2 al = a.alpha[j], ga = a.gam[j];
+    for (int64_t u = gw; u < static_cast<int64_t>(a.A.n) * a.G; u += nwarps) {
+      const size_t idx = static_cast<size_t>(u / a.G) * a.Fp + j;
+      const double2 wi = cfms(al, a.q1[idx], a.r[idx]);
+      a.r[idx] = wi;
+      a.q2[idx] = cfma(ga, a.q2[idx], a.s[idx]);
+      part[0] = sw_nrm(part[0], wi);
+      const double2 d = sw_dot(make_double2(part[1], part[2]), a.rh[idx], wi);
+      part[1] = d.x;
+      part[2] = d.y;
+    }
+  }
+  double tot[3];
+  if (!sweep_grid_sum<3>(a, part, sh, a.tickets + TK_T, tot)) return;
+  for (int jj = threadIdx.x; jj < a.F && jj == (int)threadIdx.x; jj += blockDim.x) {
+    if (a.status[jj] != ST_RUNNING) continue;
+    swq_half(a, jj, tot[0], 2 * (a.iters[jj] - 1 - a.start[jj]) + 1);
+    if (a.status[jj] != ST_RUNNING) continue;
+    const double2 rho_new = make_double2(tot[1], tot[2]);
+    if (!cfinite(rho_new)) a.status[jj] = HELM_ERR_NONFINITE;
+    else if (czero(a.rho[jj])) a.status[jj] = HELM_ERR_BREAKDOWN;
+    else {
+      a.beta[jj] = cdiv(rho_new, a.rho[jj]);
+      a.rho[jj] = rho_new;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int any = 0;
+    for (int g2 = 0; g2 < a.G; ++g2) {
+      int on = 0;
+      for (int l = 0; l < 32; ++l) on |= a.status[g2 * 32 + l] == ST_RUNNING && a.chk[g2 * 32 + l] != 0;
+      a.gcheck[g2] = on;
+      any |= on;
+    }
+    *a.anychk = any;
+    sweep_refresh_groups(a);
+  }
+}
+
+// T4: u = w + beta un; x += eta d
+__global__ void __launch_bounds__(512) k_swq_u(SweepArgs a) {
+  if (a.st->status != ST_RUNNING) return;
+  SWEEP_ELEMENTWISE_BEGIN
+  if (!run) return;
+  const double2 be = a.beta[j], eta = a.omg[j];
+  for (int64_t u = gw; u < static_cast<int64_t>(a.A.n) * a.G; u += nwarps) {
+    const size_t idx = static_cast<size_t>(u / a.G) * a.Fp + j;
+    a.p[idx] = cfma(be, a.s[idx], a.r[idx]);
+    a.x[idx] = cfma(eta, a.q2[idx], a.x[idx]);
+  }
+}
+
+// T5: Au = A_j u; v = Au + beta (A un + beta v); sigma = (r0, v) -> alpha, gamma
+__global__ void __launch_bounds__(512) k_swq_spmv_u(SweepArgs a) {
+  extern __shared__ double sh[];
+  if (a.st->status != ST_RUNNING) return;
+  const int64_t gw = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int jl = static_cast<int>(gw % a.G) * 32 + (threadIdx.x & 31);
+  const double2 be = a.beta[jl];
+  double part[2] = {0.0, 0.0};
+  auto body = [&](int32_t i, int j, double2 ax) {
+    const size_t idx = static_cast<size_t>(i) * a.Fp + j;
+    a.t[idx] = ax;
+    const double2 vn = cfma(be, cfma(be, a.v[idx], a.q1[idx]), ax);
+    a.v[idx] = vn;
+    const double2 d = sw_dot(make_double2(part[0], part[1]), a.rh[idx], vn);
+    part[0] = d.x;
+    part[1] = d.y;
+  };
+  sweep_spmv(a, a.p, body);
+  double tot[2];
+  if (!sweep_grid_sum<2>(a, part, sh, a.tickets + TK_AUX1, tot)) return;
+  for (int j = threadIdx.x; j < a.F && j == (int)threadIdx.x; j += blockDim.x) {
+    if (a.status[j] != ST_RUNNING) continue;
+    const double2 sigma = make_double2(tot[0], tot[1]);
+    if (!cfinite(sigma)) a.status[j] = HELM_ERR_NONFINITE;
+    else if (czero(sigma) || czero(a.rho[j])) a.status[j] = HELM_ERR_BREAKDOWN;
+    else {
+      const double2 al = cdiv(a.rho[j], sigma);
+      if (!cfinite(al)) a.status[j] = HELM_ERR_NONFINITE;
+      else {
+        a.alpha[j] = al;
+        swq_gamma(a, j);
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) sweep_refresh_groups(a);
+}
+
+// T6: the true residual of the frequencies whose bound fell below tol (only
+// their groups make the product); iteration cap and deadline for every
+// running frequency; the loop condition.
+__global__ void __launch_bounds__(512) k_swq_check(SweepArgs a) {
+  extern __shared__ double sh[];
+  if (a.st->status != ST_RUNNING) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) sweep_set_cond(a, false);
+    return;
+  }
+  const bool late = a.st->deadline_ns != 0ull && (globaltimer_ns() - a.st->t0) > a.st->deadline_ns;
+  if (*a.anychk == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      for (int j = 0; j < a.F; ++j) {
+        if (a.status[j] != ST_RUNNING) continue;
+        if (a.iters[j] >= a.st->maxit) a.status[j] = HELM_ERR_NOT_CONVERGED;
+        else if (late) a.status[j] = HELM_ERR_TIMEOUT;
+      }
+      sweep_refresh_groups(a);
+    }
+    return;
+  }
+  SweepArgs ac = a;
+  ac.gactive = a.gcheck;  // only the groups with a frequency to check
+  double part[1] = {0.0};
+  auto body = [&](int32_t i, int j, double2 ax) {
+    if (a.chk[j] == 0) return;
+    const double2 bi = a.b[a.b_ld ? static_cast<size_t>(i) * a.b_ld + j : static_cast<size_t>(i)];
+    part[0] = sw_nrm(part[0], csub(bi, ax));
+  };
+  sweep_spmv(ac, a.x, body);
+  double tot[1];
+  if (!sweep_grid_sum<1>(a, part, sh, a.tickets + TK_AUX2, tot)) return;
+  for (int j = threadIdx.x; j < a.F && j == (int)threadIdx.x; j += blockDim.x) {
+    if (a.status[j] != ST_RUNNING) continue;
+    int status = ST_RUNNING;
+    if (a.chk[j] != 0) {
+      const double rt = sqrt(tot[0]) / a.bnorm[j];
+      a.chk[j] = 0;
+      if (!isfinite(rt)) status = HELM_ERR_NONFINITE;
+      else if (rt <= a.st->tol) status = HELM_OK;
+      else if (a.iters[j] >= a.st->maxit) status = HELM_ERR_NOT_CONVERGED;
+      else if (late) status = HELM_ERR_TIMEOUT;
+      // the bound is below tol but the true residual is not: the recurrence
+      // has drifted from b - A x; the host starts this frequency again
+      else status = ST_RESTART;
+    } else if (a.iters[j] >= a.st->maxit) {
+      status = HELM_ERR_NOT_CONVERGED;
+    } else if (late) {
+      status = HELM_ERR_TIMEOUT;
+    }
+    a.status[j] = status;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int g2 = 0; g2 < a.G; ++g2) a.gcheck[g2] = 0;
+    *a.anychk = 0;
+    sweep_refresh_groups(a);
+  }
+}
+
 // X_user[i * ldx + j] <-> x[i * Fp + j]
 __global__ void k_sw_copy(int32_t n, int32_t F, int32_t Fp, const double2* __restrict__ src, int32_t lds,
                           double2* __restrict__ dst, int32_t ldd) {
@@ -795,6 +1141,13 @@ struct helm_sweep_s {
   float* kmb32 = nullptr;         // FP32 copies of K, M, B (3 nnz)
   double* oscal = nullptr;
   int32_t* oact = nullptr;
+  // batched TFQMR: 2 vectors [n][Fcapq] (A un, d), gamma and (theta, tau)
+  // [2 Fcapq], check flags and start iterations [2 Fcapq], group check flags
+  // [Fcapq / 32] and one sweep-wide flag
+  double2* vecq = nullptr;
+  double2* tqscal = nullptr;
+  int32_t* tqint = nullptr;
+  int32_t Fcapq = 0;
   int warps_per_block = 8;        // autotuned
   bool tuned = false;
   std::mutex mu;
@@ -803,7 +1156,7 @@ struct helm_sweep_s {
     const void* b = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
-  } graph, graph32;
+  } graph, graph32, graphq;
 };
 
 namespace {
@@ -811,7 +1164,7 @@ namespace {
 // Graphs capture buffer addresses: both are dropped whenever a buffer they
 // use is replaced.
 void drop_sweep_graphs(helm_sweep S) {
-  for (helm_sweep_s::G* g : {&S->graph, &S->graph32}) {
+  for (helm_sweep_s::G* g : {&S->graph, &S->graph32, &S->graphq}) {
     if (g->exec) cudaGraphExecDestroy(g->exec);
     if (g->graph) cudaGraphDestroy(g->graph);
     *g = helm_sweep_s::G();
@@ -956,6 +1309,41 @@ helm_status sweep_alloc_mixed(helm_sweep S, int32_t Fp, cudaStream_t s) {
   return HELM_OK;
 }
 
+// Buffers of the batched TFQMR (allocated at its first use).
+helm_status sweep_alloc_tfqmr(helm_sweep S, int32_t Fp) {
+  if (S->Fcapq >= Fp) return HELM_OK;
+  cudaFree(S->vecq);
+  cudaFree(S->tqscal);
+  cudaFree(S->tqint);
+  S->vecq = nullptr;
+  S->tqscal = nullptr;
+  S->tqint = nullptr;
+  S->Fcapq = 0;
+  const size_t nf = static_cast<size_t>(std::max<int32_t>(S->n, 1)) * Fp;
+  HELM_CUDA_TRY(cudaMalloc(&S->vecq, 2 * nf * sizeof(double2)));
+  HELM_CUDA_TRY(cudaMalloc(&S->tqscal, 2 * static_cast<size_t>(Fp) * sizeof(double2)));
+  HELM_CUDA_TRY(cudaMalloc(&S->tqint, (2 * static_cast<size_t>(Fp) + Fp / 32 + 1) * sizeof(int32_t)));
+  S->Fcapq = Fp;
+  if (S->graphq.exec) {
+    cudaGraphExecDestroy(S->graphq.exec);
+    cudaGraphDestroy(S->graphq.graph);
+  }
+  S->graphq = helm_sweep_s::G();
+  return HELM_OK;
+}
+
+void set_tfqmr_args(helm_sweep S, SweepArgs& a) {
+  const size_t nf = static_cast<size_t>(std::max<int32_t>(S->n, 1)) * a.Fp;
+  a.q1 = S->vecq;
+  a.q2 = S->vecq + nf;
+  a.gam = S->tqscal;
+  a.tt = S->tqscal + a.Fp;
+  a.chk = S->tqint;
+  a.start = S->tqint + a.Fp;
+  a.gcheck = S->tqint + 2 * static_cast<size_t>(a.Fp);
+  a.anychk = S->tqint + 2 * static_cast<size_t>(a.Fp) + a.Fp / 32;
+}
+
 struct SweepShape {
   int threads, grid;
   size_t smem;  // per-frequency reduction scratch
@@ -978,7 +1366,11 @@ SweepShape sweep_shape(helm_sweep S, int G) {
         reinterpret_cast<const void*>(&k_sw_tail<double2>), reinterpret_cast<const void*>(&k_sw_init<float2>),
         reinterpret_cast<const void*>(&k_sw_p<float2>), reinterpret_cast<const void*>(&k_sw_v<float2>),
         reinterpret_cast<const void*>(&k_sw_s<float2>), reinterpret_cast<const void*>(&k_sw_t<float2>),
-        reinterpret_cast<const void*>(&k_sw_xr<float2>)}) {
+        reinterpret_cast<const void*>(&k_sw_xr<float2>), reinterpret_cast<const void*>(&k_swq_init_a),
+        reinterpret_cast<const void*>(&k_swq_init_b), reinterpret_cast<const void*>(&k_swq_even),
+        reinterpret_cast<const void*>(&k_swq_spmv_un), reinterpret_cast<const void*>(&k_swq_odd),
+        reinterpret_cast<const void*>(&k_swq_u), reinterpret_cast<const void*>(&k_swq_spmv_u),
+        reinterpret_cast<const void*>(&k_swq_check)}) {
     int b = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, sh.threads, sh.smem) == cudaSuccess && b >= 1)
       per_sm = std::min(per_sm, b);
@@ -1009,9 +1401,11 @@ void enqueue_sweep_body(const SweepArgsT<V>& a, const SweepShape& sh, cudaStream
   k_sw_xr<V><<<sh.grid, sh.threads, sh.smem, s>>>(a);
 }
 
-template <class V>
-helm_status build_sweep_graph(const SweepArgsT<V>& base, const SweepShape& sh, cudaGraph_t* gout,
-                              cudaGraphExec_t* eout) {
+// init -> conditional WHILE (body: one iteration) -> tail, as one graph;
+// init, body and tail enqueue their kernels with the given arguments.
+template <class V, class Init, class Body, class Tail>
+helm_status build_sweep_graph_with(const SweepArgsT<V>& base, Init init, Body body_fn, Tail tail,
+                                   cudaGraph_t* gout, cudaGraphExec_t* eout) {
   cudaStream_t cs = nullptr;
   HELM_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   cudaGraph_t graph = nullptr;
@@ -1026,7 +1420,7 @@ helm_status build_sweep_graph(const SweepArgsT<V>& base, const SweepShape& sh, c
     a.has_cond = 1;
     if (cudaStreamBeginCaptureToGraph(cs, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
       break;
-    k_sw_init<V><<<sh.grid, sh.threads, sh.smem, cs>>>(a);
+    init(a, cs);
     cudaStreamCaptureStatus cst;
     const cudaGraphNode_t* deps = nullptr;
     size_t ndeps = 0;
@@ -1044,11 +1438,11 @@ helm_status build_sweep_graph(const SweepArgsT<V>& base, const SweepShape& sh, c
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
       break;
-    enqueue_sweep_body(a, sh, cs);
+    body_fn(a, cs);
     if (cudaStreamEndCapture(cs, &tmp) != cudaSuccess) break;
     if (cudaStreamBeginCaptureToGraph(cs, graph, &wnode, nullptr, 1, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
       break;
-    k_sw_tail<V><<<sh.grid, sh.threads, sh.smem, cs>>>(a);
+    tail(a, cs);
     if (cudaStreamEndCapture(cs, &tmp) != cudaSuccess) break;
     if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) break;
     result = HELM_OK;
@@ -1063,6 +1457,38 @@ helm_status build_sweep_graph(const SweepArgsT<V>& base, const SweepShape& sh, c
   *gout = graph;
   *eout = exec;
   return HELM_OK;
+}
+
+template <class V>
+helm_status build_sweep_graph(const SweepArgsT<V>& base, const SweepShape& sh, cudaGraph_t* gout,
+                              cudaGraphExec_t* eout) {
+  return build_sweep_graph_with(
+      base, [&](const SweepArgsT<V>& a, cudaStream_t cs) { k_sw_init<V><<<sh.grid, sh.threads, sh.smem, cs>>>(a); },
+      [&](const SweepArgsT<V>& a, cudaStream_t cs) { enqueue_sweep_body(a, sh, cs); },
+      [&](const SweepArgsT<V>& a, cudaStream_t cs) { k_sw_tail<V><<<sh.grid, sh.threads, sh.smem, cs>>>(a); }, gout,
+      eout);
+}
+
+// The batched TFQMR's launches: init (two kernels), one iteration (six).
+void swq_init(const SweepArgs& a, const SweepShape& sh, cudaStream_t s) {
+  k_swq_init_a<<<sh.grid, sh.threads, sh.smem, s>>>(a);
+  k_swq_init_b<<<sh.grid, sh.threads, sh.smem, s>>>(a);
+}
+void swq_body(const SweepArgs& a, const SweepShape& sh, cudaStream_t s) {
+  k_swq_even<<<sh.grid, sh.threads, sh.smem, s>>>(a);
+  k_swq_spmv_un<<<sh.grid, sh.threads, 0, s>>>(a);
+  k_swq_odd<<<sh.grid, sh.threads, sh.smem, s>>>(a);
+  k_swq_u<<<sh.grid, sh.threads, 0, s>>>(a);
+  k_swq_spmv_u<<<sh.grid, sh.threads, sh.smem, s>>>(a);
+  k_swq_check<<<sh.grid, sh.threads, sh.smem, s>>>(a);
+}
+
+helm_status build_tfqmr_graph(const SweepArgs& base, const SweepShape& sh, cudaGraph_t* gout, cudaGraphExec_t* eout) {
+  return build_sweep_graph_with(
+      base, [&](const SweepArgs& a, cudaStream_t cs) { swq_init(a, sh, cs); },
+      [&](const SweepArgs& a, cudaStream_t cs) { swq_body(a, sh, cs); },
+      [&](const SweepArgs& a, cudaStream_t cs) { k_sw_tail<double2><<<sh.grid, sh.threads, sh.smem, cs>>>(a); },
+      gout, eout);
 }
 
 // Time the batched SpMV with 4, 8 and 16 warps per block; keep the fastest.
@@ -1317,8 +1743,13 @@ helm_status helm_sweep_destroy(helm_sweep S) {
   cudaFree(S->kmb32);
   cudaFree(S->oscal);
   cudaFree(S->oact);
+  cudaFree(S->vecq);
+  cudaFree(S->tqscal);
+  cudaFree(S->tqint);
   if (S->graph32.exec) cudaGraphExecDestroy(S->graph32.exec);
   if (S->graph32.graph) cudaGraphDestroy(S->graph32.graph);
+  if (S->graphq.exec) cudaGraphExecDestroy(S->graphq.exec);
+  if (S->graphq.graph) cudaGraphDestroy(S->graphq.graph);
   (void)cudaGetLastError();
   if (prev >= 0) cudaSetDevice(prev);
   delete S;
@@ -1333,7 +1764,8 @@ helm_status helm_sweep_solve(helm_sweep S, int32_t nfreq, const double* h_omega,
   if (!S || nfreq < 1 || nfreq > kMaxF || !h_omega || (b_ld != 0 && b_ld < nfreq) || ldx < nfreq) return HELM_ERR_INVALID;
   if (S->n > 0 && (!d_b || !d_X)) return HELM_ERR_INVALID;
   if (!aligned(d_b, 16) || !aligned(d_X, 16) || !(opts.tol >= 0.0) || opts.maxit < 0) return HELM_ERR_INVALID;
-  if ((opts.precision != HELM_PREC_FP64 && opts.precision != HELM_PREC_MIXED) || opts.method != HELM_BICGSTAB)
+  if (opts.precision != HELM_PREC_FP64 && opts.precision != HELM_PREC_MIXED) return HELM_ERR_INVALID;
+  if (opts.method != HELM_BICGSTAB && !(opts.method == HELM_TFQMR && opts.precision == HELM_PREC_FP64))
     return HELM_ERR_INVALID;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   std::lock_guard<std::mutex> lk(S->mu);
@@ -1375,18 +1807,27 @@ helm_status helm_sweep_solve(helm_sweep S, int32_t nfreq, const double* h_omega,
     k_sw_copy<<<vec_grid_for(static_cast<int64_t>(S->n) * nfreq), 256, 0, s>>>(
         S->n, nfreq, Fp, static_cast<const double2*>(d_X), ldx, a.x, Fp);
   }
-  // graph for (F, b, stride)
-  if (!(S->graph.exec && S->graph.F == nfreq && S->graph.b == bsrc && S->graph.b_ld == bld)) {
-    if (S->graph.exec) {
-      cudaGraphExecDestroy(S->graph.exec);
-      cudaGraphDestroy(S->graph.graph);
+  const bool tq = opts.method == HELM_TFQMR;
+  if (tq) {
+    st = sweep_alloc_tfqmr(S, Fp);
+    if (st != HELM_OK) return st;
+    set_tfqmr_args(S, a);
+  }
+  // graph for (method, F, b, stride)
+  helm_sweep_s::G& gr = tq ? S->graphq : S->graph;
+  if (!(gr.exec && gr.F == nfreq && gr.b == bsrc && gr.b_ld == bld)) {
+    if (gr.exec) {
+      cudaGraphExecDestroy(gr.exec);
+      cudaGraphDestroy(gr.graph);
     }
-    S->graph = helm_sweep_s::G();
+    gr = helm_sweep_s::G();
     if (!bcopy) {
-      if (build_sweep_graph(a, sh, &S->graph.graph, &S->graph.exec) == HELM_OK) {
-        S->graph.F = nfreq;
-        S->graph.b = bsrc;
-        S->graph.b_ld = bld;
+      const helm_status gs = tq ? build_tfqmr_graph(a, sh, &gr.graph, &gr.exec)
+                                : build_sweep_graph(a, sh, &gr.graph, &gr.exec);
+      if (gs == HELM_OK) {
+        gr.F = nfreq;
+        gr.b = bsrc;
+        gr.b_ld = bld;
       }
     }
   }
@@ -1397,13 +1838,17 @@ helm_status helm_sweep_solve(helm_sweep S, int32_t nfreq, const double* h_omega,
   for (int32_t fresh = 1, use_x0 = opts.use_x0 ? 1 : 0;; fresh = 0, use_x0 = 1) {
     k_sw_configure<double2><<<1, 256, 0, s>>>(a, opts.tol, opts.maxit, use_x0, opts.deadline_s, fresh, d_restart);
     HELM_CUDA_TRY(cudaGetLastError());
-    if (S->graph.exec && !bcopy) {
-      HELM_CUDA_TRY(cudaGraphLaunch(S->graph.exec, s));
+    if (gr.exec && !bcopy) {
+      HELM_CUDA_TRY(cudaGraphLaunch(gr.exec, s));
     } else {
       SolverState hs;
-      k_sw_init<double2><<<sh.grid, sh.threads, sh.smem, s>>>(a);
+      if (tq) swq_init(a, sh, s);
+      else k_sw_init<double2><<<sh.grid, sh.threads, sh.smem, s>>>(a);
       for (;;) {
-        for (int k = 0; k < 8; ++k) enqueue_sweep_body(a, sh, s);
+        for (int k = 0; k < 8; ++k) {
+          if (tq) swq_body(a, sh, s);
+          else enqueue_sweep_body(a, sh, s);
+        }
         HELM_CUDA_TRY(cudaGetLastError());
         HELM_CUDA_TRY(cudaMemcpyAsync(&hs, a.st, sizeof(hs), cudaMemcpyDeviceToHost, s));
         HELM_CUDA_TRY(cudaStreamSynchronize(s));
@@ -1421,7 +1866,10 @@ helm_status helm_sweep_solve(helm_sweep S, int32_t nfreq, const double* h_omega,
     // restarts from its x (iterations permitting), as the single solve does
     bool any = false;
     for (int j = 0; j < Fp; ++j) {
-      restart[j] = j < nfreq && status[j] == HELM_OK && relres_true[j] > opts.tol && iters[j] < opts.maxit;
+      // (TFQMR: also a frequency whose bound met tol while its true residual
+      // did not, reported as ST_RESTART)
+      restart[j] = j < nfreq && ((status[j] == HELM_OK && relres_true[j] > opts.tol && iters[j] < opts.maxit) ||
+                                 status[j] == ST_RESTART);
       if (restart[j]) {
         any = true;
         restarts[j] += 1;
@@ -1437,7 +1885,7 @@ helm_status helm_sweep_solve(helm_sweep S, int32_t nfreq, const double* h_omega,
   HELM_CUDA_TRY(cudaStreamSynchronize(s));
   helm_status worst = HELM_OK;
   for (int j = 0; j < nfreq; ++j) {
-    helm_status sj = status[j] == ST_RUNNING ? HELM_ERR_CUDA : static_cast<helm_status>(status[j]);
+    helm_status sj = status[j] < 0 ? HELM_ERR_CUDA : static_cast<helm_status>(status[j]);
     if (sj == HELM_OK && !(relres_true[j] <= opts.tol)) sj = HELM_ERR_NOT_CONVERGED;
     if (h_infos) {
       h_infos[j].iters = iters[j];
