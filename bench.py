@@ -419,6 +419,8 @@ def extension_summary(dev, args):
                                                 inner_tol=0.01))
     S.solve(w, b, tol=cfg.tol, maxit=50000, method=helm.HELM_TFQMR)
     (Xq, infq), t_tfqmr = timed(lambda: S.solve(w, b, tol=cfg.tol, maxit=50000, method=helm.HELM_TFQMR))
+    S.solve(w, b, tol=cfg.tol, maxit=50000, method=helm.HELM_BICGSTABL, ell=4)
+    (Xl, infl), t_bl = timed(lambda: S.solve(w, b, tol=cfg.tol, maxit=50000, method=helm.HELM_BICGSTABL, ell=4))
     S.close()
     t_single, it_single, ok_single = 0.0, 0, True
     for F in cfg.freqs:
@@ -449,7 +451,13 @@ def extension_summary(dev, args):
                                 "converged": all(i["status"] == "ok" for i in infq),
                                 "worst_relres_true": max(i["relres_true"] for i in infq),
                                 "iters_total": sum(i["iters"] for i in infq),
-                                "restarts": sum(i["restarts"] for i in infq)}}
+                                "restarts": sum(i["restarts"] for i in infq)},
+                      "bicgstab4": {"s": round(t_bl, 3), "freq_solves_per_s": round(len(w) / t_bl, 3),
+                                    "vs_bicgstab_batched": round(t_sweep / t_bl, 3),
+                                    "converged": all(i["status"] == "ok" for i in infl),
+                                    "worst_relres_true": max(i["relres_true"] for i in infl),
+                                    "cycles_total": sum(i["iters"] for i in infl),
+                                    "restarts": sum(i["restarts"] for i in infl)}}
 
     # config 3
     cfg = helmgen.CONFIGS["cavity200"]

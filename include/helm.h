@@ -346,7 +346,8 @@ helm_status helm_conj_scale(int64_t n, const double* alpha, const void* d_x, voi
 
 /*
  * Frequency sweep (the extension of Section 4's solvers to many wavenumbers
- * k_j = w_j / c on one mesh): BiCGStab or TFQMR for all frequencies at once on
+ * k_j = w_j / c on one mesh): BiCGStab, TFQMR or BiCGStab(l) for all
+ * frequencies at once on
  *   A_j = K - w_j^2 M + i w_j B,
  * K, M, B real on one CSR pattern (stiffness, mass scaled by 1/c^2, impedance
  * face scaled by 1/c), A_j formed on the fly inside the SpMV.  Converged
@@ -373,11 +374,13 @@ helm_status helm_sweep_destroy(helm_sweep S);
  *   d_X     : complex128 solutions, x_j[i] = d_X[i * ldx + j], ldx >= nfreq
  *             (read first when o->use_x0).
  *   o       : tol, maxit, use_x0, deadline_s, method, precision, inner_tol
- *             used.  method HELM_BICGSTAB (FP64 or mixed precision) or
+ *             used.  method HELM_BICGSTAB (FP64 or mixed precision),
  *             HELM_TFQMR (FP64 only; the recurrences of helm_bicgstab_solve's
  *             TFQMR per frequency, iterations = two products with A_j; the
  *             quasi-residual bound triggers a true-residual check after each
- *             iteration); other methods return HELM_ERR_INVALID.
+ *             iteration) or HELM_BICGSTABL (FP64 only, o->ell = 1..8, else
+ *             HELM_ERR_INVALID; helm_bicgstab_solve's BiCGStab(l) per
+ *             frequency, iterations = cycles of 2 l products with A_j).
  *             precision HELM_PREC_MIXED: FP64 refinement per
  *             frequency around complex64 inner sweeps -- each step forms
  *             r_j = b_j - A_j x_j in FP64, solves A_j d_j = r_j / sigma_j

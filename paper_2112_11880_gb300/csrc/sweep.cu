@@ -1,7 +1,8 @@
-// Batched frequency sweep: BiCGStab or TFQMR (Section 4's solvers) for F
-// frequencies on one sparsity pattern, A_j = K - w_j^2 M + i w_j B formed on
-// the fly (the Helmholtz operator of Section 1 at wavenumbers k = w_j / c,
-// with the impedance term); BiCGStab also with complex64 inner solves.
+// Batched frequency sweep: BiCGStab, TFQMR or BiCGStab(l) (Section 4's
+// solvers) for F frequencies on one sparsity pattern, A_j = K - w_j^2 M +
+// i w_j B formed on the fly (the Helmholtz operator of Section 1 at
+// wavenumbers k = w_j / c, with the impedance term); BiCGStab also with
+// complex64 inner solves.
 //
 // Layout: every Krylov vector is node-major, frequency-minor: V[i * Fp + j],
 // Fp = F rounded up to a multiple of 32.  A warp owns one row and 32
@@ -38,6 +39,8 @@ namespace helm {
 namespace {
 
 constexpr int kMaxF = 128;  // frequencies per sweep (<= threads per block: one thread per frequency)
+constexpr int kSwMaxEll = 8;                                     // batched BiCGStab(l): l <= 8
+constexpr int kSwGram = (kSwMaxEll + 1) * (kSwMaxEll + 2) / 2;  // Gram entries per frequency (45)
 
 struct SweepDev {
   int32_t n;
@@ -76,6 +79,13 @@ struct SweepArgsT {
   V *q1, *q2;
   double2 *gam, *tt;
   int32_t *chk, *gcheck, *anychk, *start;
+  // batched BiCGStab(l) only: r_0..r_l and u_0..u_l (r_0 = r, u_0 = p, the
+  // shadow r~ = rh), rho1 [Fp], the minimal-residual coefficients [Fp][8],
+  // the Gram matrices [Fp][45] and the Gram step's block partials
+  V *rl[kSwMaxEll + 1], *ul[kSwMaxEll + 1];
+  int32_t ell;
+  double2 *rho1, *gcoef, *gram;
+  double* gpart;
   SolverState* st;                      // tol, maxit, deadline, use_x0
   double* partials;                     // [blocks][Fp][K]
   unsigned int* tickets;
@@ -943,6 +953,386 @@ __global__ void __launch_bounds__(512) k_swq_check(SweepArgs a) {
   }
 }
 
+// ---------------------------------------------------------------- batched BiCGStab(l)
+//
+// BiCGStab(l) of the single solve (Sleijpen & Fokkema 1993: per cycle l BiCG
+// steps, 2 l products with A_j, and one minimal-residual step over r_1..r_l)
+// for every frequency at once.  The scalar step before each BiCG step (at
+// j = 0: the cycle count and rho0 = -omega rho0; then beta = alpha rho1 /
+// rho0, rho0 = rho1) runs in the last block of the kernel before it.  The
+// minimal-residual coefficients g of each frequency solve the normal
+// equations of min ||r_0 - sum_k g_k r_k|| (Gram matrix of r_0..r_l in one
+// fused per-frequency reduction, Cholesky in FP64 by the frequency's own
+// thread), as in the single solve.
+
+__device__ __forceinline__ void swl_stop(const SweepArgs& a, int j, double r2) {
+  const double bt = a.st->tol * a.bnorm[j];
+  a.relres[j] = sqrt(r2) / a.bnorm[j];
+  if (!isfinite(r2)) a.status[j] = HELM_ERR_NONFINITE;
+  else if (r2 <= bt * bt) a.status[j] = HELM_OK;
+}
+
+// scalar step before BiCG step j of frequency f (first: j = 0, a new cycle)
+__device__ __forceinline__ void swl_beta(const SweepArgs& a, int f, bool first) {
+  if (first) {
+    a.iters[f] += 1;
+    const double2 om = a.omg[f];
+    a.rho[f] = cmul(make_double2(-om.x, -om.y), a.rho[f]);
+  }
+  const double2 r1 = a.rho1[f];
+  if (!cfinite(r1)) a.status[f] = HELM_ERR_NONFINITE;
+  else if (czero(a.rho[f])) a.status[f] = HELM_ERR_BREAKDOWN;
+  else {
+    a.beta[f] = cmul(a.alpha[f], cdiv(r1, a.rho[f]));
+    a.rho[f] = r1;
+  }
+}
+
+// init: r_0 = b - A_j x (or b, x = 0), r~ = r_0, u_0 = 0; ||b||, ||r_0||,
+// rho1 = (r~, r_0); rho0 = 1, alpha = 0, omega = 1; the first scalar step
+__global__ void __launch_bounds__(512) k_swl_init(SweepArgs a) {
+  extern __shared__ double sh[];
+  const int use_x0 = a.st->use_x0;
+  SWEEP_ELEMENTWISE_BEGIN
+  double part[4] = {0.0, 0.0, 0.0, 0.0};
+  auto body = [&](int32_t i, int jj, double2 ax) {
+    const size_t idx = static_cast<size_t>(i) * a.Fp + jj;
+    const double2 bi = a.b[a.b_ld ? static_cast<size_t>(i) * a.b_ld + jj : static_cast<size_t>(i)];
+    const double2 ri = csub(bi, ax);
+    a.r[idx] = ri;
+    a.rh[idx] = ri;
+    a.p[idx] = make_double2(0.0, 0.0);
+    part[0] = sw_nrm(part[0], bi);
+    part[1] = sw_nrm(part[1], ri);
+    const double2 d = sw_dot(make_double2(part[2], part[3]), ri, ri);
+    part[2] = d.x;
+    part[3] = d.y;
+  };
+  if (use_x0) {
+    sweep_spmv(a, a.x, body);
+  } else if (run) {
+    for (int64_t u = gw; u < static_cast<int64_t>(a.A.n) * a.G; u += nwarps) {
+      const int32_t i = static_cast<int32_t>(u / a.G);
+      a.x[static_cast<size_t>(i) * a.Fp + j] = make_double2(0.0, 0.0);
+      body(i, j, make_double2(0.0, 0.0));
+    }
+  }
+  double tot[4];
+  if (!sweep_grid_sum<4>(a, part, sh, a.tickets + TK_INIT, tot)) return;
+  for (int jj = threadIdx.x; jj < a.F && jj == (int)threadIdx.x; jj += blockDim.x) {
+    if (a.status[jj] != ST_RUNNING) continue;  // frozen by a restart of other frequencies
+    const double bn = sqrt(tot[0]);
+    a.bnorm[jj] = bn;
+    if (!isfinite(bn)) {
+      a.status[jj] = HELM_ERR_NONFINITE;
+    } else if (bn == 0.0) {
+      a.status[jj] = HELM_OK;
+    } else {
+      swl_stop(a, jj, tot[1]);
+      if (a.status[jj] == ST_RUNNING && a.st->maxit <= 0) a.status[jj] = HELM_ERR_NOT_CONVERGED;
+      a.rho[jj] = make_double2(1.0, 0.0);
+      a.alpha[jj] = make_double2(0.0, 0.0);
+      a.omg[jj] = make_double2(1.0, 0.0);
+      a.rho1[jj] = make_double2(tot[2], tot[3]);
+      if (a.status[jj] == ST_RUNNING) swl_beta(a, jj, true);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) sweep_refresh_groups(a);
+}
+
+// B1: u_i = r_i - beta u_i, i <= js
+__global__ void __launch_bounds__(512) k_swl_u(SweepArgs a, int js) {
+  if (a.st->status != ST_RUNNING) return;
+  SWEEP_ELEMENTWISE_BEGIN
+  if (!run) return;
+  const double2 be = a.beta[j];
+  for (int64_t u = gw; u < static_cast<int64_t>(a.A.n) * a.G; u += nwarps) {
+    const size_t idx = static_cast<size_t>(u / a.G) * a.Fp + j;
+    for (int i = 0; i <= js; ++i) a.ul[i][idx] = cfms(be, a.ul[i][idx], a.rl[i][idx]);
+  }
+}
+
+// B2: u_{js+1} = A_j u_js, gamma = (r~, u_{js+1}) -> alpha = rho0 / gamma
+__global__ void __launch_bounds__(512) k_swl_au(SweepArgs a, int js) {
+  extern __shared__ double sh[];
+  if (a.st->status != ST_RUNNING) return;
+  double part[2] = {0.0, 0.0};
+  double2* out = a.ul[js + 1];
+  auto body = [&](int32_t i, int j, double2 ax) {
+    const size_t idx = static_cast<size_t>(i) * a.Fp + j;
+    out[idx] = ax;
+    const double2 d = sw_dot(make_double2(part[0], part[1]), a.rh[idx], ax);
+    part[0] = d.x;
+    part[1] = d.y;
+  };
+  sweep_spmv(a, a.ul[js], body);
+  double tot[2];
+  if (!sweep_grid_sum<2>(a, part, sh, a.tickets + TK_V, tot)) return;
+  for (int j = threadIdx.x; j < a.F && j == (int)threadIdx.x; j += blockDim.x) {
+    if (a.status[j] != ST_RUNNING) continue;
+    const double2 gm = make_double2(tot[0], tot[1]);
+    if (!cfinite(gm)) a.status[j] = HELM_ERR_NONFINITE;
+    else if (czero(gm)) a.status[j] = HELM_ERR_BREAKDOWN;
+    else {
+      const double2 al = cdiv(a.rho[j], gm);
+      if (!cfinite(al)) a.status[j] = HELM_ERR_NONFINITE;
+      else a.alpha[j] = al;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) sweep_refresh_groups(a);
+}
+
+// B3: r_i -= alpha u_{i+1} (i <= js), x += alpha u_0; ||r_0||^2 -> stop test
+__global__ void __launch_bounds__(512) k_swl_r(SweepArgs a, int js) {
+  extern __shared__ double sh[];
+  if (a.st->status != ST_RUNNING) return;
+  SWEEP_ELEMENTWISE_BEGIN
+  double part[1] = {0.0};
+  if (run) {
+    const double2 al = a.alpha[j];
+    for (int64_t u = gw; u < static_cast<int64_t>(a.A.n) * a.G; u += nwarps) {
+      const size_t idx = static_cast<size_t>(u / a.G) * a.Fp + j;
+      for (int i = 0; i <= js; ++i) {
+        const double2 ri = cfms(al, a.ul[i + 1][idx], a.rl[i][idx]);
+        a.rl[i][idx] = ri;
+        if (i == 0) part[0] = sw_nrm(part[0], ri);
+      }
+      a.x[idx] = cfma(al, a.ul[0][idx], a.x[idx]);
+    }
+  }
+  double tot[1];
+  if (!sweep_grid_sum<1>(a, part, sh, a.tickets + TK_S, tot)) return;
+  for (int jj = threadIdx.x; jj < a.F && jj == (int)threadIdx.x; jj += blockDim.x)
+    if (a.status[jj] == ST_RUNNING) swl_stop(a, jj, tot[0]);
+  __syncthreads();
+  if (threadIdx.x == 0) sweep_refresh_groups(a);
+}
+
+// B4: r_{js+1} = A_j r_js, rho1 = (r~, r_{js+1}); the scalar step of BiCG step js + 1
+__global__ void __launch_bounds__(512) k_swl_ar(SweepArgs a, int js) {
+  extern __shared__ double sh[];
+  if (a.st->status != ST_RUNNING) return;
+  double part[2] = {0.0, 0.0};
+  double2* out = a.rl[js + 1];
+  auto body = [&](int32_t i, int j, double2 ax) {
+    const size_t idx = static_cast<size_t>(i) * a.Fp + j;
+    out[idx] = ax;
+    const double2 d = sw_dot(make_double2(part[0], part[1]), a.rh[idx], ax);
+    part[0] = d.x;
+    part[1] = d.y;
+  };
+  sweep_spmv(a, a.rl[js], body);
+  double tot[2];
+  if (!sweep_grid_sum<2>(a, part, sh, a.tickets + TK_T, tot)) return;
+  for (int j = threadIdx.x; j < a.F && j == (int)threadIdx.x; j += blockDim.x) {
+    if (a.status[j] != ST_RUNNING) continue;
+    a.rho1[j] = make_double2(tot[0], tot[1]);
+    if (js + 1 < a.ell) swl_beta(a, j, false);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) sweep_refresh_groups(a);
+}
+
+// M1: per-frequency Gram matrix G_ik = (r_i, r_k), 0 <= i <= k <= L, one fused
+// reduction (per-block partials in warp order, then block order); the
+// frequency's thread solves sum_k G_ik g_k = G_i0 (i = 1..L) by Cholesky in
+// FP64.  Dynamic shared memory: at least 2 doubles per thread.
+template <int L>
+__global__ void __launch_bounds__(512) k_swl_gram(SweepArgs a) {
+  constexpr int NG = (L + 1) * (L + 2) / 2;
+  extern __shared__ double sh[];
+  __shared__ bool s_last;
+  if (a.st->status != ST_RUNNING) return;
+  SWEEP_ELEMENTWISE_BEGIN
+  double acc[2 * NG];
+#pragma unroll
+  for (int e = 0; e < 2 * NG; ++e) acc[e] = 0.0;
+  if (run) {
+    for (int64_t u = gw; u < static_cast<int64_t>(a.A.n) * a.G; u += nwarps) {
+      const size_t idx = static_cast<size_t>(u / a.G) * a.Fp + j;
+      double2 rv[L + 1];
+#pragma unroll
+      for (int i = 0; i <= L; ++i) rv[i] = a.rl[i][idx];
+      int e = 0;
+#pragma unroll
+      for (int i = 0; i <= L; ++i)
+#pragma unroll
+        for (int k = i; k <= L; ++k, ++e) {
+          const double2 d = sw_dot(make_double2(acc[2 * e], acc[2 * e + 1]), rv[i], rv[k]);
+          acc[2 * e] = d.x;
+          acc[2 * e + 1] = d.y;
+        }
+    }
+  }
+  // block partials, entry by entry: the warps of a frequency's group in warp order
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int e = 0; e < NG; ++e) {
+    sh[(warp * 32 + lane) * 2] = acc[2 * e];
+    sh[(warp * 32 + lane) * 2 + 1] = acc[2 * e + 1];
+    __syncthreads();
+    const int jt = threadIdx.x;
+    if (jt < a.Fp) {
+      double s0 = 0.0, s1 = 0.0;
+      for (int w = 0; w < nw; ++w) {
+        const int gg = static_cast<int>((static_cast<int64_t>(blockIdx.x) * nw + w) % a.G);
+        if (gg != jt / 32) continue;
+        s0 += sh[(w * 32 + (jt & 31)) * 2];
+        s1 += sh[(w * 32 + (jt & 31)) * 2 + 1];
+      }
+      const size_t o = (static_cast<size_t>(blockIdx.x) * a.Fp + jt) * (2 * NG) + 2 * e;
+      a.gpart[o] = s0;
+      a.gpart[o + 1] = s1;
+    }
+    __syncthreads();
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(a.tickets + TK_AUX2, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // totals: Q threads per frequency add blocks q, q + Q, ...; the Q sums in q order
+  const int Q = blockDim.x / a.Fp;
+  const int jf = threadIdx.x % a.Fp, q = threadIdx.x / a.Fp;
+  for (int e = 0; e < NG; ++e) {
+    double s0 = 0.0, s1 = 0.0;
+    if (q < Q) {
+      for (unsigned int bb = q; bb < gridDim.x; bb += Q) {
+        const size_t o = (static_cast<size_t>(bb) * a.Fp + jf) * (2 * NG) + 2 * e;
+        s0 += ld_cg(&a.gpart[o]);
+        s1 += ld_cg(&a.gpart[o + 1]);
+      }
+    }
+    __syncthreads();
+    if (q < Q) {
+      sh[(q * a.Fp + jf) * 2] = s0;
+      sh[(q * a.Fp + jf) * 2 + 1] = s1;
+    }
+    __syncthreads();
+    if (threadIdx.x < a.Fp) {
+      double t0 = 0.0, t1 = 0.0;
+      for (int qq = 0; qq < Q; ++qq) {
+        t0 += sh[(qq * a.Fp + threadIdx.x) * 2];
+        t1 += sh[(qq * a.Fp + threadIdx.x) * 2 + 1];
+      }
+      a.gram[static_cast<size_t>(threadIdx.x) * kSwGram + e] = make_double2(t0, t1);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) a.tickets[TK_AUX2] = 0u;
+  const int f = threadIdx.x;
+  if (f < a.F && a.status[f] == ST_RUNNING) {
+    const double2* gm = a.gram + static_cast<size_t>(f) * kSwGram;
+    // G_ik for i <= k at index e(i, k); G_ki = conj(G_ik)
+    auto G = [&](int i, int k) -> double2 {
+      const bool sw = i > k;
+      const int lo = sw ? k : i, hi = sw ? i : k;
+      const double2 v = gm[lo * (L + 1) - lo * (lo - 1) / 2 + (hi - lo)];
+      return sw ? make_double2(v.x, -v.y) : v;
+    };
+    double2 Lc[L][L];
+    double2 g[L];
+    bool ok = true;
+    for (int i = 0; i < L && ok; ++i) {
+      for (int k = 0; k <= i; ++k) {
+        double2 sacc = G(i + 1, k + 1);
+        for (int m = 0; m < k; ++m) sacc = csub(sacc, cmul(Lc[i][m], make_double2(Lc[k][m].x, -Lc[k][m].y)));
+        if (i == k) {
+          if (!(sacc.x > 0.0) || !isfinite(sacc.x)) {
+            ok = false;
+            break;
+          }
+          Lc[i][i] = make_double2(sqrt(sacc.x), 0.0);
+        } else {
+          Lc[i][k] = make_double2(sacc.x / Lc[k][k].x, sacc.y / Lc[k][k].x);
+        }
+      }
+    }
+    if (!ok) {
+      a.status[f] = HELM_ERR_BREAKDOWN;
+    } else {
+      double2 y[L];
+      for (int i = 0; i < L; ++i) {  // L y = c
+        double2 sacc = G(i + 1, 0);
+        for (int m = 0; m < i; ++m) sacc = csub(sacc, cmul(Lc[i][m], y[m]));
+        y[i] = make_double2(sacc.x / Lc[i][i].x, sacc.y / Lc[i][i].x);
+      }
+      for (int i = L - 1; i >= 0; --i) {  // L^H g = y
+        double2 sacc = y[i];
+        for (int m = i + 1; m < L; ++m) sacc = csub(sacc, cmul(make_double2(Lc[m][i].x, -Lc[m][i].y), g[m]));
+        g[i] = make_double2(sacc.x / Lc[i][i].x, sacc.y / Lc[i][i].x);
+      }
+      bool fin = true;
+      for (int i = 0; i < L; ++i) {
+        fin &= cfinite(g[i]);
+        a.gcoef[static_cast<size_t>(f) * kSwMaxEll + i] = g[i];
+      }
+      if (!fin) a.status[f] = HELM_ERR_NONFINITE;
+      else {
+        a.omg[f] = g[L - 1];
+        if (czero(g[L - 1])) a.status[f] = HELM_ERR_BREAKDOWN;
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) sweep_refresh_groups(a);
+}
+
+// M2: x += sum g_k r_{k-1}; r_0 -= sum g_k r_k; u_0 -= sum g_k u_k;
+// ||r_0||^2, (r~, r_0) -> stop test, rho1; iteration cap, deadline; the
+// first scalar step of the next cycle
+template <int L>
+__global__ void __launch_bounds__(512) k_swl_mr(SweepArgs a) {
+  extern __shared__ double sh[];
+  if (a.st->status != ST_RUNNING) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) sweep_set_cond(a, false);
+    return;
+  }
+  SWEEP_ELEMENTWISE_BEGIN
+  double part[3] = {0.0, 0.0, 0.0};
+  if (run) {
+    double2 gk[L];
+#pragma unroll
+    for (int k = 0; k < L; ++k) gk[k] = a.gcoef[static_cast<size_t>(j) * kSwMaxEll + k];
+    for (int64_t u = gw; u < static_cast<int64_t>(a.A.n) * a.G; u += nwarps) {
+      const size_t idx = static_cast<size_t>(u / a.G) * a.Fp + j;
+      double2 xq = a.x[idx], r0 = a.rl[0][idx], u0 = a.ul[0][idx];
+      double2 rprev = r0;
+#pragma unroll
+      for (int k = 1; k <= L; ++k) {
+        const double2 rk = a.rl[k][idx];
+        xq = cfma(gk[k - 1], rprev, xq);
+        r0 = cfms(gk[k - 1], rk, r0);
+        u0 = cfms(gk[k - 1], a.ul[k][idx], u0);
+        rprev = rk;
+      }
+      a.x[idx] = xq;
+      a.rl[0][idx] = r0;
+      a.ul[0][idx] = u0;
+      part[0] = sw_nrm(part[0], r0);
+      const double2 d = sw_dot(make_double2(part[1], part[2]), a.rh[idx], r0);
+      part[1] = d.x;
+      part[2] = d.y;
+    }
+  }
+  double tot[3];
+  if (!sweep_grid_sum<3>(a, part, sh, a.tickets + TK_XR, tot)) return;
+  const bool late = a.st->deadline_ns != 0ull && (globaltimer_ns() - a.st->t0) > a.st->deadline_ns;
+  for (int jj = threadIdx.x; jj < a.F && jj == (int)threadIdx.x; jj += blockDim.x) {
+    if (a.status[jj] != ST_RUNNING) continue;
+    swl_stop(a, jj, tot[0]);
+    a.rho1[jj] = make_double2(tot[1], tot[2]);
+    if (a.status[jj] != ST_RUNNING) continue;
+    if (a.iters[jj] >= a.st->maxit) a.status[jj] = HELM_ERR_NOT_CONVERGED;
+    else if (late) a.status[jj] = HELM_ERR_TIMEOUT;
+    else swl_beta(a, jj, true);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) sweep_refresh_groups(a);
+}
+
 // X_user[i * ldx + j] <-> x[i * Fp + j]
 __global__ void k_sw_copy(int32_t n, int32_t F, int32_t Fp, const double2* __restrict__ src, int32_t lds,
                           double2* __restrict__ dst, int32_t ldd) {
@@ -1148,6 +1538,15 @@ struct helm_sweep_s {
   double2* tqscal = nullptr;
   int32_t* tqint = nullptr;
   int32_t Fcapq = 0;
+  // batched BiCGStab(l): r_1..r_l, u_1..u_l [2 l][n][Fcapl]; rho1, the
+  // coefficients and the Gram matrices [Fcapl * (1 + 8 + 45)]; the Gram
+  // step's block partials
+  double2* vecl = nullptr;
+  double2* lscal = nullptr;
+  double* gpart = nullptr;
+  int32_t Fcapl = 0, ellcap = 0;
+  size_t gpart_cap = 0;
+  int graphl_ell = 0;
   int warps_per_block = 8;        // autotuned
   bool tuned = false;
   std::mutex mu;
@@ -1156,7 +1555,7 @@ struct helm_sweep_s {
     const void* b = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
-  } graph, graph32, graphq;
+  } graph, graph32, graphq, graphl;
 };
 
 namespace {
@@ -1164,7 +1563,7 @@ namespace {
 // Graphs capture buffer addresses: both are dropped whenever a buffer they
 // use is replaced.
 void drop_sweep_graphs(helm_sweep S) {
-  for (helm_sweep_s::G* g : {&S->graph, &S->graph32, &S->graphq}) {
+  for (helm_sweep_s::G* g : {&S->graph, &S->graph32, &S->graphq, &S->graphl}) {
     if (g->exec) cudaGraphExecDestroy(g->exec);
     if (g->graph) cudaGraphDestroy(g->graph);
     *g = helm_sweep_s::G();
@@ -1315,6 +1714,11 @@ helm_status sweep_alloc_tfqmr(helm_sweep S, int32_t Fp) {
   cudaFree(S->vecq);
   cudaFree(S->tqscal);
   cudaFree(S->tqint);
+  cudaFree(S->vecl);
+  cudaFree(S->lscal);
+  cudaFree(S->gpart);
+  if (S->graphl.exec) cudaGraphExecDestroy(S->graphl.exec);
+  if (S->graphl.graph) cudaGraphDestroy(S->graphl.graph);
   S->vecq = nullptr;
   S->tqscal = nullptr;
   S->tqint = nullptr;
@@ -1342,6 +1746,59 @@ void set_tfqmr_args(helm_sweep S, SweepArgs& a) {
   a.start = S->tqint + a.Fp;
   a.gcheck = S->tqint + 2 * static_cast<size_t>(a.Fp);
   a.anychk = S->tqint + 2 * static_cast<size_t>(a.Fp) + a.Fp / 32;
+}
+
+// Buffers of the batched BiCGStab(l) (allocated at its first use, grown
+// with l and the number of frequencies).
+helm_status sweep_alloc_bicgstabl(helm_sweep S, int32_t Fp, int ell, size_t blocks) {
+  if (S->Fcapl < Fp || S->ellcap < ell) {
+    cudaFree(S->vecl);
+    cudaFree(S->lscal);
+    S->vecl = nullptr;
+    S->lscal = nullptr;
+    S->Fcapl = 0;
+    S->ellcap = 0;
+    const int32_t F2 = std::max(Fp, S->Fcapl);
+    const size_t nf = static_cast<size_t>(std::max<int32_t>(S->n, 1)) * F2;
+    HELM_CUDA_TRY(cudaMalloc(&S->vecl, 2 * static_cast<size_t>(ell) * nf * sizeof(double2)));
+    HELM_CUDA_TRY(cudaMalloc(&S->lscal, static_cast<size_t>(F2) * (1 + kSwMaxEll + kSwGram) * sizeof(double2)));
+    S->Fcapl = F2;
+    S->ellcap = ell;
+    if (S->graphl.exec) {
+      cudaGraphExecDestroy(S->graphl.exec);
+      cudaGraphDestroy(S->graphl.graph);
+    }
+    S->graphl = helm_sweep_s::G();
+  }
+  const size_t need = blocks * static_cast<size_t>(Fp) * 2 * kSwGram;
+  if (S->gpart_cap < need) {
+    cudaFree(S->gpart);
+    S->gpart = nullptr;
+    S->gpart_cap = 0;
+    HELM_CUDA_TRY(cudaMalloc(&S->gpart, need * sizeof(double)));
+    S->gpart_cap = need;
+    if (S->graphl.exec) {
+      cudaGraphExecDestroy(S->graphl.exec);
+      cudaGraphDestroy(S->graphl.graph);
+    }
+    S->graphl = helm_sweep_s::G();
+  }
+  return HELM_OK;
+}
+
+void set_bicgstabl_args(helm_sweep S, SweepArgs& a, int ell) {
+  const size_t nf = static_cast<size_t>(std::max<int32_t>(S->n, 1)) * a.Fp;
+  a.ell = ell;
+  a.rl[0] = a.r;
+  a.ul[0] = a.p;
+  for (int k = 1; k <= kSwMaxEll; ++k) {
+    a.rl[k] = k <= ell ? S->vecl + static_cast<size_t>(k - 1) * nf : nullptr;
+    a.ul[k] = k <= ell ? S->vecl + static_cast<size_t>(ell + k - 1) * nf : nullptr;
+  }
+  a.rho1 = S->lscal;
+  a.gcoef = S->lscal + a.Fp;
+  a.gram = S->lscal + static_cast<size_t>(a.Fp) * (1 + kSwMaxEll);
+  a.gpart = S->gpart;
 }
 
 struct SweepShape {
@@ -1487,6 +1944,41 @@ helm_status build_tfqmr_graph(const SweepArgs& base, const SweepShape& sh, cudaG
   return build_sweep_graph_with(
       base, [&](const SweepArgs& a, cudaStream_t cs) { swq_init(a, sh, cs); },
       [&](const SweepArgs& a, cudaStream_t cs) { swq_body(a, sh, cs); },
+      [&](const SweepArgs& a, cudaStream_t cs) { k_sw_tail<double2><<<sh.grid, sh.threads, sh.smem, cs>>>(a); },
+      gout, eout);
+}
+
+// The batched BiCGStab(l)'s launches: init, one cycle (4 l + 2 kernels).
+template <int L>
+void swl_body_l(const SweepArgs& a, const SweepShape& sh, cudaStream_t s) {
+  for (int js = 0; js < L; ++js) {
+    k_swl_u<<<sh.grid, sh.threads, 0, s>>>(a, js);
+    k_swl_au<<<sh.grid, sh.threads, sh.smem, s>>>(a, js);
+    k_swl_r<<<sh.grid, sh.threads, sh.smem, s>>>(a, js);
+    k_swl_ar<<<sh.grid, sh.threads, sh.smem, s>>>(a, js);
+  }
+  k_swl_gram<L><<<sh.grid, sh.threads, sh.smem, s>>>(a);
+  k_swl_mr<L><<<sh.grid, sh.threads, sh.smem, s>>>(a);
+}
+
+void swl_body(const SweepArgs& a, const SweepShape& sh, cudaStream_t s) {
+  switch (a.ell) {
+    case 1: swl_body_l<1>(a, sh, s); break;
+    case 2: swl_body_l<2>(a, sh, s); break;
+    case 3: swl_body_l<3>(a, sh, s); break;
+    case 4: swl_body_l<4>(a, sh, s); break;
+    case 5: swl_body_l<5>(a, sh, s); break;
+    case 6: swl_body_l<6>(a, sh, s); break;
+    case 7: swl_body_l<7>(a, sh, s); break;
+    default: swl_body_l<8>(a, sh, s); break;
+  }
+}
+
+helm_status build_bicgstabl_graph(const SweepArgs& base, const SweepShape& sh, cudaGraph_t* gout,
+                                  cudaGraphExec_t* eout) {
+  return build_sweep_graph_with(
+      base, [&](const SweepArgs& a, cudaStream_t cs) { k_swl_init<<<sh.grid, sh.threads, sh.smem, cs>>>(a); },
+      [&](const SweepArgs& a, cudaStream_t cs) { swl_body(a, sh, cs); },
       [&](const SweepArgs& a, cudaStream_t cs) { k_sw_tail<double2><<<sh.grid, sh.threads, sh.smem, cs>>>(a); },
       gout, eout);
 }
@@ -1746,6 +2238,11 @@ helm_status helm_sweep_destroy(helm_sweep S) {
   cudaFree(S->vecq);
   cudaFree(S->tqscal);
   cudaFree(S->tqint);
+  cudaFree(S->vecl);
+  cudaFree(S->lscal);
+  cudaFree(S->gpart);
+  if (S->graphl.exec) cudaGraphExecDestroy(S->graphl.exec);
+  if (S->graphl.graph) cudaGraphDestroy(S->graphl.graph);
   if (S->graph32.exec) cudaGraphExecDestroy(S->graph32.exec);
   if (S->graph32.graph) cudaGraphDestroy(S->graph32.graph);
   if (S->graphq.exec) cudaGraphExecDestroy(S->graphq.exec);
@@ -1765,8 +2262,10 @@ helm_status helm_sweep_solve(helm_sweep S, int32_t nfreq, const double* h_omega,
   if (S->n > 0 && (!d_b || !d_X)) return HELM_ERR_INVALID;
   if (!aligned(d_b, 16) || !aligned(d_X, 16) || !(opts.tol >= 0.0) || opts.maxit < 0) return HELM_ERR_INVALID;
   if (opts.precision != HELM_PREC_FP64 && opts.precision != HELM_PREC_MIXED) return HELM_ERR_INVALID;
-  if (opts.method != HELM_BICGSTAB && !(opts.method == HELM_TFQMR && opts.precision == HELM_PREC_FP64))
+  if (opts.method != HELM_BICGSTAB &&
+      !((opts.method == HELM_TFQMR || opts.method == HELM_BICGSTABL) && opts.precision == HELM_PREC_FP64))
     return HELM_ERR_INVALID;
+  if (opts.method == HELM_BICGSTABL && (opts.ell < 1 || opts.ell > kSwMaxEll)) return HELM_ERR_INVALID;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   std::lock_guard<std::mutex> lk(S->mu);
   const int32_t Fp = (nfreq + 31) / 32 * 32;
@@ -1808,26 +2307,34 @@ helm_status helm_sweep_solve(helm_sweep S, int32_t nfreq, const double* h_omega,
         S->n, nfreq, Fp, static_cast<const double2*>(d_X), ldx, a.x, Fp);
   }
   const bool tq = opts.method == HELM_TFQMR;
+  const bool bl = opts.method == HELM_BICGSTABL;
   if (tq) {
     st = sweep_alloc_tfqmr(S, Fp);
     if (st != HELM_OK) return st;
     set_tfqmr_args(S, a);
   }
-  // graph for (method, F, b, stride)
-  helm_sweep_s::G& gr = tq ? S->graphq : S->graph;
-  if (!(gr.exec && gr.F == nfreq && gr.b == bsrc && gr.b_ld == bld)) {
+  if (bl) {
+    st = sweep_alloc_bicgstabl(S, Fp, opts.ell, sh.grid);
+    if (st != HELM_OK) return st;
+    set_bicgstabl_args(S, a, opts.ell);
+  }
+  // graph for (method, l, F, b, stride)
+  helm_sweep_s::G& gr = tq ? S->graphq : bl ? S->graphl : S->graph;
+  if (!(gr.exec && gr.F == nfreq && gr.b == bsrc && gr.b_ld == bld && (!bl || S->graphl_ell == opts.ell))) {
     if (gr.exec) {
       cudaGraphExecDestroy(gr.exec);
       cudaGraphDestroy(gr.graph);
     }
     gr = helm_sweep_s::G();
     if (!bcopy) {
-      const helm_status gs = tq ? build_tfqmr_graph(a, sh, &gr.graph, &gr.exec)
-                                : build_sweep_graph(a, sh, &gr.graph, &gr.exec);
+      const helm_status gs = tq   ? build_tfqmr_graph(a, sh, &gr.graph, &gr.exec)
+                             : bl ? build_bicgstabl_graph(a, sh, &gr.graph, &gr.exec)
+                                  : build_sweep_graph(a, sh, &gr.graph, &gr.exec);
       if (gs == HELM_OK) {
         gr.F = nfreq;
         gr.b = bsrc;
         gr.b_ld = bld;
+        if (bl) S->graphl_ell = opts.ell;
       }
     }
   }
@@ -1843,10 +2350,12 @@ helm_status helm_sweep_solve(helm_sweep S, int32_t nfreq, const double* h_omega,
     } else {
       SolverState hs;
       if (tq) swq_init(a, sh, s);
+      else if (bl) k_swl_init<<<sh.grid, sh.threads, sh.smem, s>>>(a);
       else k_sw_init<double2><<<sh.grid, sh.threads, sh.smem, s>>>(a);
       for (;;) {
         for (int k = 0; k < 8; ++k) {
           if (tq) swq_body(a, sh, s);
+          else if (bl) swl_body(a, sh, s);
           else enqueue_sweep_body(a, sh, s);
         }
         HELM_CUDA_TRY(cudaGetLastError());
@@ -1893,7 +2402,7 @@ helm_status helm_sweep_solve(helm_sweep S, int32_t nfreq, const double* h_omega,
       h_infos[j].relres_recur = relres[j];
       h_infos[j].relres_true = relres_true[j];
       h_infos[j].status = sj;
-      h_infos[j].spmv_count = 2 * iters[j];
+      h_infos[j].spmv_count = 2 * iters[j] * (bl ? opts.ell : 1);
     }
     if (sj != HELM_OK && worst == HELM_OK) worst = sj;
   }

@@ -25,23 +25,36 @@ def _relres(p, vals, b, x):
 
 
 def _method(name):
-    return helm.HELM_TFQMR if name == "tfqmr" else helm.HELM_BICGSTAB
+    """Solver options of a method name: bicgstab, tfqmr, bicgstabl<l>."""
+    if name == "tfqmr":
+        return dict(method=helm.HELM_TFQMR)
+    if name.startswith("bicgstabl"):
+        return dict(method=helm.HELM_BICGSTABL, ell=int(name[len("bicgstabl"):]))
+    return dict(method=helm.HELM_BICGSTAB)
 
 
 def _oracle_method(name):
-    return oracle.tfqmr if name == "tfqmr" else oracle.bicgstab
+    if name == "tfqmr":
+        return oracle.tfqmr
+    if name.startswith("bicgstabl"):
+        ell = int(name[len("bicgstabl"):])
+        return lambda *args, **kw: oracle.bicgstabl(*args, ell=ell, **kw)
+    return oracle.bicgstab
 
 
-@pytest.mark.parametrize("method", ["bicgstab", "tfqmr"])
+@pytest.mark.parametrize("method", ["bicgstab", "tfqmr", "bicgstabl1", "bicgstabl2", "bicgstabl4", "bicgstabl8"])
 @pytest.mark.parametrize("dims,freqs,shared_b", [
     ((4, 3, 3), [150.0, 420.0, 800.0], True),
     ((6, 5, 4), list(np.linspace(100.0, 1000.0, 40)), False),
 ])
 def test_sweep_small_vs_oracle(dims, freqs, shared_b, method):
-    """Batched BiCGStab and batched TFQMR against the oracle's solve of the
-    same method on each explicitly assembled A_j (TFQMR also: iterations
+    """Batched BiCGStab, TFQMR and BiCGStab(l) against the oracle's solve of
+    the same method on each explicitly assembled A_j (TFQMR also: iterations
     within 5 % + 2 of the oracle's, which checks its true residual after
-    every half-step where the batched solve checks once per iteration)."""
+    every half-step where the batched solve checks once per iteration;
+    BiCGStab(l): cycles within 10 % + 1 of the oracle's, whose
+    minimal-residual step uses modified Gram-Schmidt where the batched solve
+    uses the normal equations)."""
     cfg = g.tiny_config(*dims, h=0.1, seed=6)
     p = g.assemble(cfg)
     F = len(freqs)
@@ -55,7 +68,7 @@ def test_sweep_small_vs_oracle(dims, freqs, shared_b, method):
         bt = torch.as_tensor(B, device=DEV).contiguous()
         bs = [B[:, j] for j in range(F)]
     S = helm.Sweep(p.rowptr, p.colind, p.K, p.Mc, p.Bc, device=DEV)
-    X, infos = S.solve(w, bt, tol=1e-12, maxit=20000, method=_method(method))
+    X, infos = S.solve(w, bt, tol=1e-12, maxit=20000, **_method(method))
     Xh = X.cpu().numpy()
     for j in range(F):
         vals = oracle.helmholtz_values(p.K, p.Mc, p.Bc, w[j])
@@ -69,12 +82,15 @@ def test_sweep_small_vs_oracle(dims, freqs, shared_b, method):
         assert e_g <= max(1e-8, 2 * e_o)
         if method == "tfqmr" and infos[j]["restarts"] == 0:
             assert abs(infos[j]["iters"] - io["iters"]) <= 0.05 * io["iters"] + 2, (j, infos[j], io)
+        if method.startswith("bicgstabl") and infos[j]["restarts"] == 0:
+            assert abs(infos[j]["iters"] - io["iters"]) <= 0.1 * io["iters"] + 1, (j, infos[j], io)
     S.close()
 
 
 def test_sweep60_against_oracle():
     """60x30x25 cavity, 64 frequencies 100-1000 Hz at 1e-8 (the benchmark's
-    sweep): batched BiCGStab, complex64-inner BiCGStab and batched TFQMR.  Every frequency: status ok and the true residual, recomputed with
+    sweep): batched BiCGStab, complex64-inner BiCGStab, batched TFQMR and
+    batched BiCGStab(4).  Every frequency: status ok and the true residual, recomputed with
     the oracle's SpMV on the oracle-assembled A_j, at most tol.  Five
     frequencies spread over the band, the hardest (1000 Hz) among them,
     against the oracle's solve of the same method on A_j: ||x_gpu - x_tight|| /
@@ -100,9 +116,16 @@ def test_sweep60_against_oracle():
         assert info["status"] == "ok", (j, info)
         return x
 
-    with ThreadPoolExecutor(max_workers=len(picks) * 3) as ex:
+    def oracle_bicgstabl(j):
+        vals = oracle.helmholtz_values(p.K, p.Mc, p.Bc, w[j])
+        x, info = oracle.bicgstabl(p.rowptr, p.colind, vals, b, ell=4, tol=cfg.tol, maxit=60000)
+        assert info["status"] == "ok", (j, info)
+        return x
+
+    with ThreadPoolExecutor(max_workers=len(picks) * 4) as ex:
         futs = {(j, tol): ex.submit(oracle_solve, (j, tol)) for j in picks for tol in (1e-8, 1e-13)}
         futq = {j: ex.submit(oracle_tfqmr, j) for j in picks}
+        futl = {j: ex.submit(oracle_bicgstabl, j) for j in picks}
         S = helm.Sweep(p.rowptr, p.colind, p.K, p.Mc, p.Bc, device=DEV)
         X, infos = S.solve(w, torch.as_tensor(b, device=DEV), tol=cfg.tol, maxit=30000)
         Xh = X.cpu().numpy()
@@ -140,6 +163,28 @@ def test_sweep60_against_oracle():
             assert infq[j]["status"] == "ok", (j, infq[j])
             r = _relres(p, vals, b, Xqh[:, j])
             assert r <= cfg.tol * (1 + 1e-6) and abs(r - infq[j]["relres_true"]) <= 1e-3 * r, (j, r, infq[j])
+        # batched BiCGStab(4) of the same system
+        S = helm.Sweep(p.rowptr, p.colind, p.K, p.Mc, p.Bc, device=DEV)
+        Xl, infl = S.solve(w, torch.as_tensor(b, device=DEV), tol=cfg.tol, maxit=30000, method=helm.HELM_BICGSTABL,
+                           ell=4)
+        Xlh = Xl.cpu().numpy()
+        S.close()
+        print(f"sweep60 BiCGStab(4): cycles total {sum(i['iters'] for i in infl)}, restarts "
+              f"{sum(i['restarts'] for i in infl)}")
+        for j in range(len(w)):
+            vals = oracle.helmholtz_values(p.K, p.Mc, p.Bc, w[j])
+            assert infl[j]["status"] == "ok", (j, infl[j])
+            r = _relres(p, vals, b, Xlh[:, j])
+            assert r <= cfg.tol * (1 + 1e-6) and abs(r - infl[j]["relres_true"]) <= 1e-3 * r, (j, r, infl[j])
+        for j in picks:
+            x_t = futs[(j, 1e-13)].result()
+            x_l = futl[j].result()
+            nt = np.linalg.norm(x_t)
+            e_l = np.linalg.norm(x_l - x_t) / nt
+            e_g = np.linalg.norm(Xlh[:, j] - x_t) / nt
+            print(f"  F = {cfg.freqs[j]:.1f} Hz bicgstab(4): gpu error {e_g:.2e}, oracle BiCGStab(4) error "
+                  f"{e_l:.2e}, cycles {infl[j]['iters']}")
+            assert e_g <= max(1e-8, 2.0 * e_l), ("bicgstabl", j, e_g, e_l)
         for j in picks:
             x_t = futs[(j, 1e-13)].result()
             x_q = futq[j].result()
@@ -246,7 +291,7 @@ def test_sweep_operator_entries_and_product():
     S.close()
 
 
-@pytest.mark.parametrize("method", ["bicgstab", "tfqmr"])
+@pytest.mark.parametrize("method", ["bicgstab", "tfqmr", "bicgstabl4"])
 def test_sweep_restarts_a_frequency_whose_true_residual_misses_tol(method):
     """At a tolerance near rounding level the recurrence of some frequencies
     meets tol before their true residual does; those restart from their x
@@ -260,7 +305,7 @@ def test_sweep_restarts_a_frequency_whose_true_residual_misses_tol(method):
     S = helm.Sweep(p.rowptr, p.colind, p.K, p.Mc, p.Bc, device=DEV)
     restarted = 0
     for tol in (1e-13, 1e-15):
-        X, infos = S.solve(w, torch.as_tensor(b, device=DEV), tol=tol, maxit=3000, method=_method(method))
+        X, infos = S.solve(w, torch.as_tensor(b, device=DEV), tol=tol, maxit=3000, **_method(method))
         Xh = X.cpu().numpy()
         for j in range(len(w)):
             vals = oracle.helmholtz_values(p.K, p.Mc, p.Bc, w[j])
@@ -281,18 +326,18 @@ def test_sweep_restarts_a_frequency_whose_true_residual_misses_tol(method):
     S.close()
 
 
-@pytest.mark.parametrize("method", ["bicgstab", "tfqmr"])
+@pytest.mark.parametrize("method", ["bicgstab", "tfqmr", "bicgstabl4"])
 def test_sweep_masking_freezes_converged_frequencies(method):
     cfg = g.tiny_config(5, 4, 4, h=0.1, seed=7)
     p = g.assemble(cfg)
     b = torch.as_tensor(g.source(p), device=DEV)
     w = [g.omega(f) for f in (100.0, 900.0)]
     S = helm.Sweep(p.rowptr, p.colind, p.K, p.Mc, p.Bc, device=DEV)
-    X, infos = S.solve(w, b, tol=1e-10, method=_method(method))
+    X, infos = S.solve(w, b, tol=1e-10, **_method(method))
     assert all(i["status"] == "ok" for i in infos)
     assert infos[0]["iters"] < infos[1]["iters"]      # uneven counts, each stopped at its own
     # maxit reached for the hard one only
-    X2, infos2 = S.solve(w, b, tol=1e-10, maxit=infos[0]["iters"], method=_method(method))
+    X2, infos2 = S.solve(w, b, tol=1e-10, maxit=infos[0]["iters"], **_method(method))
     assert infos2[0]["status"] == "ok" and infos2[1]["status"] == "not_converged"
     assert np.allclose(X2[:, 0].cpu().numpy(), X[:, 0].cpu().numpy(), rtol=0, atol=0)
     S.close()
