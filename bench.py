@@ -565,6 +565,48 @@ def run_spmv_only(args):
     A.close()
 
 
+def run_spmv64(args):
+    """The complex64 product (the inner solves of mixed precision) on the
+    cavity120 and cavity200 matrices, with the diagonal copy and with the
+    sliced copy alone: `reps` launches after `warmup`, both matrices larger
+    than L2.  GB/s on the complex64 CSR algorithmic bytes 12 nnz + 4 (n + 1)
+    + 16 n."""
+    import numpy as np
+    import torch
+
+    import paper_2112_11880_gb300 as helm
+    from paper_2112_11880_gb300 import build as hbuild
+    hbuild.build()
+    dev = torch.device("cuda", 0)
+    peaks, peak_src = load_peaks()
+    for name in ("cavity120", "cavity200"):
+        cfg = helmgen.CONFIGS[name]
+        p, vals, _ = build_problem(cfg)
+        x = torch.as_tensor(helmgen.complex_vector(p.n, 1).astype(np.complex64), device=dev)
+        y = torch.empty_like(x)
+        res = {}
+        for sliced in (False, True):
+            A = helm.CsrMatrix.from_host(p.rowptr, p.colind, vals.astype(np.complex64), device=dev, sliced_only=sliced)
+            for _ in range(args.warmup):
+                A.matvec(x, y)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.reps):
+                A.matvec(x, y)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / max(args.reps, 1)
+            gbs = (12 * p.nnz + 4 * (p.n + 1) + 16 * p.n) / ms / 1e6
+            res["sliced" if sliced else "diagonal"] = {"us": round(ms * 1e3, 2), "gbs_alg": round(gbs, 1),
+                                                       "frac": round(gbs / float(peaks["hbm_gbs"]), 3),
+                                                       "diagonals": A.diagonals()}
+            A.close()
+        print(json.dumps({"kernel": "spmv_c64", "workload": name, "n": p.n, "nnz": p.nnz, **res,
+                          "peak_gbs": peaks["hbm_gbs"], "peak_source": peak_src}), flush=True)
+
+
 # Vector lengths of the paper's BLAS-1 measurements (Section 3, Tables 2-7):
 # the order of Audi3D-4 and three larger sizes.
 VECTOR_SIZES = (648_849, 2_000_000, 9_000_000, 14_000_000)
@@ -803,8 +845,9 @@ def main():
     ap.add_argument("--ref-iters-per-solve", type=int, default=int(os.environ.get("HELM_ITERS_PER_SOLVE", "0")) or 0)
     ap.add_argument("--mixed-maxit", type=int, default=200000)
     ap.add_argument("--inner-tol", type=float, default=1e-3)
-    ap.add_argument("--mode", default="bench", choices=["bench", "spmv", "extensions", "vectors"],
+    ap.add_argument("--mode", default="bench", choices=["bench", "spmv", "spmv64", "extensions", "vectors"],
                     help="spmv: only the complex128 SpMV loop on the same matrix (profiling target); "
+                         "spmv64: the complex64 product with the diagonal and the sliced copy; "
                          "vectors: the BLAS-1 operations alone at the paper's vector lengths")
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--extensions", default="on", choices=["on", "off"],
@@ -820,6 +863,8 @@ def main():
         run_extensions(args)
     elif args.mode == "vectors":
         run_vectors(args)
+    elif args.mode == "spmv64":
+        run_spmv64(args)
     elif args.impl == "reference":
         if not args.ref_iters_per_solve:
             args.ref_iters_per_solve = REF_ITERS_PER_SOLVE

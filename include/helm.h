@@ -58,6 +58,8 @@ typedef enum { HELM_C128 = 0, HELM_C64 = 1 } helm_dtype;
 /* Flags for helm_csr_create. */
 #define HELM_CSR_VALIDATE 1u  /* check rowptr monotone, colind in range and
                                  sorted within rows (one device pass + sync) */
+#define HELM_CSR_SLICED_ONLY 2u  /* no diagonal copy: complex64 products read
+                                    the sliced copy too */
 
 typedef struct helm_csr_s* helm_csr; /* opaque CSR handle */
 
@@ -70,14 +72,23 @@ typedef struct helm_csr_s* helm_csr; /* opaque CSR handle */
  *   d_rowptr : int32[n+1], rowptr[0] = 0, non-decreasing.
  *   d_colind : int32[nnz], column of each entry, 0 <= colind < n.
  *   d_vals   : complex[nnz] of type dt (complex128 or complex64).
- *   flags    : HELM_CSR_VALIDATE or 0.
+ *   flags    : HELM_CSR_VALIDATE, HELM_CSR_SLICED_ONLY (or'ed) or 0.
  * Ownership: the handle keeps the three device pointers (no copy); they must
  * stay valid and unchanged until helm_csr_destroy.  What it derives from them
  * is its own: a sliced-ELLPACK copy of the matrix (slices of 32 rows, entry k
  * of each row at a stride of 32: the columns, the real parts of the values
  * and, separately, the entries with a nonzero imaginary part; about 12 bytes
  * per stored entry for complex128), and the complex64 and right-Jacobi copies
- * (at the first solve that needs them).
+ * (at the first solve that needs them).  When every entry lies on one of at
+ * most 32 diagonals col - row = const (the longest row's), rows are sorted
+ * without duplicates, and the diagonals hold at most 1.5 slots per stored
+ * entry (a structured mesh in its natural numbering), the complex64 value
+ * sets also get a diagonal copy of their real parts (float[diagonals][n], no
+ * column index; 4 bytes per slot): the complex64 product, bound by HBM on
+ * GB300, reads it instead of the sliced copy, with the same result for
+ * finite x (the diagonals are summed in column order, empty slots skipped).
+ * complex128 products always read the sliced copy (their bound is the FP64
+ * pipe, and empty slots would add FP64 work).
  * Work done: row statistics, the sliced copy, workspace allocation, and the
  * choice of SpMV variant: for nnz >= 2^18 the stand-alone SpMV's variants
  * are timed on this matrix and the fastest is kept (every variant gives the
@@ -94,6 +105,11 @@ helm_status helm_csr_create(helm_csr* out, int32_t n, int64_t nnz, const int32_t
 /* helm_csr_destroy -- free the handle's workspace (synchronises the device
  * work of the handle first).  NULL is accepted. */
 helm_status helm_csr_destroy(helm_csr A);
+
+/* helm_csr_diagonals -- *out (host) = the number of diagonals of the
+ * handle's diagonal copy, 0 when it has none (complex64 products then read
+ * the sliced copy).  HELM_ERR_INVALID for a NULL argument. */
+helm_status helm_csr_diagonals(helm_csr A, int32_t* out);
 
 /*
  * helm_spmv -- y = alpha * A x + beta * y (Section 3, Table 8: CSR SpMV,

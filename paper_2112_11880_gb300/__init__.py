@@ -33,6 +33,7 @@ STATUS_NAMES = {0: "ok", 1: "invalid", 2: "cuda", 3: "nomem", 4: "not_converged"
 HELM_C128 = 0
 HELM_C64 = 1
 HELM_CSR_VALIDATE = 1
+HELM_CSR_SLICED_ONLY = 2
 
 HELM_BICGSTAB = 0
 HELM_TFQMR = 1
@@ -76,6 +77,7 @@ SIGNATURES = {
     "helm_csr_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, ctypes.c_int64, _P, _P, _P,
                                        ctypes.c_int, ctypes.c_uint32, _P]),
     "helm_csr_destroy": (ctypes.c_int, [_P]),
+    "helm_csr_diagonals": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
     "helm_spmv": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "helm_dot": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, _P, _P, ctypes.c_int, _P, _P]),
     "helm_dot_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, _P, _P, ctypes.c_int, _P, _P]),
@@ -166,6 +168,13 @@ def helm_csr_create(n, nnz, d_rowptr, d_colind, d_vals, dt, flags=0, stream=None
 
 def helm_csr_destroy(handle) -> None:
     _check(load_library().helm_csr_destroy(handle), "helm_csr_destroy")
+
+
+def helm_csr_diagonals(handle) -> int:
+    """Diagonals of the handle's diagonal copy (0: complex64 products read the sliced copy)."""
+    out = ctypes.c_int32(0)
+    _check(load_library().helm_csr_diagonals(handle, ctypes.byref(out)), "helm_csr_diagonals")
+    return out.value
 
 
 def helm_spmv(handle, alpha, x, beta, y, stream=None) -> None:
@@ -395,7 +404,7 @@ class CsrMatrix:
     """A CSR matrix on the GPU with its libhelm handle.  Holds references to
     the index and value tensors so they outlive the handle."""
 
-    def __init__(self, rowptr, colind, vals, validate: bool = False, stream=None):
+    def __init__(self, rowptr, colind, vals, validate: bool = False, stream=None, sliced_only: bool = False):
         import torch
         _require_cuda(rowptr, colind, vals)
         if rowptr.dtype != torch.int32 or colind.dtype != torch.int32:
@@ -404,15 +413,16 @@ class CsrMatrix:
         self.n = rowptr.numel() - 1
         self.nnz = colind.numel()
         self.dtype = vals.dtype
+        flags = (HELM_CSR_VALIDATE if validate else 0) | (HELM_CSR_SLICED_ONLY if sliced_only else 0)
         self.handle = helm_csr_create(self.n, self.nnz, _ptr(rowptr), _ptr(colind), _ptr(vals), _dtype_code(vals),
-                                      HELM_CSR_VALIDATE if validate else 0, stream)
+                                      flags, stream)
 
     @classmethod
-    def from_host(cls, rowptr, colind, vals, device="cuda", validate: bool = False):
+    def from_host(cls, rowptr, colind, vals, device="cuda", validate: bool = False, sliced_only: bool = False):
         import torch
         return cls(torch.as_tensor(rowptr, dtype=torch.int32).to(device).contiguous(),
                    torch.as_tensor(colind, dtype=torch.int32).to(device).contiguous(),
-                   torch.as_tensor(vals).to(device).contiguous(), validate=validate)
+                   torch.as_tensor(vals).to(device).contiguous(), validate=validate, sliced_only=sliced_only)
 
     def matvec(self, x, y=None, alpha=1.0, beta=0.0, stream=None):
         import torch
@@ -422,6 +432,9 @@ class CsrMatrix:
         _check_vector(y, self.n, self.dtype, "y")
         helm_spmv(self.handle, alpha, x, beta, y, stream)
         return y
+
+    def diagonals(self) -> int:
+        return helm_csr_diagonals(self.handle)
 
     def close(self):
         if getattr(self, "handle", None):

@@ -7,6 +7,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <climits>
+#include <cstdint>
 #include <mutex>
 #include <new>
 #include <utility>
@@ -341,6 +343,62 @@ __global__ void k_c128_to_c64(int64_t n, const double2* __restrict__ a, float2* 
   }
 }
 
+// ---------------------------------------------------------------- diagonal copy (complex64 products)
+
+// The longest row: key = (length << 32) | row, the largest key wins.
+__global__ void k_dia_probe(int32_t n, const int32_t* __restrict__ rowptr, unsigned long long* key) {
+  unsigned long long best = 0ull;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const unsigned long long len = static_cast<unsigned long long>(rowptr[i + 1] - rowptr[i]);
+    const unsigned long long k = (len << 32) | static_cast<unsigned long long>(static_cast<uint32_t>(i));
+    best = k > best ? k : best;
+  }
+  for (int o = 16; o; o >>= 1) {
+    const unsigned long long v = __shfl_xor_sync(0xffffffffu, best, o);
+    best = v > best ? v : best;
+  }
+  if ((threadIdx.x & 31) == 0 && best) atomicMax(key, best);
+}
+
+struct DiaOffsets {
+  int32_t nd;
+  int32_t off[32];
+};
+
+// Flags an entry whose diagonal col - row is not among D's, and a row whose
+// columns are not strictly ascending.
+__global__ void k_dia_check(int32_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+                            DiaOffsets D, int* bad) {
+  int local = 0;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int64_t prev = INT64_MIN;
+    for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+      const int32_t c = colind[k];
+      if (c <= prev) local = 1;
+      prev = c;
+      const int32_t d = c - i;
+      bool found = false;
+      for (int q = 0; q < D.nd; ++q) found |= D.off[q] == d;
+      if (!found) local = 1;
+    }
+  }
+  if (local) atomicOr(bad, 1);
+}
+
+// dval[d][i] = Re a(i, i + off[d]) as float (the array starts zeroed)
+template <class V>
+__global__ void k_dia_fill(int32_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+                           const V* __restrict__ vals, DiaOffsets D, float* __restrict__ dval) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+      const int32_t d = colind[k] - i;
+      int q = 0;
+      while (q < D.nd - 1 && D.off[q] != d) ++q;
+      dval[static_cast<size_t>(q) * n + i] = static_cast<float>(vals[k].x);
+    }
+  }
+}
+
 // ---------------------------------------------------------------- host helpers
 
 void debug_cuda_error(cudaError_t e, const char* file, int line) {
@@ -548,7 +606,102 @@ static helm_status build_sell_pattern(helm_csr A, cudaStream_t s) {
   return HELM_OK;
 }
 
+// Whether the pattern lies on at most 32 diagonals with little padding: the
+// longest row's diagonals are the candidates, one device pass checks every
+// entry (and that rows are sorted without duplicates).  Sets A->ndia and
+// A->dia_off; leaves ndia = 0 (sliced copy only) otherwise.
+constexpr double kDiaMaxFill = 1.5;  // diagonal slots per stored entry at most
+
+static helm_status analyze_diagonals(helm_csr A, cudaStream_t s) {
+  A->ndia = 0;
+  if (A->n == 0 || A->nnz == 0 || A->max_row > 32) return HELM_OK;
+  unsigned long long* d_key = nullptr;
+  int* d_bad = nullptr;
+  unsigned long long key = 0;
+  int bad = 0;
+  DiaOffsets D;
+  std::memset(&D, 0, sizeof(D));
+  helm_status st = HELM_OK;
+  do {
+    if (cudaMalloc(&d_key, sizeof(unsigned long long)) != cudaSuccess || cudaMalloc(&d_bad, sizeof(int)) != cudaSuccess) {
+      st = HELM_ERR_NOMEM;
+      break;
+    }
+    cudaError_t e = cudaMemsetAsync(d_key, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) {
+      k_dia_probe<<<vec_grid_for(A->n), 256, 0, s>>>(A->n, A->rowptr, d_key);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&key, d_key, sizeof(key), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      st = HELM_ERR_CUDA;
+      break;
+    }
+    const int32_t row = static_cast<int32_t>(key & 0xffffffffull), len = static_cast<int32_t>(key >> 32);
+    if (len < 1 || len > 32) break;
+    if (static_cast<double>(len) * A->n > kDiaMaxFill * static_cast<double>(A->nnz)) break;
+    int32_t k0 = 0;
+    int32_t cols[32];
+    e = cudaMemcpyAsync(&k0, A->rowptr + row, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cols, A->colind + k0, sizeof(int32_t) * len, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_bad, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      st = HELM_ERR_CUDA;
+      break;
+    }
+    D.nd = len;
+    for (int q = 0; q < len; ++q) D.off[q] = cols[q] - row;
+    bool ascending = true;
+    for (int q = 1; q < len; ++q) ascending &= D.off[q] > D.off[q - 1];
+    if (!ascending) break;
+    k_dia_check<<<vec_grid_for(A->n), 256, 0, s>>>(A->n, A->rowptr, A->colind, D, d_bad);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      st = HELM_ERR_CUDA;
+      break;
+    }
+    if (bad) break;
+    if (cudaMalloc(&A->dia_off, sizeof(int32_t) * len) != cudaSuccess) {
+      st = HELM_ERR_NOMEM;
+      break;
+    }
+    if (cudaMemcpyAsync(A->dia_off, D.off, sizeof(int32_t) * len, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      st = HELM_ERR_CUDA;
+      break;
+    }
+    A->ndia = len;
+  } while (false);
+  cudaFree(d_key);
+  cudaFree(d_bad);
+  (void)cudaGetLastError();
+  return st;
+}
+
+// The diagonal copy of a complex64 value set (when the handle has one).
+static helm_status build_dia_vals(helm_csr A, const float2* vals, SellVals* out, cudaStream_t s) {
+  if (A->ndia == 0) return HELM_OK;
+  DiaOffsets D;
+  std::memset(&D, 0, sizeof(D));
+  D.nd = A->ndia;
+  HELM_CUDA_TRY(cudaMemcpyAsync(D.off, A->dia_off, sizeof(int32_t) * A->ndia, cudaMemcpyDeviceToHost, s));
+  HELM_CUDA_TRY(cudaStreamSynchronize(s));
+  const size_t slots = static_cast<size_t>(A->ndia) * A->n;
+  HELM_CUDA_TRY(cudaMalloc(&out->dval, sizeof(float) * slots));
+  HELM_CUDA_TRY(cudaMemsetAsync(out->dval, 0, sizeof(float) * slots, s));
+  k_dia_fill<float2><<<vec_grid_for(A->n), 256, 0, s>>>(A->n, A->rowptr, A->colind, vals, D,
+                                                         static_cast<float*>(out->dval));
+  HELM_CUDA_TRY(cudaGetLastError());
+  return HELM_OK;
+}
+
 static void free_sell_vals(SellVals* v) {
+  cudaFree(v->dval);
   cudaFree(v->sval);
   cudaFree(v->isoff);
   cudaFree(v->icol);
@@ -598,6 +751,7 @@ static helm_status build_sell_vals_t(helm_csr A, const V* vals, SellVals* out, c
 helm_status build_sell_vals(helm_csr A, const void* vals, helm_dtype dt, SellVals* out, cudaStream_t s) {
   helm_status st = dt == HELM_C128 ? build_sell_vals_t<double2>(A, static_cast<const double2*>(vals), out, s)
                                    : build_sell_vals_t<float2>(A, static_cast<const float2*>(vals), out, s);
+  if (st == HELM_OK && dt == HELM_C64) st = build_dia_vals(A, static_cast<const float2*>(vals), out, s);
   if (st != HELM_OK) free_sell_vals(out);
   return st;
 }
@@ -794,6 +948,8 @@ helm_status helm_csr_create(helm_csr* out, int32_t n, int64_t nnz, const int32_t
   // the SELL-32 copy the SpMV engine reads (columns, real parts, imaginary
   // entries), then the stand-alone SpMV variant for this matrix
   helm_status st = build_sell_pattern(A, s);
+  // complex64 products read the diagonal copy when the pattern has one
+  if (st == HELM_OK && !(flags & HELM_CSR_SLICED_ONLY)) st = analyze_diagonals(A, s);
   if (st == HELM_OK) st = build_sell_vals(A, d_vals, dt, &A->sv, s);
   if (st == HELM_OK)
     st = dt == HELM_C128 ? autotune_spmv<double2>(A, csr_dev<double2>(A, static_cast<const double2*>(d_vals), A->sv), s)
@@ -822,6 +978,7 @@ helm_status helm_csr_destroy(helm_csr A) {
   cudaFree(A->vals32);
   cudaFree(A->sell_off);
   cudaFree(A->sell_col);
+  cudaFree(A->dia_off);
   free_sell_vals(&A->sv);
   free_sell_vals(&A->sv32);
   free_sell_vals(&A->svjac);
@@ -832,6 +989,12 @@ helm_status helm_csr_destroy(helm_csr A) {
   (void)cudaGetLastError();
   if (prev >= 0) cudaSetDevice(prev);
   delete A;
+  return HELM_OK;
+}
+
+helm_status helm_csr_diagonals(helm_csr A, int32_t* out) {
+  if (!A || !out) return HELM_ERR_INVALID;
+  *out = A->ndia;
   return HELM_OK;
 }
 

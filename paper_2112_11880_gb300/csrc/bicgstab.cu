@@ -204,16 +204,19 @@ __global__ void __launch_bounds__(kSolverThreads, kSolverMinBlocks) k_bicgstab_p
   for (;;) {  // one pass per (re)start
     // init: r = b - A x or b
     {
-      double acc4[4] = {0.0, 0.0, 0.0, 0.0};
+      double acc2[2] = {0.0, 0.0};
+      double2 d = make_double2(0.0, 0.0);
       const int use_x0 = sst.use_x0;
       if (use_x0) {
         InitEpi<V> epi = init_epi<V>(a);
         spmv_run<V, InitEpi<V>, NoGate, PGather, kPU>(a.A, a.x, epi, nullptr, nullptr);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) acc4[k] = epi.part[k];
+        acc2[0] = epi.part[0];
+        acc2[1] = epi.part[1];
+        d = epi.d;
       } else {
-        ph_init_zero<V>(a, acc4);
+        ph_init_zero<V>(a, acc2, d);
       }
+      double acc4[4] = {acc2[0], acc2[1], d.x, d.y};
       double tot[4];
       HELM_TOTAL(4, acc4, tot);
       if (threadIdx.x == 0) sc_init(&sst, tot, use_x0);

@@ -52,6 +52,7 @@ struct SellVals {
   int32_t* icol = nullptr;   // columns of the imaginary entries
   void* ival = nullptr;      // imaginary parts
   int32_t* ilen = nullptr;   // [n] imaginary entries per row
+  void* dval = nullptr;      // complex64 sets of a handle with a diagonal copy: real parts [ndia][n]
 };
 
 // complex128 Krylov vectors per handle (BiCGStab uses 6, TFQMR 8)
@@ -96,6 +97,10 @@ struct helm_csr_s {
   int64_t sell_entries = 0;            // stored entries including padding
   int32_t* sell_off = nullptr;         // [nsl + 1]
   int32_t* sell_col = nullptr;         // [sell_entries]
+  // diagonal copy of the pattern (complex64 products): every entry lies on
+  // one of ndia <= 32 diagonals col - row = dia_off[d] (ascending)
+  int32_t ndia = 0;
+  int32_t* dia_off = nullptr;
   helm::SellVals sv;                   // the caller's values (complex128 or complex64)
   helm::SellVals sv32;                 // the complex64 copy (mixed precision, complex128 handles)
   helm::SellVals svjac;                // A D^-1 (right Jacobi)

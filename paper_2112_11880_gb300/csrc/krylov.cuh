@@ -56,23 +56,34 @@ constexpr int32_t kModePlain = 0;
 constexpr int32_t kModeRefine = 1;
 constexpr int kInnerMax = 50000;  // inner iterations per refinement step at most
 
-// Every partial sum of a dot product or norm accumulates in FP64 (S, and
-// double2 for complex sums): for complex128 operands with the FP64 product
-// (4 or 2 FMA), for complex64 operands the product is formed in FP32 and
-// added in FP64 -- the complex64 kernels are HBM-bound and the FP64 pipe is
-// otherwise idle there, while an FP32 running sum over the ~10 rows a
-// thread takes on the 200x100x80 cavity visibly slowed the inner solves.
+// Per-thread partial sums of dot products and norms (S real, C complex)
+// accumulate in FP64: for complex128 operands the FP64 product (4 or 2 FMA),
+// for complex64 operands the product formed in FP32 and added in FP64.
+// Measured alternatives for complex64: an uncompensated FP32 running sum
+// over the ~10 rows a thread takes on the 200x100x80 cavity slowed the inner
+// solves of mixed precision visibly; a compensated (Kahan) FP32 sum made an
+// inner iteration 2-6 % faster on the 120x60x50 and 200x100x80 cavities, but
+// the 200x100x80 solve to 1e-10 then stalled (289,524 inner iterations, not
+// converged, against 188,207 to convergence with FP64 sums).
 template <class V> struct Prec;
 template <> struct Prec<double2> {
   using S = double;
+  using C = double2;
   __device__ static __forceinline__ double2 cvt(double2 z) { return z; }
+  __device__ static __forceinline__ S szero() { return 0.0; }
+  __device__ static __forceinline__ C czero() { return make_double2(0.0, 0.0); }
 };
 template <> struct Prec<float2> {
   using S = double;
+  using C = double2;
   __device__ static __forceinline__ float2 cvt(double2 z) {
     return make_float2(static_cast<float>(z.x), static_cast<float>(z.y));
   }
+  __device__ static __forceinline__ S szero() { return 0.0; }
+  __device__ static __forceinline__ C czero() { return make_double2(0.0, 0.0); }
 };
+__device__ __forceinline__ double to_d(double v) { return v; }
+__device__ __forceinline__ double2 to_d2(double2 v) { return v; }
 
 // acc + conj(a) b and acc + |a|^2 in the precision rules above
 __device__ __forceinline__ double2 dot_acc(double2 acc, double2 a, double2 b) { return cfma_conj(a, b, acc); }
@@ -331,7 +342,8 @@ __device__ __forceinline__ void sc_after_xr(SolverState* st, const double (&tot)
 
 // init without x0: x = 0, r = r^ = b, p = v = 0; (||b||^2, ||r||^2, (r^, r))
 template <class V>
-__device__ __forceinline__ void ph_init_zero(const KArgs<V>& a, typename Prec<V>::S (&acc)[4]) {
+__device__ __forceinline__ void ph_init_zero(const KArgs<V>& a, typename Prec<V>::S (&acc)[2],
+                                             typename Prec<V>::C& d) {
   const V z = vzero<V>();
   for (SliceRows q(a.A.n); q.active(); q.advance()) {
     const int32_t i = q.row();
@@ -343,9 +355,7 @@ __device__ __forceinline__ void ph_init_zero(const KArgs<V>& a, typename Prec<V>
     a.p[i] = z;
     a.v[i] = z;
     acc[0] = nrm_acc(acc[0], bi);
-    const double2 d = dot_acc(make_double2(acc[2], acc[3]), bi, bi);
-    acc[2] = d.x;
-    acc[3] = d.y;
+    d = dot_acc(d, bi, bi);
   }
   acc[1] = acc[0];
 }
@@ -355,7 +365,8 @@ template <class V>
 struct InitEpi {
   const V* b;
   V *r, *rh, *p, *v;
-  typename Prec<V>::S part[4];
+  typename Prec<V>::S part[2];
+  typename Prec<V>::C d;
   V bpre;
   __device__ __forceinline__ void prefetch(int32_t i) { bpre = b[i]; }
   __device__ __forceinline__ void row(int32_t i, V ax) {
@@ -367,15 +378,12 @@ struct InitEpi {
     v[i] = vzero<V>();
     part[0] = nrm_acc(part[0], bi);
     part[1] = nrm_acc(part[1], ri);
-    const double2 d = dot_acc(make_double2(part[2], part[3]), ri, ri);
-    part[2] = d.x;
-    part[3] = d.y;
+    d = dot_acc(d, ri, ri);
   }
 };
 template <class V>
 __device__ __forceinline__ InitEpi<V> init_epi(const KArgs<V>& a) {
-  using S = typename Prec<V>::S;
-  return InitEpi<V>{a.b, a.r, a.rh, a.p, a.v, {S(0), S(0), S(0), S(0)}, vzero<V>()};
+  return InitEpi<V>{a.b, a.r, a.rh, a.p, a.v, {Prec<V>::szero(), Prec<V>::szero()}, Prec<V>::czero(), vzero<V>()};
 }
 
 // P1: p = r + beta (p - omega v); the next row's loads are issued before
@@ -411,7 +419,7 @@ template <class V>
 struct VEpi {
   V* v;
   const V* rhp;
-  double2 part;
+  typename Prec<V>::C part;
   V rh;
   __device__ __forceinline__ void prefetch(int32_t i) { rh = rhp[i]; }
   __device__ __forceinline__ void row(int32_t i, V ax) {
@@ -421,14 +429,14 @@ struct VEpi {
 };
 template <class V>
 __device__ __forceinline__ VEpi<V> v_epi(const KArgs<V>& a) {
-  return VEpi<V>{a.v, a.rh, make_double2(0.0, 0.0), vzero<V>()};
+  return VEpi<V>{a.v, a.rh, Prec<V>::czero(), vzero<V>()};
 }
 
 // P3: s = r - alpha v, ||s||^2
 template <class V>
 __device__ __forceinline__ typename Prec<V>::S ph_s(const KArgs<V>& a, V alpha) {
   using S = typename Prec<V>::S;
-  S acc = S(0);
+  S acc = Prec<V>::szero();
   SliceRows q(a.A.n);
   int32_t i = q.row();
   if (!q.active() || i >= a.A.n) return acc;
@@ -459,8 +467,8 @@ template <class V>
 struct TEpi {
   V* t;
   const V* sp;
-  double2 ts;
-  double tt;
+  typename Prec<V>::C ts;
+  typename Prec<V>::S tt;
   V si;
   __device__ __forceinline__ void prefetch(int32_t i) { si = sp[i]; }
   __device__ __forceinline__ void row(int32_t i, V ax) {
@@ -471,13 +479,14 @@ struct TEpi {
 };
 template <class V>
 __device__ __forceinline__ TEpi<V> t_epi(const KArgs<V>& a) {
-  return TEpi<V>{a.t, a.s, make_double2(0.0, 0.0), 0.0, vzero<V>()};
+  return TEpi<V>{a.t, a.s, Prec<V>::czero(), Prec<V>::szero(), vzero<V>()};
 }
 
 // P5: x += alpha p + omega s, r = s - omega t; (r^, r), ||r||^2.  With
 // sconv (the solve stopped at s) only x += alpha p.
 template <class V>
-__device__ __forceinline__ void ph_xr(const KArgs<V>& a, V alpha, V omega, bool sconv, double2& rr, double& r2) {
+__device__ __forceinline__ void ph_xr(const KArgs<V>& a, V alpha, V omega, bool sconv, typename Prec<V>::C& rr,
+                                      typename Prec<V>::S& r2) {
   SliceRows q(a.A.n);
   int32_t i = q.row();
   if (!q.active() || i >= a.A.n) return;
@@ -522,19 +531,23 @@ __device__ __forceinline__ void ph_xr(const KArgs<V>& a, V alpha, V omega, bool 
 template <class V>
 __global__ void __launch_bounds__(kSolverThreads, kSolverMinBlocks) k_init(KArgs<V> a) {
   using S = typename Prec<V>::S;
+  using C = typename Prec<V>::C;
   __shared__ double red[32 * 4];
   SolverState* st = a.st;
   const int use_x0 = st->use_x0;
-  S acc[4] = {S(0), S(0), S(0), S(0)};
+  S acc[2] = {Prec<V>::szero(), Prec<V>::szero()};
+  C d = Prec<V>::czero();
   if (use_x0) {
     InitEpi<V> epi = init_epi<V>(a);
     spmv_run<V>(a.A, a.x, epi, nullptr, a.dev_err);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) acc[k] = epi.part[k];
+    acc[0] = epi.part[0];
+    acc[1] = epi.part[1];
+    d = epi.d;
   } else {
-    ph_init_zero<V>(a, acc);
+    ph_init_zero<V>(a, acc, d);
   }
-  double part[4] = {double(acc[0]), double(acc[1]), double(acc[2]), double(acc[3])};
+  const double2 dd = to_d2(d);
+  double part[4] = {to_d(acc[0]), to_d(acc[1]), dd.x, dd.y};
   double tot[4];
   if (!grid_total_last<4>(part, a.partials, a.tickets + TK_INIT, red, tot)) return;
   if (threadIdx.x != 0) return;
@@ -558,7 +571,8 @@ __global__ void __launch_bounds__(kSolverThreads, kSolverMinBlocks) k_v(KArgs<V>
   if (st->status != ST_RUNNING) return;
   VEpi<V> epi = v_epi<V>(a);
   spmv_run<V>(a.A, a.p, epi, nullptr, a.dev_err);
-  double part[2] = {double(epi.part.x), double(epi.part.y)};
+  const double2 pd = to_d2(epi.part);
+  double part[2] = {pd.x, pd.y};
   double tot[2];
   if (!grid_total_last<2>(part, a.partials, a.tickets + TK_V, red, tot)) return;
   if (threadIdx.x != 0) return;
@@ -571,7 +585,7 @@ __global__ void __launch_bounds__(kSolverThreads, kSolverMinBlocks) k_s(KArgs<V>
   __shared__ double red[32];
   SolverState* st = a.st;
   if (st->status != ST_RUNNING || refine_step_pending(st)) return;
-  double part[1] = {double(ph_s<V>(a, Prec<V>::cvt(st->alpha)))};
+  double part[1] = {to_d(ph_s<V>(a, Prec<V>::cvt(st->alpha)))};
   double tot[1];
   if (!grid_total_last<1>(part, a.partials, a.tickets + TK_S, red, tot)) return;
   if (threadIdx.x != 0) return;
@@ -587,7 +601,8 @@ __global__ void __launch_bounds__(kSolverThreads, kSolverMinBlocks) k_t(KArgs<V>
   if (st->status != ST_RUNNING || st->phase != PH_RUN || refine_step_pending(st)) return;
   TEpi<V> epi = t_epi<V>(a);
   spmv_run<V>(a.A, a.s, epi, nullptr, a.dev_err);
-  double part[3] = {double(epi.ts.x), double(epi.ts.y), double(epi.tt)};
+  const double2 tsd = to_d2(epi.ts);
+  double part[3] = {tsd.x, tsd.y, to_d(epi.tt)};
   double tot[3];
   if (!grid_total_last<3>(part, a.partials, a.tickets + TK_T, red, tot)) return;
   if (threadIdx.x != 0) return;
@@ -605,10 +620,11 @@ __global__ void __launch_bounds__(kSolverThreads, kSolverMinBlocks) k_xr(KArgs<V
     return;
   }
   if (refine_step_pending(st)) return;  // the mixed-precision graph body sets the condition itself
-  double2 rr = make_double2(0.0, 0.0);
-  double r2 = 0.0;
+  typename Prec<V>::C rr = Prec<V>::czero();
+  typename Prec<V>::S r2 = Prec<V>::szero();
   ph_xr<V>(a, Prec<V>::cvt(st->alpha), Prec<V>::cvt(st->omega), st->phase == PH_SCONV, rr, r2);
-  double part[3] = {double(rr.x), double(rr.y), double(r2)};
+  const double2 rrd = to_d2(rr);
+  double part[3] = {rrd.x, rrd.y, to_d(r2)};
   double tot[3];
   if (!grid_total_last<3>(part, a.partials, a.tickets + TK_XR, red, tot)) return;
   if (threadIdx.x != 0) return;

@@ -35,6 +35,9 @@
 // residual.
 // Graph: init (+ first inner start) -> while(5 FP32 kernels + 6 step
 // kernels) -> tail; the step kernels return at once when no step is due.
+// (A conditional IF node around the step kernels inside the WHILE body was
+// tried: adding it fails with cudaErrorInvalidValue on this CUDA 13.0 stack,
+// with its handle on the body or the top graph, with or without a default.)
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -445,11 +448,16 @@ void mx_fold(const RuArgs& a, const MxShapes& sh, int always, cudaStream_t s) {
   k_gcr_orth<<<sh.vec_grid, 256, 0, s>>>(a, always);
   k_gcr_xupd<<<sh.vec_grid, 256, 0, s>>>(a, always);
 }
-void mx_body(const RuArgs& a, const KArgs<float2>& k, const MxShapes& sh, cudaStream_t s) {
-  enqueue_body(k, sh.k, s);
+// the refinement step: fold the inner solution into x (GCR), the FP64
+// residual and a fresh inner start
+void mx_step(const RuArgs& a, const MxShapes& sh, cudaStream_t s) {
   mx_fold(a, sh, 0, s);
   k_mx_residual<<<sh.grid128, R128, kSmem128, s>>>(a);
   k_mx_restart<<<sh.vec_grid, 256, 0, s>>>(a);
+}
+void mx_body(const RuArgs& a, const KArgs<float2>& k, const MxShapes& sh, cudaStream_t s) {
+  enqueue_body(k, sh.k, s);
+  mx_step(a, sh, s);
 }
 void mx_tail(const RuArgs& a, const MxShapes& sh, cudaStream_t s) {
   mx_fold(a, sh, 1, s);

@@ -72,6 +72,9 @@ struct CsrDev {
   const int32_t* icol;
   const R* ival;
   const int32_t* ilen;    // [n] imaginary entries per row (read only in slices that have some)
+  int32_t ndia;           // complex64 with a diagonal copy: the real parts on ndia diagonals, else 0
+  const int32_t* doff;    // [ndia] ascending offsets col - row
+  const R* dval;          // [ndia][n] real part of entry (r, r + doff[d]), 0 where none
 };
 
 template <class V> __device__ __forceinline__ V vzero();
@@ -218,6 +221,46 @@ struct SliceRows {
   __device__ __forceinline__ int32_t row() const { return s * 32 + lane; }
 };
 
+// Row r of a complex64 matrix with a diagonal copy: the real parts from the
+// diagonals, in ascending column order (the CSR order of a sorted row), then
+// the row's imaginary entries as in sell_row.  Every diagonal's value and
+// gather are loaded independently of one another (no load waits on another
+// one); a diagonal without an entry in this row (value 0) leaves the sum
+// untouched, so the result is that of sell_row for finite x.  The complex64
+// product is bound by HBM on this GPU (its arithmetic is FP32): the diagonal
+// copy reads 4 bytes per stored real part and no column index, against 8
+// for the sliced copy.
+template <class G = GatherReadOnly>
+__device__ __forceinline__ float2 dia_row(const CsrDev<float2>& A, int32_t s, int lane, int32_t r, const float2* x) {
+  float2 acc = make_float2(0.f, 0.f);
+  if (r < A.n) {
+    const float* dv = A.dval + r;
+#pragma unroll 9
+    for (int32_t d = 0; d < A.ndia; ++d) {
+      const int32_t j = r + __ldg(A.doff + d);
+      const float a = __ldcs(dv + static_cast<size_t>(d) * A.n);
+      float2 xv = make_float2(0.f, 0.f);
+      if (static_cast<uint32_t>(j) < static_cast<uint32_t>(A.n)) xv = G::ld(x + j);
+      const float sx = fmaf(a, xv.x, acc.x), sy = fmaf(a, xv.y, acc.y);
+      const bool nz = a != 0.f;
+      acc.x = nz ? sx : acc.x;
+      acc.y = nz ? sy : acc.y;
+    }
+  }
+  const int32_t ib = A.isoff[s];
+  const int32_t iw = (A.isoff[s + 1] - ib) >> 5;
+  if (iw > 0) {
+    const int32_t il = r < A.n ? A.ilen[r] : 0;
+    for (int32_t q = 0; q < iw; ++q) {
+      if (q < il) {
+        const float b = A.ival[ib + q * 32 + lane];
+        acc = mac_imag(b, G::ld(x + A.icol[ib + q * 32 + lane]), acc);
+      }
+    }
+  }
+  return acc;
+}
+
 struct NoGate {
   __device__ __forceinline__ bool operator()() const { return true; }
 };
@@ -240,7 +283,13 @@ __device__ __forceinline__ bool spmv_run(const CsrDev<V>& A, const V* __restrict
       len = A.rowptr[r + 1] - A.rowptr[r];
       epi.prefetch(r);
     }
-    const V acc = sell_row<V, G, U>(A, q.s, q.lane, r, len, x);
+    V acc;
+    if constexpr (std::is_same<V, float2>::value) {
+      if (A.ndia > 0) acc = dia_row<G>(A, q.s, q.lane, r, x);
+      else acc = sell_row<V, G, U>(A, q.s, q.lane, r, len, x);
+    } else {
+      acc = sell_row<V, G, U>(A, q.s, q.lane, r, len, x);
+    }
     if (r < A.n) epi.row(r, acc);
   }
   return true;
@@ -263,11 +312,13 @@ template <class V> struct Engine {
 template <class V>
 inline CsrDev<V> csr_dev(const helm_csr_s* A, const V* vals, const SellVals& sv) {
   using R = typename RealOf<V>::T;
+  const bool dia = sv.dval != nullptr && A->ndia > 0;
   return CsrDev<V>{A->n,        A->nnz,   A->rowptr,
                    A->colind,   vals,     A->nsl,
                    A->sell_off, A->sell_col, static_cast<const R*>(sv.sval),
                    sv.isoff,    sv.icol,  static_cast<const R*>(sv.ival),
-                   sv.ilen};
+                   sv.ilen,     dia ? A->ndia : 0, dia ? A->dia_off : nullptr,
+                   dia ? static_cast<const R*>(sv.dval) : nullptr};
 }
 
 }  // namespace helm

@@ -201,6 +201,103 @@ def test_axpby_complex64_and_aliased(alpha, beta):
     assert np.all(np.abs(zd.cpu().numpy() - ref) <= 4e-16 * scale + 1e-300)
 
 
+def _banded_csr(n, offsets, drop, seed):
+    """A matrix on the given diagonals with a fraction `drop` of the
+    off-diagonal slots left out (empty slots of the diagonal copy)."""
+    rng = np.random.default_rng(seed)
+    rp, ci, vv = [0], [], []
+    for i in range(n):
+        for d in offsets:
+            j = i + d
+            if 0 <= j < n and (d == 0 or rng.random() >= drop):
+                ci.append(j)
+                vv.append(complex(rng.uniform(-1, 1), rng.uniform(-1, 1) if rng.random() < 0.2 else 0.0))
+        rp.append(len(ci))
+    return np.array(rp, np.int32), np.array(ci, np.int32), np.array(vv, np.complex128)
+
+
+def _dia_cases():
+    out = {"box20": MATS["box20"]}  # n = 9261: a partial last slice of 13 rows
+    p = g.assemble(g.tiny_config(20, 16, 12, h=0.05, seed=3))  # n = 4641: a last slice of one row
+    out["mesh4641"] = (p.rowptr, p.colind, g.helmholtz_values(p, 600.0))
+    out["banded"] = _banded_csr(1003, [-40, -3, -1, 0, 1, 2, 17, 333], 0.1, 9)
+    return out
+
+
+DIA = _dia_cases()
+
+
+@pytest.mark.parametrize("name", list(DIA))
+def test_spmv_c64_diagonal_copy_matches_sliced(name):
+    """complex64 matrices on few diagonals get a diagonal copy: the product
+    equals the sliced copy's bit for bit (same FP32 operations in column
+    order, empty slots skipped; also with an Inf in x next to a row that has
+    no entry there) and meets the complex64 gate against the oracle."""
+    rp, ci, v = DIA[name]
+    n = len(rp) - 1
+    v32 = v.astype(np.complex64)
+    A = helm.CsrMatrix.from_host(rp, ci, v32, device=DEV)
+    B = helm.CsrMatrix.from_host(rp, ci, v32, device=DEV, sliced_only=True)
+    assert A.diagonals() > 0 and B.diagonals() == 0
+    x32 = g.complex_vector(n, 13).astype(np.complex64)
+    ya = A.matvec(_dev(x32))
+    yb = B.matvec(_dev(x32))
+    assert torch.equal(torch.view_as_real(ya), torch.view_as_real(yb))
+    y = ya.cpu().numpy().astype(np.complex128)
+    ref = oracle.spmv(rp, ci, v32.astype(np.complex128), x32.astype(np.complex128))
+    scale = _abs_scale(rp, ci, v32.astype(np.complex128), x32.astype(np.complex128))
+    assert np.all(np.abs(y - ref) <= (np.diff(rp) + 2) * 2 * U32 * scale + 1e-30)
+    y0 = g.complex_vector(n, 14).astype(np.complex64)
+    ya, yb = _dev(y0.copy()), _dev(y0.copy())
+    A.matvec(_dev(x32), ya, alpha=0.5 - 2j, beta=1 + 1j)
+    B.matvec(_dev(x32), yb, alpha=0.5 - 2j, beta=1 + 1j)
+    assert torch.equal(torch.view_as_real(ya), torch.view_as_real(yb))
+    # an Inf in x at a column that some row's diagonal slot covers without an entry
+    rows_with = set(np.repeat(np.arange(n), np.diff(rp))[ci == 1].tolist())
+    if len(rows_with) < n:
+        xi = x32.copy()
+        xi[1] = np.inf
+        ya, yb = A.matvec(_dev(xi)).cpu().numpy(), B.matvec(_dev(xi)).cpu().numpy()
+        assert np.array_equal(ya, yb, equal_nan=True)
+        assert np.all(np.isfinite(ya[[i for i in range(n) if i not in rows_with]]))
+    A.close()
+    B.close()
+
+
+def test_diagonal_copy_only_where_it_fits():
+    """No diagonal copy for a pattern off its longest row's diagonals, or one
+    whose diagonals would hold more than 1.5 slots per entry (a small mesh,
+    mostly boundary; a band with half its slots empty)."""
+    rp, ci, v = MATS["ragged"]
+    A = helm.CsrMatrix.from_host(rp, ci, v.astype(np.complex64), device=DEV)
+    assert A.diagonals() == 0
+    A.close()
+    for rp, ci, v in (_banded_csr(500, [-7, -1, 0, 1, 7], 0.6, 4), MATS["tiny"]):
+        A = helm.CsrMatrix.from_host(rp, ci, v.astype(np.complex64), device=DEV)
+        assert A.diagonals() == 0
+        A.close()
+
+
+def test_mixed_solve_same_with_and_without_diagonal_copy():
+    """The complex64 inner solves of mixed precision read the diagonal copy
+    of the handle's complex64 values; the whole solve matches a handle
+    without it bit for bit."""
+    p = g.assemble(g.CONFIGS["box20"])
+    vals = g.helmholtz_values(p, 1500.0)
+    b = _dev(g.source(p))
+    out = []
+    for sliced in (False, True):
+        A = helm.CsrMatrix.from_host(p.rowptr, p.colind, vals, device=DEV, sliced_only=sliced)
+        assert (A.diagonals() > 0) != sliced
+        x, info = helm.solve(A, b, tol=1e-8, maxit=20000, precision=helm.HELM_PREC_MIXED)
+        assert info["status"] == "ok", info
+        out.append((x, info))
+        A.close()
+    (xa, ia), (xb, ib) = out
+    assert torch.equal(torch.view_as_real(xa), torch.view_as_real(xb))
+    assert ia["iters"] == ib["iters"] and ia["relres_true"] == ib["relres_true"]
+
+
 def test_invalid_arguments_rejected():
     rp, ci, v = MATS["tiny"]
     bad = ci.copy()
