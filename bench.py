@@ -404,6 +404,15 @@ def extension_summary(dev, args):
     infos, dt = timed(lambda: [helm.helm_bicgstab_solve(A.handle, b, x, o) for _ in range(reps)])
     out["box20"] = {"solves_per_s": round(reps / dt, 3), "iters": infos[-1]["iters"],
                     "relres_true": infos[-1]["relres_true"], "status": infos[-1]["status"]}
+    # Schwarz decomposition of the same system: 4 slabs, one plane of overlap,
+    # impedance term, the subdomain solves batched (GCR over 256 directions)
+    S = helm.Ddm(A, 4, (cfg.nx + 1) * (cfg.ny + 1), window=256)
+    (xd, idd), t_ddm = timed(lambda: S.solve(b, tol=cfg.tol, maxit=1000, inner_tol=1e-2))
+    S.close()
+    out["box20"]["ddm"] = {"subdomains": 4, "overlap_planes": 1, "inner_tol": 1e-2, "s": round(t_ddm, 3),
+                           "vs_bicgstab": round((dt / reps) / t_ddm, 3), "outer_steps": idd["iters"],
+                           "inner_iters": (idd["spmv_count"] - idd["iters"]) // 2, "status": idd["status"],
+                           "relres_true": idd["relres_true"]}
     A.close()
 
     # config 4

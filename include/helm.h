@@ -436,6 +436,68 @@ helm_status helm_sweep_spmv(helm_sweep S, int32_t nfreq, const double* h_omega, 
                             void* d_Y, int32_t ldy, helm_stream_t stream);
 
 /* helm_status_string -- static description of a status code. */
+/*
+ * Schwarz domain decomposition with the subdomain solves batched on one GPU
+ * (the route of Section 4's closing remarks for problems beyond one GPU,
+ * here with all subdomains on the same device).
+ *
+ * helm_ddm_create -- split the rows of A (complex128 handle, borrowed: it
+ * must outlive the decomposition) into nsub contiguous blocks of near-equal
+ * size [s_p, e_p) = [p n / nsub, (p + 1) n / nsub), extend each by `overlap`
+ * rows on both sides (clamped to [0, n)), and build on the device the
+ * block-diagonal matrix D = diag(A_1, ..., A_nsub) of the subdomain matrices
+ * A_p, with its own handle (so one solve of D is the batch of all subdomain
+ * solves).  A_p is the principal submatrix of A on the extended block; with
+ * flags HELM_DDM_IMPEDANCE every row of it that couples to rows outside the
+ * block gets i sum_{j outside} |a_ij| added to its (stored) diagonal, an
+ * absorbing condition on the artificial boundary (the algebraic form of
+ * optimized Schwarz methods; plain principal submatrices stall on
+ * indefinite Helmholtz systems).  For a structured mesh in its natural
+ * numbering the blocks are slabs of node planes and an overlap of k planes
+ * is k times the plane size.  window: GCR directions helm_ddm_solve keeps
+ * (1..512; 2 window + 4 complex128 vectors of length n are allocated).
+ * 1 <= nsub <= n, overlap >= 0, flags 0 or HELM_DDM_IMPEDANCE;
+ * HELM_ERR_INVALID otherwise or when D would hold 2^31 rows or entries or
+ * more.  Synchronises `stream`.
+ */
+typedef struct helm_ddm_s* helm_ddm; /* opaque */
+#define HELM_DDM_IMPEDANCE 1u
+helm_status helm_ddm_create(helm_ddm* out, helm_csr A, int32_t nsub, int32_t overlap, int32_t window,
+                            uint32_t flags, helm_stream_t stream);
+helm_status helm_ddm_destroy(helm_ddm S);
+
+/* helm_ddm_subdomains -- *rows = rows of D (the sum of the extended block
+ * sizes), *nnz = its entries; either pointer may be NULL. */
+helm_status helm_ddm_subdomains(helm_ddm S, int32_t* rows, int64_t* nnz);
+
+/*
+ * helm_ddm_apply -- d_z = M d_r, the restricted additive Schwarz
+ * preconditioner (Cai & Sarkis 1999): M r = sum_p Rt_p^T A_p^{-1} R_p r, R_p
+ * the restriction to the extended block p, Rt_p^T the prolongation that keeps
+ * the rows of the block p owns; the A_p^{-1} together as one BiCGStab solve
+ * of D to a relative residual inner_tol (at most 5000 iterations; 0 asks for
+ * the tightest it reaches).  d_r, d_z: complex128[n], distinct.  Synchronises
+ * `stream`.
+ */
+helm_status helm_ddm_apply(helm_ddm S, const void* d_r, void* d_z, double inner_tol,
+                           helm_stream_t stream);
+
+/*
+ * helm_ddm_solve -- A x = b by GCR (the last `window` directions kept, the
+ * minimal-residual step over them) preconditioned by helm_ddm_apply:
+ * flexible, since each application's inner solve stops at its own
+ * tolerance.  o: tol (as for helm_bicgstab_solve: HELM_OK only with the
+ * recomputed true residual at most tol; a recurrence that met tol without it
+ * starts the window again from the true residual), maxit (outer steps),
+ * use_x0, inner_tol (the subdomain solves' relative residual, default 1e-3),
+ * deadline_s (host wall clock); the other fields are ignored.  info: iters =
+ * outer steps, restarts = window restarts, spmv_count = products with A plus
+ * two per inner iteration (products with D).  The outer loop runs on the
+ * host; synchronises `stream`.
+ */
+helm_status helm_ddm_solve(helm_ddm S, const void* d_b, void* d_x, const helm_opts* o,
+                           helm_info* info, helm_stream_t stream);
+
 const char* helm_status_string(helm_status s);
 
 #ifdef __cplusplus

@@ -182,6 +182,38 @@ def jacobi_solve(method, rowptr, colind, vals, b, **kw):
     return dinv * y, info
 
 
+def ddm_blocks(n: int, nsub: int, overlap: int):
+    """The decomposition of helm_ddm_create written out: owned blocks
+    [p n / nsub, (p + 1) n / nsub) and their extensions by `overlap` rows on
+    both sides, clamped to [0, n).  Returns [(s, e, a, b)]."""
+    out = []
+    for p in range(nsub):
+        s, e = p * n // nsub, (p + 1) * n // nsub
+        out.append((s, e, max(0, s - overlap), min(n, e + overlap)))
+    return out
+
+
+def ras_apply(rowptr, colind, vals, r, nsub: int, overlap: int, impedance: bool = False) -> np.ndarray:
+    """Restricted additive Schwarz (Cai & Sarkis 1999) by its definition,
+    z = sum_p Rt_p^T A_p^{-1} R_p r, with A_p the principal submatrix of A on
+    the extended block p (dense LAPACK solves; small matrices only) and Rt_p^T
+    keeping the rows block p owns.  impedance: A_p's rows that couple to rows
+    outside the block get i sum_{j outside} |a_ij| on their diagonal (an
+    absorbing condition on the artificial boundary)."""
+    Ad = densify(rowptr, colind, vals)
+    n = Ad.shape[0]
+    r = np.asarray(r, dtype=np.complex128)
+    z = np.zeros(n, dtype=np.complex128)
+    for s, e, a, b in ddm_blocks(n, nsub, overlap):
+        Ap = Ad[a:b, a:b].copy()
+        if impedance:
+            lost = np.abs(Ad[a:b, :a]).sum(axis=1) + np.abs(Ad[a:b, b:]).sum(axis=1)
+            Ap[np.arange(b - a), np.arange(b - a)] += 1j * lost
+        y = np.linalg.solve(Ap, r[a:b])
+        z[s:e] = y[s - a:e - a]
+    return z
+
+
 def helmholtz_values(K, Mc, Bc, w: float) -> np.ndarray:
     """A(w) = K - w^2 M_c + i w B_c entry by entry (the frequency-dependent
     system of the Helmholtz problem of Section 1 with the impedance term)."""

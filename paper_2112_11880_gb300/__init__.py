@@ -34,6 +34,7 @@ HELM_C128 = 0
 HELM_C64 = 1
 HELM_CSR_VALIDATE = 1
 HELM_CSR_SLICED_ONLY = 2
+HELM_DDM_IMPEDANCE = 1
 
 HELM_BICGSTAB = 0
 HELM_TFQMR = 1
@@ -96,6 +97,12 @@ SIGNATURES = {
     "helm_sweep_solve": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, ctypes.c_int32, _P, ctypes.c_int32,
                                         ctypes.POINTER(helm_opts), _P, _P]),
     "helm_sweep_spmv": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, ctypes.c_int32, _P, ctypes.c_int32, _P]),
+    "helm_ddm_create": (ctypes.c_int, [ctypes.POINTER(_P), _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_uint32, _P]),
+    "helm_ddm_destroy": (ctypes.c_int, [_P]),
+    "helm_ddm_subdomains": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)]),
+    "helm_ddm_apply": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, _P]),
+    "helm_ddm_solve": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(helm_opts), ctypes.POINTER(helm_info), _P]),
 }
 
 _lib = None
@@ -330,6 +337,62 @@ def helm_sweep_solve(handle, omegas, b, X, opts: Optional[helm_opts] = None, str
     if st in (HELM_ERR_INVALID, HELM_ERR_CUDA, HELM_ERR_NOMEM):
         raise HelmError(st, "helm_sweep_solve")
     return [infos[j].as_dict() for j in range(F)]
+
+
+class Ddm:
+    """Schwarz decomposition of a CsrMatrix into `nsub` overlapping row
+    blocks, the subdomain solves batched (see helm_ddm_create)."""
+
+    def __init__(self, A, nsub: int, overlap: int, window: int = 256, impedance: bool = True, stream=None):
+        self.A = A  # the handle borrows A
+        h = _P()
+        _check(load_library().helm_ddm_create(ctypes.byref(h), A.handle, int(nsub), int(overlap), int(window),
+                                              HELM_DDM_IMPEDANCE if impedance else 0, _stream(stream)),
+               "helm_ddm_create")
+        self.handle = h.value
+        self.n = A.n
+
+    def subdomains(self):
+        rows, nnz = ctypes.c_int32(0), ctypes.c_int64(0)
+        _check(load_library().helm_ddm_subdomains(self.handle, ctypes.byref(rows), ctypes.byref(nnz)),
+               "helm_ddm_subdomains")
+        return rows.value, nnz.value
+
+    def apply(self, r, z=None, inner_tol: float = 1e-3, stream=None):
+        """z = M r, the restricted additive Schwarz preconditioner."""
+        import torch
+        _check_vector(r, self.n, torch.complex128, "r")
+        if z is None:
+            z = torch.empty_like(r)
+        _check_vector(z, self.n, torch.complex128, "z")
+        _check(load_library().helm_ddm_apply(self.handle, _ptr(r), _ptr(z), float(inner_tol), _stream(stream)),
+               "helm_ddm_apply")
+        return z
+
+    def solve(self, b, x=None, stream=None, **opts):
+        import torch
+        _check_vector(b, self.n, torch.complex128, "b")
+        if x is None:
+            x = torch.zeros_like(b)
+        _check_vector(x, self.n, torch.complex128, "x")
+        info = helm_info()
+        o = default_opts(**opts)
+        st = load_library().helm_ddm_solve(self.handle, _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(info),
+                                           _stream(stream))
+        if st in (HELM_ERR_INVALID, HELM_ERR_CUDA, HELM_ERR_NOMEM):
+            raise HelmError(st, "helm_ddm_solve")
+        return x, info.as_dict()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load_library().helm_ddm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Sweep:

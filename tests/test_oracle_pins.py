@@ -561,3 +561,63 @@ def test_jacobi_solve_matches_dense_lu(method):
         assert r <= 2e-12
         cond = np.linalg.cond(oracle.densify(p.rowptr, p.colind, vals))
         assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= 10 * cond * 1e-12
+
+
+# ---------------------------------------------------------------- restricted additive Schwarz
+
+def _csr_of_dense(D):
+    rp, ci, vv = [0], [], []
+    for i in range(D.shape[0]):
+        nz = np.nonzero(D[i])[0]
+        ci.extend(nz.tolist())
+        vv.extend(D[i, nz].tolist())
+        rp.append(len(ci))
+    return np.array(rp, np.int32), np.array(ci, np.int32), np.array(vv, np.complex128)
+
+
+def test_ras_closed_form_on_a_tridiagonal_matrix():
+    """tridiag(-1, 2, -1) of order 4, two blocks, overlap 1: the extended
+    blocks are rows 0-2 and 1-3, each the 3x3 matrix whose inverse is
+    [[3, 2, 1], [2, 4, 2], [1, 2, 3]] / 4.  For r = e_1 block 0 keeps rows 0, 1
+    of (2, 4, 2) / 4 and block 1 rows 1, 2 (its rows 2, 3 of A) of
+    (3, 2, 1) / 4: z = (1/2, 1, 1/2, 1/4)."""
+    T = 2 * np.eye(4) - np.eye(4, k=1) - np.eye(4, k=-1)
+    rp, ci, vv = _csr_of_dense(T.astype(np.complex128))
+    z = oracle.ras_apply(rp, ci, vv, np.array([0, 1, 0, 0], np.complex128), nsub=2, overlap=1)
+    assert np.allclose(z, [0.5, 1.0, 0.5, 0.25], rtol=0, atol=1e-15)
+    assert oracle.ddm_blocks(4, 2, 1) == [(0, 2, 0, 3), (2, 4, 1, 4)]
+    # with the impedance term: block 0's row 2 loses |a_23| = 1, block 1's
+    # first row (row 1 of A) loses |a_10| = 1, so the blocks are
+    # [[2,-1,0],[-1,2,-1],[0,-1,2+i]] and [[2+i,-1,0],[-1,2,-1],[0,-1,2]];
+    # solving them by hand gives y = (11-2i, 22-4i, .)/25 and (., 8-6i, 4-3i)/25
+    z = oracle.ras_apply(rp, ci, vv, np.array([0, 1, 0, 0], np.complex128), nsub=2, overlap=1, impedance=True)
+    assert np.allclose(z, np.array([11 - 2j, 22 - 4j, 8 - 6j, 4 - 3j]) / 25, rtol=0, atol=1e-15)
+    assert oracle.ddm_blocks(10, 3, 2) == [(0, 3, 0, 5), (3, 6, 1, 8), (6, 10, 4, 10)]
+
+
+def test_ras_is_the_inverse_where_the_blocks_do_not_couple():
+    """One block (any overlap), or a block-diagonal matrix split along its
+    blocks (any overlap): the restricted additive Schwarz operator is A^-1
+    itself, with or without the impedance term (no row loses a coupling).
+    And it is linear in r."""
+    p = g.assemble(g.tiny_config(3, 3, 2, h=0.1, seed=4))
+    vals = g.helmholtz_values(p, 500.0)
+    r = g.complex_vector(p.n, 30)
+    xs = oracle.dense_solve(p.rowptr, p.colind, vals, r)
+    for ov in (0, 3, 100):
+        assert np.allclose(oracle.ras_apply(p.rowptr, p.colind, vals, r, 1, ov), xs, rtol=1e-12, atol=0)
+    A = oracle.densify(p.rowptr, p.colind, vals)
+    B = np.zeros((2 * p.n, 2 * p.n), np.complex128)
+    B[:p.n, :p.n] = A
+    B[p.n:, p.n:] = 2.0 * A
+    rp, ci, vv = _csr_of_dense(B)
+    r2 = g.complex_vector(2 * p.n, 31)
+    exact = np.linalg.solve(B, r2)
+    for ov in (0, 5):
+        assert np.allclose(oracle.ras_apply(rp, ci, vv, r2, 2, 0), exact, rtol=1e-12, atol=0)
+        assert np.allclose(oracle.ras_apply(rp, ci, vv, r2, 2, 0, impedance=True), exact, rtol=1e-12, atol=0)
+        assert np.allclose(oracle.ras_apply(rp, ci, vv, r2, 2, ov), exact, rtol=1e-12, atol=0)
+    ra = oracle.ras_apply(p.rowptr, p.colind, vals, r, 3, 4)
+    rb = oracle.ras_apply(p.rowptr, p.colind, vals, 2j * r + xs, 3, 4)
+    rc = oracle.ras_apply(p.rowptr, p.colind, vals, xs, 3, 4)
+    assert np.allclose(rb, 2j * ra + rc, rtol=1e-12, atol=1e-14 * np.abs(rb).max())
