@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(kSolverThreads, kSolverMinBlocks) k_bicgstab_p
         __syncthreads();
         if (sst.status != ST_RUNNING) break;
       }
-      // P5 (+ block 0's deadline verdict as a fourth sum)
+      // P5 (+ block 0's deadline decision as a fourth sum)
       {
         double2 rr = make_double2(0.0, 0.0);
         double r2 = 0.0;
