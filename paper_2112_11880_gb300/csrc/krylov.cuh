@@ -559,7 +559,7 @@ __global__ void __launch_bounds__(kSolverThreads, kSolverMinBlocks) k_init(KArgs
 template <class V>
 __global__ void __launch_bounds__(kSolverThreads, kSolverMinBlocks) k_p(KArgs<V> a) {
   const SolverState* st = a.st;
-  if (st->status != ST_RUNNING) return;
+  if (st->status != ST_RUNNING || refine_step_pending(st)) return;
   ph_p<V>(a, Prec<V>::cvt(st->beta), Prec<V>::cvt(st->omega));
 }
 
@@ -568,7 +568,7 @@ template <class V>
 __global__ void __launch_bounds__(kSolverThreads, kSolverMinBlocks) k_v(KArgs<V> a) {
   __shared__ double red[32 * 2];
   SolverState* st = a.st;
-  if (st->status != ST_RUNNING) return;
+  if (st->status != ST_RUNNING || refine_step_pending(st)) return;
   VEpi<V> epi = v_epi<V>(a);
   spmv_run<V>(a.A, a.p, epi, nullptr, a.dev_err);
   const double2 pd = to_d2(epi.part);
@@ -619,7 +619,10 @@ __global__ void __launch_bounds__(kSolverThreads, kSolverMinBlocks) k_xr(KArgs<V
     if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(a, false);
     return;
   }
-  if (refine_step_pending(st)) return;  // the mixed-precision graph body sets the condition itself
+  if (refine_step_pending(st)) {  // mixed precision: the inner loop ends for the refinement step
+    if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(a, false);
+    return;
+  }
   typename Prec<V>::C rr = Prec<V>::czero();
   typename Prec<V>::S r2 = Prec<V>::szero();
   ph_xr<V>(a, Prec<V>::cvt(st->alpha), Prec<V>::cvt(st->omega), st->phase == PH_SCONV, rr, r2);
@@ -629,7 +632,7 @@ __global__ void __launch_bounds__(kSolverThreads, kSolverMinBlocks) k_xr(KArgs<V
   if (!grid_total_last<3>(part, a.partials, a.tickets + TK_XR, red, tot)) return;
   if (threadIdx.x != 0) return;
   sc_after_xr(st, tot, deadline_passed(st));
-  set_cond(a, st->status == ST_RUNNING);
+  set_cond(a, st->status == ST_RUNNING && !refine_step_pending(st));
 }
 
 // Solver grid: one wave of the solver kernels -- the blocks that fit on every

@@ -33,11 +33,17 @@
 // converged slowly and, folded without a step length, diverged whenever an
 // inner solve stagnated.  The convergence test is always the FP64 true
 // residual.
-// Graph: init (+ first inner start) -> while(5 FP32 kernels + 6 step
-// kernels) -> tail; the step kernels return at once when no step is due.
-// (A conditional IF node around the step kernels inside the WHILE body was
-// tried: adding it fails with cudaErrorInvalidValue on this CUDA 13.0 stack,
-// with its handle on the body or the top graph, with or without a default.)
+// Launch structure: init (+ first inner start); then per refinement step one
+// launch of the inner graph (a conditional WHILE over the 5 complex64
+// kernels, which ends when a step is due or the solve stops) and one of the
+// step graph (its 6 kernels), the host reading the state between steps; then
+// the tail.  An inner iteration so launches its five kernels and nothing
+// else (with the step kernels inside the loop body, returning at once when
+// no step is due, an inner iteration cost 84.5 instead of 76.1 us on
+// the 120x60x50 cavity).  A conditional IF node around the step kernels
+// inside the WHILE body was tried first: adding it fails with
+// cudaErrorInvalidValue on this CUDA 13.0 stack (handle on the body or the
+// top graph, with or without a default).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -459,6 +465,73 @@ void mx_body(const RuArgs& a, const KArgs<float2>& k, const MxShapes& sh, cudaSt
   enqueue_body(k, sh.k, s);
   mx_step(a, sh, s);
 }
+// A graph of one conditional WHILE node whose body is body(cond, stream).
+template <class Body>
+helm_status build_loop_graph(Body body, GraphEntry* out) {
+  cudaStream_t cs = nullptr;
+  HELM_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  helm_status result = HELM_ERR_CUDA;
+  do {
+    if (cudaGraphCreate(&graph, 0) != cudaSuccess) break;
+    cudaGraphConditionalHandle cond;
+    if (cudaGraphConditionalHandleCreate(&cond, graph, 1u, cudaGraphCondAssignDefault) != cudaSuccess) break;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    if (cudaGraphAddNode(&wnode, graph, nullptr, nullptr, 0, &cp) != cudaSuccess) break;
+    cudaGraph_t tmp = nullptr;
+    if (cudaStreamBeginCaptureToGraph(cs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      break;
+    for (int u = 0; u < kBodyUnroll; ++u) body(cond, cs);
+    if (cudaStreamEndCapture(cs, &tmp) != cudaSuccess) break;
+    if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) break;
+    result = HELM_OK;
+  } while (false);
+  cudaStreamDestroy(cs);
+  if (result != HELM_OK) {
+    (void)cudaGetLastError();
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    return result;
+  }
+  out->exec = exec;
+  out->graph = graph;
+  return HELM_OK;
+}
+
+// A graph of the kernels fn(stream) enqueues (stream capture).
+template <class Fn>
+helm_status build_plain_graph(Fn fn, GraphEntry* out) {
+  cudaStream_t cs = nullptr;
+  HELM_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  helm_status result = HELM_ERR_CUDA;
+  do {
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) break;
+    fn(cs);
+    if (cudaStreamEndCapture(cs, &graph) != cudaSuccess || !graph) break;
+    if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) break;
+    result = HELM_OK;
+  } while (false);
+  cudaStreamDestroy(cs);
+  if (result != HELM_OK) {
+    (void)cudaGetLastError();
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    return result;
+  }
+  out->exec = exec;
+  out->graph = graph;
+  return HELM_OK;
+}
+
 void mx_tail(const RuArgs& a, const MxShapes& sh, cudaStream_t s) {
   mx_fold(a, sh, 1, s);
   k_mx_tail<<<sh.grid128, R128, kSmem128, s>>>(a);
@@ -529,54 +602,59 @@ helm_status solve_mixed(helm_csr A, const double2* b, double2* x, const helm_opt
   a.tickets = A->tickets;
   a.dev_err = A->dev_err;
 
-  // graph per (b, x), tagged as mixed in the cache key
-  GraphEntry* g = nullptr;
-  auto key = graph_key(b, x, 2, o);
-  auto it = A->graphs.find(key);
-  if (o.launch == HELM_LAUNCH_HOST) {
-  } else if (it != A->graphs.end()) {
-    g = &it->second;
-  } else {
-    auto wa = [&](cudaGraphConditionalHandle c) {
-      RuArgs r = a;
-      r.cond = c;
-      r.has_cond = 1;
-      return r;
-    };
-    auto wk = [&](cudaGraphConditionalHandle c) {
-      KArgs<float2> kk = k;
-      kk.cond = c;
-      kk.has_cond = 1;
-      return kk;
-    };
-    GraphEntry e;
-    if (build_while_graph([&](cudaGraphConditionalHandle c, cudaStream_t cs) { mx_init(wa(c), sh, cs); },
-                          [&](cudaGraphConditionalHandle c, cudaStream_t cs) { mx_body(wa(c), wk(c), sh, cs); },
-                          [&](cudaGraphConditionalHandle c, cudaStream_t cs) { mx_tail(wa(c), sh, cs); },
-                          &e) == HELM_OK)
-      g = &(A->graphs[key] = e);
+  // the inner-loop graph and the step graph per (b, x), tagged as mixed in
+  // the cache key
+  GraphEntry* gi = nullptr;
+  GraphEntry* gs = nullptr;
+  if (o.launch != HELM_LAUNCH_HOST) {
+    auto ki = graph_key(b, x, 2, o), ks = graph_key(b, x, 3, o);
+    auto ii = A->graphs.find(ki), is = A->graphs.find(ks);
+    if (ii != A->graphs.end() && is != A->graphs.end()) {
+      gi = &ii->second;
+      gs = &is->second;
+    } else {
+      GraphEntry ei, es;
+      const bool ok_i = build_loop_graph(
+                            [&](cudaGraphConditionalHandle c, cudaStream_t cs) {
+                              KArgs<float2> kk = k;
+                              kk.cond = c;
+                              kk.has_cond = 1;
+                              enqueue_body(kk, sh.k, cs);
+                            },
+                            &ei) == HELM_OK;
+      const bool ok_s = ok_i && build_plain_graph([&](cudaStream_t cs) { mx_step(a, sh, cs); }, &es) == HELM_OK;
+      if (ok_i && ok_s) {
+        gi = &(A->graphs[ki] = ei);
+        gs = &(A->graphs[ks] = es);
+      } else {
+        if (ei.exec) cudaGraphExecDestroy(ei.exec);
+        if (ei.graph) cudaGraphDestroy(ei.graph);
+      }
+    }
   }
 
   // an explicit graph request does not fall back to the host-driven loop
-  if (!g && o.launch == HELM_LAUNCH_GRAPH) return HELM_ERR_CUDA;
+  if (!gi && o.launch == HELM_LAUNCH_GRAPH) return HELM_ERR_CUDA;
   HELM_CUDA_TRY(cudaMemsetAsync(A->dev_err, 0, sizeof(unsigned int), s));
   k_configure<<<1, 1, 0, s>>>(A->state, o.tol, o.maxit, o.use_x0 ? 1 : 0, o.deadline_s, 1);
   k_mx_configure<<<1, 1, 0, s>>>(A->state, o.inner_tol);
   HELM_CUDA_TRY(cudaGetLastError());
   SolverState* hs = A->state_host;
-  if (g) {
-    HELM_CUDA_TRY(cudaGraphLaunch(g->exec, s));
-  } else {
-    mx_init(a, sh, s);
-    for (;;) {
+  mx_init(a, sh, s);
+  for (;;) {
+    if (gi) {
+      HELM_CUDA_TRY(cudaGraphLaunch(gi->exec, s));
+      HELM_CUDA_TRY(cudaGraphLaunch(gs->exec, s));
+    } else {
       for (int q = 0; q < 8; ++q) mx_body(a, k, sh, s);
       HELM_CUDA_TRY(cudaGetLastError());
-      HELM_CUDA_TRY(cudaMemcpyAsync(hs, A->state, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
-      HELM_CUDA_TRY(cudaStreamSynchronize(s));
-      if (hs->status != ST_RUNNING) break;
     }
-    mx_tail(a, sh, s);
+    HELM_CUDA_TRY(cudaMemcpyAsync(hs, A->state, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
+    HELM_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hs->status != ST_RUNNING) break;
   }
+  mx_tail(a, sh, s);
+  HELM_CUDA_TRY(cudaGetLastError());
   unsigned int herr = 0;
   HELM_CUDA_TRY(cudaMemcpyAsync(hs, A->state, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
   HELM_CUDA_TRY(cudaMemcpyAsync(&herr, A->dev_err, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
