@@ -30,6 +30,7 @@
 #pragma once
 
 #include <algorithm>
+#include <type_traits>
 #include <cstring>
 #include <initializer_list>
 #include <utility>
@@ -710,6 +711,14 @@ inline SliceShape slice_shape(int32_t n, int num_sms, int max_threads, int block
 #ifndef HELM_SOLVER_BPS
 #define HELM_SOLVER_BPS 2
 #endif
+// The complex64 solver (the inner solves of mixed precision, HBM-bound) may
+// take another shape.
+#ifndef HELM_SOLVER32_THREADS
+#define HELM_SOLVER32_THREADS HELM_SOLVER_THREADS
+#endif
+#ifndef HELM_SOLVER32_BPS
+#define HELM_SOLVER32_BPS HELM_SOLVER_BPS
+#endif
 
 // Grid of the solver's kernels; the kernels (and `extra` ones: the tail, the
 // persistent kernel) must fit HELM_SOLVER_BPS such blocks per SM.
@@ -719,11 +728,13 @@ inline helm_status krylov_shapes(helm_csr A, KShapes<V>* sh, std::initializer_li
                                   reinterpret_cast<const void*>(&k_v<V>),    reinterpret_cast<const void*>(&k_s<V>),
                                   reinterpret_cast<const void*>(&k_t<V>),    reinterpret_cast<const void*>(&k_xr<V>)};
   for (const void* f : extra) fns.push_back(f);
-  const SliceShape ss = slice_shape(A->n, A->num_sms, HELM_SOLVER_THREADS, HELM_SOLVER_BPS);
+  const bool c64 = std::is_same<V, float2>::value;
+  const int bps = c64 ? HELM_SOLVER32_BPS : HELM_SOLVER_BPS;
+  const SliceShape ss = slice_shape(A->n, A->num_sms, c64 ? HELM_SOLVER32_THREADS : HELM_SOLVER_THREADS, bps);
   for (const void* fn : fns) {
     int b = 0;
     HELM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, ss.threads, 0));
-    if (b < HELM_SOLVER_BPS) return HELM_ERR_CUDA;
+    if (b < bps) return HELM_ERR_CUDA;
   }
   sh->grid = ss.grid;
   sh->threads = ss.threads;
