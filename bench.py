@@ -625,6 +625,46 @@ def run_spmv64(args):
                           "peak_gbs": peaks["hbm_gbs"], "peak_source": peak_src}), flush=True)
 
 
+def run_sweep(args):
+    """The batched sweep on the 60x30x25 cavity: 64 frequencies with one
+    shared right-hand side (graph loop) and 60 frequencies with one
+    right-hand side each, stored with stride 60 (copied to the sweep's
+    layout; host-driven loop, whose kernels a profiler can see).  `reps`
+    solves of each after one warm-up, to 1e-8 (at most `maxit` iterations):
+    BiCGStab, TFQMR and BiCGStab(4) on the shared right-hand side, BiCGStab
+    on the per-frequency ones."""
+    import numpy as np
+    import torch
+
+    import paper_2112_11880_gb300 as helm
+    from paper_2112_11880_gb300 import build as hbuild
+    hbuild.build()
+    dev = torch.device("cuda", 0)
+    cfg = helmgen.CONFIGS["sweep60"]
+    p = helmgen.assemble(cfg)
+    b = helmgen.source(p)
+    S = helm.Sweep(p.rowptr, p.colind, p.K, p.Mc, p.Bc, device=dev)
+    shared = torch.as_tensor(b, device=dev)
+    per_freq = torch.as_tensor(np.repeat(b[:, None], 60, axis=1), device=dev).contiguous()
+    methods = {"bicgstab": dict(method=helm.HELM_BICGSTAB), "tfqmr": dict(method=helm.HELM_TFQMR),
+               "bicgstabl4": dict(method=helm.HELM_BICGSTABL, ell=4)}
+    for name, F, rhs in (("bicgstab", 64, shared), ("tfqmr", 64, shared), ("bicgstabl4", 64, shared),
+                         ("bicgstab", 60, per_freq)):
+        w = [helmgen.omega(f) for f in cfg.freqs[:F]]
+        S.solve(w, rhs, tol=cfg.tol, maxit=args.sweep_maxit, **methods[name])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.reps):
+            X, infos = S.solve(w, rhs, tol=cfg.tol, maxit=args.sweep_maxit, **methods[name])
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / max(args.reps, 1)
+        print(json.dumps({"mode": "sweep", "method": name, "frequencies": F,
+                          "rhs": "shared" if rhs.dim() == 1 else "per frequency", "s": round(dt, 4),
+                          "iters_total": sum(i["iters"] for i in infos),
+                          "converged": all(i["status"] == "ok" for i in infos)}), flush=True)
+    S.close()
+
+
 # Vector lengths of the paper's BLAS-1 measurements (Section 3, Tables 2-7):
 # the order of Audi3D-4 and three larger sizes.
 VECTOR_SIZES = (648_849, 2_000_000, 9_000_000, 14_000_000)
@@ -863,11 +903,13 @@ def main():
     ap.add_argument("--ref-iters-per-solve", type=int, default=int(os.environ.get("HELM_ITERS_PER_SOLVE", "0")) or 0)
     ap.add_argument("--mixed-maxit", type=int, default=400000)
     ap.add_argument("--inner-tol", type=float, default=1e-3)
-    ap.add_argument("--mode", default="bench", choices=["bench", "spmv", "spmv64", "extensions", "vectors"],
+    ap.add_argument("--mode", default="bench", choices=["bench", "spmv", "spmv64", "sweep", "extensions", "vectors"],
                     help="spmv: only the complex128 SpMV loop on the same matrix (profiling target); "
                          "spmv64: the complex64 product with the diagonal and the sliced copy; "
+                         "sweep: the batched sweep alone (shared and per-frequency right-hand sides); "
                          "vectors: the BLAS-1 operations alone at the paper's vector lengths")
     ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--sweep-maxit", type=int, default=50000)
     ap.add_argument("--extensions", default="on", choices=["on", "off"],
                     help="on: add one pass of each other workload (box20, sweep60, cavity200 mixed, adjoint80) "
                          "to the default line as the 'extensions' key")
@@ -883,6 +925,8 @@ def main():
         run_vectors(args)
     elif args.mode == "spmv64":
         run_spmv64(args)
+    elif args.mode == "sweep":
+        run_sweep(args)
     elif args.impl == "reference":
         if not args.ref_iters_per_solve:
             args.ref_iters_per_solve = REF_ITERS_PER_SOLVE

@@ -413,8 +413,12 @@ helm_status helm_sweep_destroy(helm_sweep S);
  *             frozen), its iteration count continuing.
  *   h_infos : host helm_info[nfreq] or NULL; filled after the last pass.
  * The first call on a sweep times three tile shapes of the batched SpMV and
- * keeps the fastest (autotuning).  Returns HELM_OK when every frequency
- * converged, else the first failing frequency's status.
+ * keeps the fastest (autotuning).  An FP64 solve forms the real parts of all
+ * A_j once (K - w_j^2 M, nnz x F_p doubles held by the sweep, F_p = nfreq
+ * rounded up to 32) when they take at most 8 GiB; beyond that, or when the
+ * allocation fails, every product forms them (the same values).  Returns
+ * HELM_OK when every frequency converged, else the first failing
+ * frequency's status.
  */
 helm_status helm_sweep_solve(helm_sweep S, int32_t nfreq, const double* h_omega, const void* d_b,
                              int32_t b_ld, void* d_X, int32_t ldx, const helm_opts* o,

@@ -39,6 +39,10 @@ namespace helm {
 namespace {
 
 constexpr int kMaxF = 128;  // frequencies per sweep (<= threads per block: one thread per frequency)
+#ifndef HELM_SWEEP_FORM_MAX
+#define HELM_SWEEP_FORM_MAX (size_t(8) << 30)
+#endif
+constexpr size_t kSweepFormMax = HELM_SWEEP_FORM_MAX;  // bytes of formed A_j real parts at most (0: never)
 constexpr int kSwMaxEll = 8;                                     // batched BiCGStab(l): l <= 8
 constexpr int kSwGram = (kSwMaxEll + 1) * (kSwMaxEll + 2) / 2;  // Gram entries per frequency (45)
 
@@ -54,6 +58,10 @@ struct SweepDev {
   const float* K32;          // FP32 copies for the complex64 inner sweep (null in the FP64 sweep)
   const float* M32;
   const float* B32;
+  // FP64 sweep: the real parts of every A_j, are[k * are_ld + j] = fma(-w_j^2,
+  // M_k, K_k), formed once per solve (null: formed inside every product)
+  const double* are;
+  int32_t are_ld;
 };
 
 // Arguments of the sweep kernels.  V is the type of the Krylov vectors:
@@ -210,19 +218,33 @@ __device__ __forceinline__ double2 sweep_row(const SweepDev& A, int32_t i, int j
   const int64_t k0 = __ldg(A.rowptr + i), k1 = __ldg(A.rowptr + i + 1);
   double2 acc = make_double2(0.0, 0.0);
   if (A.bzero_blk[i >> 5] != 0) {
+    if (A.are) {
+      // the formed real parts: one coalesced load per entry and 32 frequencies
+      const double* ar = A.are + j;
 #pragma unroll 4
-    for (int64_t k = k0; k < k1; ++k) {
-      const int32_t c = __ldg(A.colind + k);
-      const double are = fma(-w2, __ldg(A.M + k), __ldg(A.K + k));
-      const double2 xv = __ldg(x + static_cast<int64_t>(c) * ld + j);
-      acc.x = fma(are, xv.x, acc.x);
-      acc.y = fma(are, xv.y, acc.y);
+      for (int64_t k = k0; k < k1; ++k) {
+        const int32_t c = __ldg(A.colind + k);
+        const double are = __ldg(ar + k * A.are_ld);
+        const double2 xv = __ldg(x + static_cast<int64_t>(c) * ld + j);
+        acc.x = fma(are, xv.x, acc.x);
+        acc.y = fma(are, xv.y, acc.y);
+      }
+    } else {
+#pragma unroll 4
+      for (int64_t k = k0; k < k1; ++k) {
+        const int32_t c = __ldg(A.colind + k);
+        const double are = fma(-w2, __ldg(A.M + k), __ldg(A.K + k));
+        const double2 xv = __ldg(x + static_cast<int64_t>(c) * ld + j);
+        acc.x = fma(are, xv.x, acc.x);
+        acc.y = fma(are, xv.y, acc.y);
+      }
     }
   } else {
 #pragma unroll 2
     for (int64_t k = k0; k < k1; ++k) {
       const int32_t c = __ldg(A.colind + k);
-      const double2 av = make_double2(fma(-w2, __ldg(A.M + k), __ldg(A.K + k)), wj * __ldg(A.B + k));
+      const double re = A.are ? __ldg(A.are + k * A.are_ld + j) : fma(-w2, __ldg(A.M + k), __ldg(A.K + k));
+      const double2 av = make_double2(re, wj * __ldg(A.B + k));
       acc = cfma(av, __ldg(x + static_cast<int64_t>(c) * ld + j), acc);
     }
   }
@@ -1359,6 +1381,21 @@ __global__ void k_sw_bzero(int32_t n, const int32_t* __restrict__ rowptr, const 
 }
 
 // FP32 copies of the K, M, B values (the complex64 inner sweep's operator)
+// are[k * Fp + j] = fma(-w_j^2, M_k, K_k): the real parts of all A_j, with
+// the product's own formula (w_j^2 = w_j * w_j), so the products give the
+// same bits as when they form them.
+__global__ void k_sw_form(int64_t nnz, int32_t Fp, const double* __restrict__ K, const double* __restrict__ M,
+                          const double* __restrict__ w, double* __restrict__ are) {
+  const int64_t total = nnz * Fp;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = q / Fp;
+    const int j = static_cast<int>(q % Fp);
+    const double wj = w[j];
+    const double w2 = wj * wj;
+    are[q] = fma(-w2, M[k], K[k]);
+  }
+}
+
 __global__ void k_sw_to_f32(int64_t nnz, const double* __restrict__ K, const double* __restrict__ M,
                             const double* __restrict__ B, float* __restrict__ out) {
   for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < nnz;
@@ -1547,6 +1584,10 @@ struct helm_sweep_s {
   int32_t Fcapl = 0, ellcap = 0;
   size_t gpart_cap = 0;
   int graphl_ell = 0;
+  // the formed real parts of the A_j of the last FP64 solve ([nnz][Fcap_are])
+  double* are = nullptr;
+  size_t are_cap = 0;
+  std::vector<double> are_w;      // the frequencies they were formed for
   int warps_per_block = 8;        // autotuned
   bool tuned = false;
   std::mutex mu;
@@ -1714,11 +1755,6 @@ helm_status sweep_alloc_tfqmr(helm_sweep S, int32_t Fp) {
   cudaFree(S->vecq);
   cudaFree(S->tqscal);
   cudaFree(S->tqint);
-  cudaFree(S->vecl);
-  cudaFree(S->lscal);
-  cudaFree(S->gpart);
-  if (S->graphl.exec) cudaGraphExecDestroy(S->graphl.exec);
-  if (S->graphl.graph) cudaGraphDestroy(S->graphl.graph);
   S->vecq = nullptr;
   S->tqscal = nullptr;
   S->tqint = nullptr;
@@ -2241,6 +2277,7 @@ helm_status helm_sweep_destroy(helm_sweep S) {
   cudaFree(S->vecl);
   cudaFree(S->lscal);
   cudaFree(S->gpart);
+  cudaFree(S->are);
   if (S->graphl.exec) cudaGraphExecDestroy(S->graphl.exec);
   if (S->graphl.graph) cudaGraphDestroy(S->graphl.graph);
   if (S->graph32.exec) cudaGraphExecDestroy(S->graph32.exec);
@@ -2300,6 +2337,33 @@ helm_status helm_sweep_solve(helm_sweep S, int32_t nfreq, const double* h_omega,
       if (cudaStreamSynchronize(s) != cudaSuccess && st == HELM_OK) st = HELM_ERR_CUDA;
     }
     return st;
+  }
+  // the real parts of every A_j, formed once for the whole solve when they fit
+  // the budget: each product then reads one value per entry and frequency
+  // instead of forming it (one FP64 FMA per entry and frequency less; the
+  // products are FP64-bound, the extra bytes are not the bound)
+  {
+    const size_t slots = static_cast<size_t>(S->nnz) * Fp;
+    if (S->nnz > 0 && kSweepFormMax > 0 && slots * sizeof(double) <= kSweepFormMax) {
+      if (S->are_cap < slots) {
+        cudaFree(S->are);
+        S->are = nullptr;
+        S->are_cap = 0;
+        S->are_w.clear();
+        if (cudaMalloc(&S->are, slots * sizeof(double)) == cudaSuccess) S->are_cap = slots;
+        else (void)cudaGetLastError();  // no room: the products form the values themselves
+        drop_sweep_graphs(S);
+      }
+      if (S->are) {
+        if (S->are_w != w) {
+          k_sw_form<<<vec_grid_for(static_cast<int64_t>(slots)), 256, 0, s>>>(S->nnz, Fp, S->K, S->M, a.w, S->are);
+          HELM_CUDA_TRY(cudaGetLastError());
+          S->are_w = w;
+        }
+        a.A.are = S->are;
+        a.A.are_ld = Fp;
+      }
+    }
   }
   if (opts.use_x0) {
     HELM_CUDA_TRY(cudaMemsetAsync(a.x, 0, static_cast<size_t>(S->n) * Fp * sizeof(double2), s));

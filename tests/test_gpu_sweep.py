@@ -341,3 +341,36 @@ def test_sweep_masking_freezes_converged_frequencies(method):
     assert infos2[0]["status"] == "ok" and infos2[1]["status"] == "not_converged"
     assert np.allclose(X2[:, 0].cpu().numpy(), X[:, 0].cpu().numpy(), rtol=0, atol=0)
     S.close()
+
+
+def test_sweep_methods_interleaved_on_one_handle():
+    """One handle solves with BiCGStab(2), TFQMR and BiCGStab in turn, then
+    with more frequencies (its buffers and graphs grow), then the first
+    sweep again: each repeat returns the same bits as the first solve of that
+    method and frequency set (the handle's launch shape is fixed after its
+    first solve), and every result meets tol in the oracle's residual."""
+    cfg = g.tiny_config(6, 5, 4, h=0.1, seed=9)
+    p = g.assemble(cfg)
+    b = g.source(p) + 0.2 * g.complex_vector(p.n, 8) * (~p.dirichlet)
+    bt = torch.as_tensor(b, device=DEV)
+    small = [g.omega(f) for f in (200.0, 450.0, 700.0)]
+    large = [g.omega(f) for f in np.linspace(150.0, 900.0, 40)]
+    S = helm.Sweep(p.rowptr, p.colind, p.K, p.Mc, p.Bc, device=DEV)
+    first = {}
+    order = [("bicgstabl2", small), ("tfqmr", small), ("bicgstab", small), ("tfqmr", large),
+             ("bicgstabl2", large), ("bicgstabl2", small), ("tfqmr", small), ("bicgstab", large),
+             ("bicgstab", small), ("tfqmr", large), ("bicgstabl2", large)]
+    for method, w in order:
+        X, infos = S.solve(w, bt, tol=1e-10, maxit=5000, **_method(method))
+        Xh = X.cpu().numpy()
+        key = (method, len(w))
+        for j in range(len(w)):
+            assert infos[j]["status"] == "ok", (key, j, infos[j])
+            vals = oracle.helmholtz_values(p.K, p.Mc, p.Bc, w[j])
+            assert _relres(p, vals, b, Xh[:, j]) <= 1e-10 * (1 + 1e-6), (key, j)
+        if key in first:
+            assert np.array_equal(Xh, first[key][0]), key
+            assert [i["iters"] for i in infos] == first[key][1], key
+        else:
+            first[key] = (Xh, [i["iters"] for i in infos])
+    S.close()
