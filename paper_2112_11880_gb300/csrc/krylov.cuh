@@ -129,6 +129,28 @@ __device__ __forceinline__ bool deadline_passed(const SolverState* st) {
 __global__ void k_configure(SolverState* st, double tol, int32_t maxit, int32_t use_x0, double deadline_s,
                             int32_t fresh);
 
+// Programmatic dependent launch.  The loop's kernels are launched so that a
+// kernel's blocks may be scheduled while its predecessor is still running:
+// they take the SMs that the predecessor's blocks leave while its last block
+// forms the scalars, and wait here until the predecessor grid has completed
+// and its writes are visible.  Every kernel of the loop calls this before it
+// reads anything, so the order of every operation is that of plain launches
+// (with a plain launch the wait returns at once).  Each grid is one wave, so
+// the waiting blocks never hold an SM that a block of the predecessor needs.
+// Measured on the 120x60x50 cavity (BiCGStab, 19,653 iterations): the
+// host-driven loop 148.6 -> 141.4 us per iteration; the graph (the WHILE
+// node, or a plain graph of 16 iterations) 138.1 us either way, although its
+// body keeps the programmatic edges: a graph launch already hides that gap.
+#ifndef HELM_PDL
+#define HELM_PDL 1
+#endif
+__device__ __forceinline__ void pdl_enter() {
+#if HELM_PDL
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#endif
+}
+
 // ---------------------------------------------------------------- reductions
 
 // Fixed-order total of the block partials partials[b K + k], b < G: thread j
@@ -531,6 +553,7 @@ __device__ __forceinline__ void ph_xr(const KArgs<V>& a, V alpha, V omega, bool 
 
 template <class V>
 __global__ void __launch_bounds__(kSolverThreads, kSolverMinBlocks) k_init(KArgs<V> a) {
+  pdl_enter();
   using S = typename Prec<V>::S;
   using C = typename Prec<V>::C;
   __shared__ double red[32 * 4];
@@ -559,6 +582,7 @@ __global__ void __launch_bounds__(kSolverThreads, kSolverMinBlocks) k_init(KArgs
 // K1: p = r + beta (p - omega v)
 template <class V>
 __global__ void __launch_bounds__(kSolverThreads, kSolverMinBlocks) k_p(KArgs<V> a) {
+  pdl_enter();
   const SolverState* st = a.st;
   if (st->status != ST_RUNNING || refine_step_pending(st)) return;
   ph_p<V>(a, Prec<V>::cvt(st->beta), Prec<V>::cvt(st->omega));
@@ -567,6 +591,7 @@ __global__ void __launch_bounds__(kSolverThreads, kSolverMinBlocks) k_p(KArgs<V>
 // K2: v = A p, (r^, v) -> alpha
 template <class V>
 __global__ void __launch_bounds__(kSolverThreads, kSolverMinBlocks) k_v(KArgs<V> a) {
+  pdl_enter();
   __shared__ double red[32 * 2];
   SolverState* st = a.st;
   if (st->status != ST_RUNNING || refine_step_pending(st)) return;
@@ -583,6 +608,7 @@ __global__ void __launch_bounds__(kSolverThreads, kSolverMinBlocks) k_v(KArgs<V>
 // K3: s = r - alpha v, ||s||
 template <class V>
 __global__ void __launch_bounds__(kSolverThreads, kSolverMinBlocks) k_s(KArgs<V> a) {
+  pdl_enter();
   __shared__ double red[32];
   SolverState* st = a.st;
   if (st->status != ST_RUNNING || refine_step_pending(st)) return;
@@ -596,6 +622,7 @@ __global__ void __launch_bounds__(kSolverThreads, kSolverMinBlocks) k_s(KArgs<V>
 // K4: t = A s, (t, s), (t, t) -> omega
 template <class V>
 __global__ void __launch_bounds__(kSolverThreads, kSolverMinBlocks) k_t(KArgs<V> a) {
+  pdl_enter();
   using S = typename Prec<V>::S;
   __shared__ double red[32 * 3];
   SolverState* st = a.st;
@@ -613,6 +640,7 @@ __global__ void __launch_bounds__(kSolverThreads, kSolverMinBlocks) k_t(KArgs<V>
 // K5: x += alpha p + omega s, r = s - omega t; stop test; rho, beta
 template <class V>
 __global__ void __launch_bounds__(kSolverThreads, kSolverMinBlocks) k_xr(KArgs<V> a) {
+  pdl_enter();
   using S = typename Prec<V>::S;
   __shared__ double red[32 * 3];
   SolverState* st = a.st;
@@ -667,13 +695,35 @@ inline void enqueue_init(const KArgs<V>& a, const KShapes<V>& sh, cudaStream_t s
   k_init<V><<<sh.grid, sh.threads, 0, s>>>(a);
 }
 
+// A loop kernel launched with programmatic stream serialization (a
+// programmatic edge from the kernel before it when captured into a graph);
+// see pdl_enter.
+template <class V>
+inline void launch_loop_kernel(void (*kernel)(KArgs<V>), const KArgs<V>& a, const KShapes<V>& sh, cudaStream_t s) {
+#if HELM_PDL
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(sh.grid));
+  cfg.blockDim = dim3(static_cast<unsigned>(sh.threads));
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  (void)cudaLaunchKernelEx(&cfg, kernel, a);  // errors surface at the caller's cudaGetLastError
+#else
+  kernel<<<sh.grid, sh.threads, 0, s>>>(a);
+#endif
+}
+
 template <class V>
 inline void enqueue_body(const KArgs<V>& a, const KShapes<V>& sh, cudaStream_t s) {
-  k_p<V><<<sh.grid, sh.threads, 0, s>>>(a);
-  k_v<V><<<sh.grid, sh.threads, 0, s>>>(a);
-  k_s<V><<<sh.grid, sh.threads, 0, s>>>(a);
-  k_t<V><<<sh.grid, sh.threads, 0, s>>>(a);
-  k_xr<V><<<sh.grid, sh.threads, 0, s>>>(a);
+  launch_loop_kernel<V>(k_p<V>, a, sh, s);
+  launch_loop_kernel<V>(k_v<V>, a, sh, s);
+  launch_loop_kernel<V>(k_s<V>, a, sh, s);
+  launch_loop_kernel<V>(k_t<V>, a, sh, s);
+  launch_loop_kernel<V>(k_xr<V>, a, sh, s);
 }
 
 template <class V>
