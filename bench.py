@@ -648,8 +648,12 @@ def run_sweep(args):
     per_freq = torch.as_tensor(np.repeat(b[:, None], 60, axis=1), device=dev).contiguous()
     methods = {"bicgstab": dict(method=helm.HELM_BICGSTAB), "tfqmr": dict(method=helm.HELM_TFQMR),
                "bicgstabl4": dict(method=helm.HELM_BICGSTABL, ell=4)}
-    for name, F, rhs in (("bicgstab", 64, shared), ("tfqmr", 64, shared), ("bicgstabl4", 64, shared),
-                         ("bicgstab", 60, per_freq)):
+    cases = (("bicgstab", "bicgstab", 64, shared), ("tfqmr", "tfqmr", 64, shared),
+             ("bicgstabl4", "bicgstabl4", 64, shared), ("bicgstab-strided", "bicgstab", 60, per_freq))
+    wanted = args.sweep_cases.split(",")
+    for case, name, F, rhs in cases:
+        if "all" not in wanted and case not in wanted:
+            continue
         w = [helmgen.omega(f) for f in cfg.freqs[:F]]
         S.solve(w, rhs, tol=cfg.tol, maxit=args.sweep_maxit, **methods[name])
         torch.cuda.synchronize()
@@ -910,6 +914,8 @@ def main():
                          "vectors: the BLAS-1 operations alone at the paper's vector lengths")
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--sweep-maxit", type=int, default=50000)
+    ap.add_argument("--sweep-cases", default="all",
+                    help="sweep mode: comma list of bicgstab, tfqmr, bicgstabl4, bicgstab-strided (or all)")
     ap.add_argument("--extensions", default="on", choices=["on", "off"],
                     help="on: add one pass of each other workload (box20, sweep60, cavity200 mixed, adjoint80) "
                          "to the default line as the 'extensions' key")
