@@ -7,6 +7,7 @@
 
 #include <map>
 #include <mutex>
+#include <tuple>
 #include <utility>
 
 #include "../../include/helm.h"
@@ -112,7 +113,7 @@ struct helm_csr_s {
   int nvec32 = 0;
 
   std::mutex mu;
-  std::map<std::pair<const void*, const void*>, helm::GraphEntry> graphs;  // (b, x) -> graph
+  std::map<std::tuple<const void*, const void*, int>, helm::GraphEntry> graphs;  // (b, x, variant) -> graph
 };
 
 namespace helm {
@@ -159,12 +160,10 @@ helm_status launch_spmv128(helm_csr A, const double2* x, double2* y, double2 alp
 helm_status launch_spmv64(helm_csr A, const float2* x, float2* y, float2 alpha, float2 beta, cudaStream_t s);
 
 // Solver entry points implemented in the solver translation units.
-// Graph-cache key of a solve: (b, x) tagged with the method and the
-// preconditioner, so that each variant keeps its own graph.
-inline std::pair<const void*, const void*> graph_key(const void* b, const void* x, int tag, const helm_opts& o) {
-  return std::make_pair(static_cast<const void*>(static_cast<const char*>(b) + tag +
-                                                 (o.precond == HELM_PRECOND_JACOBI ? 16 : 0)),
-                        x);
+// Graph-cache key of a solve: (b, x) and the variant (the method tag and
+// the preconditioner), so that each variant keeps its own graph.
+inline std::tuple<const void*, const void*, int> graph_key(const void* b, const void* x, int tag, const helm_opts& o) {
+  return std::make_tuple(b, x, 2 * tag + (o.precond == HELM_PRECOND_JACOBI ? 1 : 0));
 }
 
 helm_status ensure_jacobi(helm_csr A, cudaStream_t s);
