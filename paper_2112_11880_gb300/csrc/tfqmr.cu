@@ -447,7 +447,7 @@ helm_status tfqmr_fp64(helm_csr A, const double2* b, double2* x, const helm_opts
   a.tickets = A->tickets;
   a.dev_err = A->dev_err;
 
-  // graph cache: key (b, x) tagged by the method (low bit of b set for TFQMR)
+  // graph cache: key (b, x, variant), the variant tagged as TFQMR
   GraphEntry* g = nullptr;
   auto key = graph_key(b, x, 1, o);
   auto it = A->graphs.find(key);
@@ -500,7 +500,7 @@ helm_status tfqmr_fp64(helm_csr A, const double2* b, double2* x, const helm_opts
     fresh = 0;
   }
   helm_status result = hs->status == ST_RUNNING ? HELM_ERR_CUDA : static_cast<helm_status>(hs->status);
-  if (result == HELM_OK && !(hs->relres_true <= 1.5 * o.tol)) result = HELM_ERR_NOT_CONVERGED;
+  if (result == HELM_OK && !(hs->relres_true <= o.tol)) result = HELM_ERR_NOT_CONVERGED;
   if (info) {
     info->iters = hs->iter;
     info->restarts = hs->restarts;
