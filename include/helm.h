@@ -116,7 +116,8 @@ helm_status helm_csr_diagonals(helm_csr A, int32_t* out);
  * complex arithmetic).
  *   alpha, beta : host complex128 scalars (double[2]); for a complex64 handle
  *                 they are rounded to complex64.
- *   d_x         : complex[n] of the handle's type; must not alias d_y.
+ *   d_x         : complex[n] of the handle's type; must not overlap d_y
+ *                 (HELM_ERR_INVALID).
  *   d_y         : complex[n]; not read when beta == 0.
  * Asynchronous.
  */
@@ -285,6 +286,7 @@ void helm_opts_default(helm_opts* o);
  * (Section 4: P-BiCGSTAB, P-BiCGSTAB(l), P-TFQMR; identity preconditioner).
  *   d_b  : complex128[n] right-hand side.
  *   d_x  : complex128[n] solution, overwritten; read first when o->use_x0.
+ *          d_b and d_x must not overlap (HELM_ERR_INVALID).
  *   o    : options (NULL = defaults).
  *   info : host, filled after one synchronisation of `stream` at the end;
  *          may be NULL.
@@ -388,7 +390,8 @@ helm_status helm_sweep_destroy(helm_sweep S);
  *             b_ld >= nfreq, or b_j[i] = d_b[i] (one b shared by all
  *             frequencies) for b_ld = 0.
  *   d_X     : complex128 solutions, x_j[i] = d_X[i * ldx + j], ldx >= nfreq
- *             (read first when o->use_x0).
+ *             (read first when o->use_x0); must not overlap d_b
+ *             (HELM_ERR_INVALID).
  *   o       : tol, maxit, use_x0, deadline_s, method, precision, inner_tol
  *             used.  method HELM_BICGSTAB (FP64 or mixed precision),
  *             HELM_TFQMR (FP64 only; the recurrences of helm_bicgstab_solve's
@@ -433,7 +436,7 @@ helm_status helm_sweep_solve(helm_sweep S, int32_t nfreq, const double* h_omega,
  *   h_omega : host double[nfreq].
  *   d_X     : complex128, x_j[i] = d_X[i * ldx + j], ldx >= nfreq.
  *   d_Y     : complex128 out, y_j[i] = d_Y[i * ldy + j], ldy >= nfreq; must
- *             not alias d_X.
+ *             not overlap d_X (HELM_ERR_INVALID).
  * Asynchronous (h_omega is copied before the call returns).
  */
 helm_status helm_sweep_spmv(helm_sweep S, int32_t nfreq, const double* h_omega, const void* d_X, int32_t ldx,
@@ -480,7 +483,8 @@ helm_status helm_ddm_subdomains(helm_ddm S, int32_t* rows, int64_t* nnz);
  * the restriction to the extended block p, Rt_p^T the prolongation that keeps
  * the rows of the block p owns; the A_p^{-1} together as one BiCGStab solve
  * of D to a relative residual inner_tol (at most 5000 iterations; 0 asks for
- * the tightest it reaches).  d_r, d_z: complex128[n], distinct.  Synchronises
+ * the tightest it reaches).  d_r, d_z: complex128[n], not overlapping
+ * (HELM_ERR_INVALID).  Synchronises
  * `stream`.
  */
 helm_status helm_ddm_apply(helm_ddm S, const void* d_r, void* d_z, double inner_tol,

@@ -1002,7 +1002,8 @@ helm_status helm_spmv(helm_csr A, const double* alpha, const void* d_x, const do
                       helm_stream_t stream) {
   if (!A || !alpha || !beta) return HELM_ERR_INVALID;
   if (A->n > 0 && (!d_x || !d_y)) return HELM_ERR_INVALID;
-  if (d_x == d_y && A->n > 0) return HELM_ERR_INVALID;
+  const size_t vb = static_cast<size_t>(A->n) * (A->dt == HELM_C128 ? sizeof(double2) : sizeof(float2));
+  if (overlaps(d_x, vb, d_y, vb)) return HELM_ERR_INVALID;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (A->dt == HELM_C128) {
     if (!aligned(d_x, 16) || !aligned(d_y, 16)) return HELM_ERR_INVALID;
@@ -1094,7 +1095,8 @@ helm_status helm_bicgstab_solve(helm_csr A, const void* d_b, void* d_x, const he
   if (info) std::memset(info, 0, sizeof(*info));
   if (!A || A->dt != HELM_C128) return HELM_ERR_INVALID;
   if (A->n > 0 && (!d_b || !d_x)) return HELM_ERR_INVALID;
-  if (!aligned(d_b, 16) || !aligned(d_x, 16) || d_b == d_x) return HELM_ERR_INVALID;
+  if (!aligned(d_b, 16) || !aligned(d_x, 16)) return HELM_ERR_INVALID;
+  if (d_b == d_x || overlaps(d_b, sizeof(double2) * A->n, d_x, sizeof(double2) * A->n)) return HELM_ERR_INVALID;
   if (!(opts.tol >= 0.0) || opts.maxit < 0) return HELM_ERR_INVALID;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (opts.precond != HELM_PRECOND_NONE && opts.precond != HELM_PRECOND_JACOBI) return HELM_ERR_INVALID;

@@ -394,8 +394,8 @@ helm_status helm_ddm_subdomains(helm_ddm S, int32_t* d_rows, int64_t* d_nnz) {
 }
 
 helm_status helm_ddm_apply(helm_ddm S, const void* d_r, void* d_z, double inner_tol, helm_stream_t stream) {
-  if (!S || !d_r || !d_z || d_r == d_z || !aligned(d_r, 16) || !aligned(d_z, 16) || !(inner_tol >= 0.0))
-    return HELM_ERR_INVALID;
+  if (!S || !d_r || !d_z || !aligned(d_r, 16) || !aligned(d_z, 16) || !(inner_tol >= 0.0)) return HELM_ERR_INVALID;
+  if (overlaps(d_r, sizeof(double2) * S->n, d_z, sizeof(double2) * S->n)) return HELM_ERR_INVALID;
   std::lock_guard<std::mutex> lk(S->mu);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   int32_t it = 0;
@@ -410,7 +410,8 @@ helm_status helm_ddm_solve(helm_ddm S, const void* d_b, void* d_x, const helm_op
   if (o) opts = *o;
   else helm_opts_default(&opts);
   if (info) std::memset(info, 0, sizeof(*info));
-  if (!S || !d_b || !d_x || d_b == d_x || !aligned(d_b, 16) || !aligned(d_x, 16)) return HELM_ERR_INVALID;
+  if (!S || !d_b || !d_x || !aligned(d_b, 16) || !aligned(d_x, 16)) return HELM_ERR_INVALID;
+  if (overlaps(d_b, sizeof(double2) * S->n, d_x, sizeof(double2) * S->n)) return HELM_ERR_INVALID;
   if (!(opts.tol >= 0.0) || opts.maxit < 0) return HELM_ERR_INVALID;
   std::lock_guard<std::mutex> lk(S->mu);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

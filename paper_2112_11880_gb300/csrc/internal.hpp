@@ -139,6 +139,11 @@ void debug_cuda_error(cudaError_t e, const char* file, int line);
   } while (0)
 
 inline bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+// The byte ranges [p, p + pn) and [q, q + qn) share a byte.
+inline bool overlaps(const void* p, size_t pn, const void* q, size_t qn) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(p), b = reinterpret_cast<uintptr_t>(q);
+  return pn > 0 && qn > 0 && a < b + qn && b < a + pn;
+}
 
 // Launch-shape helpers (api.cu).
 cudaError_t set_smem_attr(const void* fn, size_t bytes);

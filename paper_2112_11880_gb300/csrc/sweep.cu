@@ -2212,6 +2212,14 @@ helm_status sweep_solve_mixed(helm_sweep S, const SweepArgs& a64, const SweepSha
 
 }  // namespace
 
+// Bytes from the first to one past the last element of an [n][ld] complex128
+// array of nfreq columns (ld = 0: one shared column).
+inline size_t sweep_extent(int32_t n, int32_t ld, int32_t nfreq) {
+  if (n <= 0) return 0;
+  const size_t rows = static_cast<size_t>(n);
+  return sizeof(double2) * (ld == 0 ? rows : (rows - 1) * static_cast<size_t>(ld) + static_cast<size_t>(nfreq));
+}
+
 extern "C" {
 
 helm_status helm_sweep_create(helm_sweep* out, int32_t n, int64_t nnz, const int32_t* d_rowptr,
@@ -2298,6 +2306,8 @@ helm_status helm_sweep_solve(helm_sweep S, int32_t nfreq, const double* h_omega,
   if (!S || nfreq < 1 || nfreq > kMaxF || !h_omega || (b_ld != 0 && b_ld < nfreq) || ldx < nfreq) return HELM_ERR_INVALID;
   if (S->n > 0 && (!d_b || !d_X)) return HELM_ERR_INVALID;
   if (!aligned(d_b, 16) || !aligned(d_X, 16) || !(opts.tol >= 0.0) || opts.maxit < 0) return HELM_ERR_INVALID;
+  if (S->n > 0 && overlaps(d_b, sweep_extent(S->n, b_ld, nfreq), d_X, sweep_extent(S->n, ldx, nfreq)))
+    return HELM_ERR_INVALID;
   if (opts.precision != HELM_PREC_FP64 && opts.precision != HELM_PREC_MIXED) return HELM_ERR_INVALID;
   if (opts.method != HELM_BICGSTAB &&
       !((opts.method == HELM_TFQMR || opts.method == HELM_BICGSTABL) && opts.precision == HELM_PREC_FP64))
@@ -2477,7 +2487,8 @@ helm_status helm_sweep_spmv(helm_sweep S, int32_t nfreq, const double* h_omega, 
                             void* d_Y, int32_t ldy, helm_stream_t stream) {
   if (!S || nfreq < 1 || nfreq > kMaxF || !h_omega || ldx < nfreq || ldy < nfreq) return HELM_ERR_INVALID;
   if (S->n == 0) return HELM_OK;
-  if (!d_X || !d_Y || d_X == d_Y || !aligned(d_X, 16) || !aligned(d_Y, 16)) return HELM_ERR_INVALID;
+  if (!d_X || !d_Y || !aligned(d_X, 16) || !aligned(d_Y, 16)) return HELM_ERR_INVALID;
+  if (overlaps(d_X, sweep_extent(S->n, ldx, nfreq), d_Y, sweep_extent(S->n, ldy, nfreq))) return HELM_ERR_INVALID;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   std::lock_guard<std::mutex> lk(S->mu);
   const int32_t Fp = (nfreq + 31) / 32 * 32;

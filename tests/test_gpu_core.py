@@ -311,6 +311,42 @@ def test_invalid_arguments_rejected():
     A.close()
 
 
+def test_overlapping_vectors_rejected():
+    """Input and output vectors that share memory (the same buffer, or views
+    one element apart) are rejected by the product, the solve, the sweep and
+    the Schwarz preconditioner; disjoint neighbours are accepted."""
+    p, vals = _tiny_problem((4, 3, 3), 400.0, 2)[:2]
+    n = p.n
+    A = helm.CsrMatrix.from_host(p.rowptr, p.colind, vals, device=DEV)
+    buf = _dev(g.complex_vector(2 * n + 1, 3))
+    lo, hi, apart = buf[0:n], buf[1:n + 1], buf[n:2 * n]
+    for y in (lo, hi):
+        with pytest.raises(helm.HelmError):
+            helm.helm_spmv(A.handle, 1.0, lo, 0.0, y)
+        with pytest.raises(helm.HelmError):
+            helm.helm_bicgstab_solve(A.handle, lo, y)
+    helm.helm_spmv(A.handle, 1.0, lo, 0.0, apart)
+    info = helm.helm_bicgstab_solve(A.handle, lo, apart, helm.default_opts(tol=1e-10))
+    assert info["status"] == "ok"
+    D = helm.Ddm(A, 2, 4)
+    with pytest.raises(helm.HelmError):
+        D.apply(lo, hi)
+    with pytest.raises(helm.HelmError):
+        D.solve(lo, hi)
+    D.close()
+    S = helm.Sweep(p.rowptr, p.colind, p.K, p.Mc, p.Bc, device=DEV)
+    w = [g.omega(f) for f in (200.0, 300.0)]
+    X = torch.zeros((n, 2), dtype=torch.complex128, device=DEV)
+    B2 = torch.zeros((n + 1, 2), dtype=torch.complex128, device=DEV)
+    with pytest.raises(helm.HelmError):
+        helm.helm_sweep_solve(S.handle, w, B2[0:n], B2[1:n + 1])
+    with pytest.raises(helm.HelmError):
+        helm.helm_sweep_spmv(S.handle, w, B2[0:n], B2[1:n + 1])
+    helm.helm_sweep_spmv(S.handle, w, B2[0:n], X)
+    S.close()
+    A.close()
+
+
 # ---------------------------------------------------------------- BiCGStab
 
 def _tiny_problem(dims, F, seed):
