@@ -315,6 +315,9 @@ def helm_sweep_spmv(handle, omegas, X, Y, stream=None) -> None:
     """Y[:, j] = A_j X[:, j] for the frequencies `omegas` (X, Y: n x F
     complex128, row-major, device)."""
     import numpy as np
+    for t in (X, Y):
+        if not t.is_cuda or t.dim() != 2 or t.stride(1) != 1:
+            raise ValueError("X, Y: 2-D CUDA tensors with unit column stride")
     w = np.ascontiguousarray(np.asarray(omegas, dtype=np.float64))
     F = int(w.size)
     _check(load_library().helm_sweep_spmv(handle, F, w.ctypes.data_as(ctypes.c_void_p), _ptr(X), int(X.stride(0)),
@@ -365,6 +368,7 @@ class Ddm:
         if z is None:
             z = torch.empty_like(r)
         _check_vector(z, self.n, torch.complex128, "z")
+        _require_cuda(r, z)
         _check(load_library().helm_ddm_apply(self.handle, _ptr(r), _ptr(z), float(inner_tol), _stream(stream)),
                "helm_ddm_apply")
         return z
@@ -375,6 +379,7 @@ class Ddm:
         if x is None:
             x = torch.zeros_like(b)
         _check_vector(x, self.n, torch.complex128, "x")
+        _require_cuda(b, x)
         info = helm_info()
         o = default_opts(**opts)
         st = load_library().helm_ddm_solve(self.handle, _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(info),
