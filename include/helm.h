@@ -310,6 +310,7 @@ helm_status helm_bicgstab_solve(helm_csr A, const void* d_b, void* d_x, const he
  *               (for L = sum |u_r - d_r|^2: conj(u_r - d_r) on receivers).
  *   d_mu      : complex128[n] output.
  *   d_dLdvals : complex128[nnz] output or NULL.
+ * The outputs must not overlap d_u, d_dLdu or each other (HELM_ERR_INVALID).
  * Synchronises once at the end (info as helm_bicgstab_solve).
  */
 helm_status helm_adjoint(helm_csr A, const void* d_u, const void* d_dLdu, const helm_opts* o,

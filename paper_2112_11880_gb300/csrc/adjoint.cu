@@ -117,7 +117,9 @@ helm_status helm_adjoint(helm_csr A, const void* d_u, const void* d_dLdu, const 
   if (A->n > 0 && (!d_u || !d_dLdu || !d_mu)) return HELM_ERR_INVALID;
   if (!aligned(d_u, 16) || !aligned(d_dLdu, 16) || !aligned(d_mu, 16) || !aligned(d_dLdvals, 16))
     return HELM_ERR_INVALID;
-  if (d_mu == d_u || d_mu == d_dLdu) return HELM_ERR_INVALID;
+  const size_t vb = sizeof(double2) * static_cast<size_t>(A->n), eb = sizeof(double2) * static_cast<size_t>(A->nnz);
+  if (overlaps(d_mu, vb, d_u, vb) || overlaps(d_mu, vb, d_dLdu, vb)) return HELM_ERR_INVALID;
+  if (d_dLdvals && (overlaps(d_dLdvals, eb, d_mu, vb) || overlaps(d_dLdvals, eb, d_u, vb))) return HELM_ERR_INVALID;
   // A^T mu = dL/du with A^T = A: the forward solver on the same handle.
   helm_status st = helm_bicgstab_solve(A, d_dLdu, d_mu, o, info, stream);
   if (st != HELM_OK) return st;

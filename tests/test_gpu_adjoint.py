@@ -75,6 +75,28 @@ def test_adjoint_scatter_and_chain_vs_oracle():
     A.close()
 
 
+def test_adjoint_rejects_overlapping_outputs():
+    """mu and dL/dA may not share memory with u, dL/du or each other."""
+    cfg = g.tiny_config(3, 3, 3, h=0.1, F=400.0, seed=4)
+    p = g.assemble(cfg)
+    vals = g.helmholtz_values(p, cfg.F)
+    A = helm.CsrMatrix.from_host(p.rowptr, p.colind, vals, device=DEV)
+    n = p.n
+    buf = torch.as_tensor(g.complex_vector(3 * n + 1, 2), device=DEV)
+    u, w = buf[0:n], buf[n:2 * n]
+    G = torch.empty(p.nnz, dtype=torch.complex128, device=DEV)
+    for mu in (buf[1:n + 1], buf[n + 1:2 * n + 1]):
+        with pytest.raises(helm.HelmError):
+            helm.helm_adjoint(A.handle, u, w, mu, G)
+    mu = buf[2 * n:3 * n]
+    Gb = torch.empty(p.nnz + n, dtype=torch.complex128, device=DEV)
+    with pytest.raises(helm.HelmError):
+        helm.helm_adjoint(A.handle, u, w, Gb[0:n], Gb[1:p.nnz + 1])
+    info = helm.helm_adjoint(A.handle, u, w, mu, G, helm.default_opts(tol=1e-10))
+    assert info["status"] == "ok"
+    A.close()
+
+
 def _loss_gpu(c, b, fem, rec, d, opts):
     with torch.no_grad():
         u = hgrad.solve_sound_speed(c, b, fem, opts)
