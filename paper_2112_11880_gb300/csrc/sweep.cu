@@ -1634,6 +1634,7 @@ helm_status sweep_alloc(helm_sweep S, int32_t Fp, size_t blocks) {
   if (S->partials_cap < need) {
     cudaFree(S->partials);
     S->partials = nullptr;
+    S->partials_cap = 0;
     HELM_CUDA_TRY(cudaMalloc(&S->partials, need * sizeof(double)));
     S->partials_cap = need;
     drop_sweep_graphs(S);
