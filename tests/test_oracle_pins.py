@@ -386,15 +386,38 @@ def test_sound_speed_gradient_against_finite_differences():
             assert abs(f - ref) <= 1e-6 * max(1.0, abs(ref)) + 1e-9
 
 
-def test_helmholtz_values_frequency_form():
-    cfg = g.CONFIGS["sweep60"]
+def test_helmholtz_values_against_element_assembly():
+    """The oracle's A(w) = K - w^2 M_c + i w B_c on the assembled arrays equals
+    the Helmholtz operator's definition summed element by element here,
+    sum_e K_e - (w / c_e)^2 M_e + i (w / c_e) B_f (B_f on the elements with a
+    face on the impedance plane), with the Dirichlet rows as identity rows and
+    their columns dropped.  The two routes share only the element matrices
+    (pinned by the exact fixture): a wrong power of w or of c_e, a sign or a
+    dropped term fails here.  A varying sound speed, two frequencies."""
+    cfg = g.tiny_config(3, 2, 3, h=0.1, seed=5)
     p = g.assemble(cfg)
-    for F in (cfg.freqs[0], cfg.freqs[37]):
+    assert np.ptp(p.c) > 0
+    Ke, Me, Bf = g.element_matrices(cfg.h)
+    en = g.element_nodes(cfg)
+    top = g.top_elements(cfg).astype(bool)
+    D = p.dirichlet
+    for F in (150.0, 900.0):
         w = g.omega(F)
-        a = oracle.helmholtz_values(p.K, p.Mc, p.Bc, w)
-        # per element: K_e - (w/c_e)^2 M_e + i (w/c_e) B_f, summed: same values
-        b = g.helmholtz_values(p, F)
-        assert np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-300)) <= 1e-15
+        E = np.zeros((p.n, p.n), dtype=np.complex128)
+        for e in range(cfg.n_elem):
+            k = w / p.c[e]
+            Ae = Ke - k * k * Me + (1j * k * Bf if top[e] else 0.0)
+            for a in range(8):
+                for b in range(8):
+                    E[en[e, a], en[e, b]] += Ae[a, b]
+        E[D, :] = 0.0
+        E[:, D] = 0.0
+        E[D, D] = 1.0
+        A = oracle.densify(p.rowptr, p.colind, oracle.helmholtz_values(p.K, p.Mc, p.Bc, w))
+        scale = np.abs(Ke).max() + (w / p.c.min()) ** 2 * np.abs(Me).max() + (w / p.c.min()) * np.abs(Bf).max()
+        assert np.max(np.abs(A - E)) <= 1e-14 * scale
+        # the impedance term is present exactly on the top plane's couplings
+        assert np.any(A.imag != 0) and np.all(A.imag[~np.isin(np.arange(p.n), en[top].ravel()), :] == 0)
     assert np.array_equal(oracle.helmholtz_values(p.K, p.Mc, p.Bc, 0.0).real, p.K)
 
 
