@@ -369,7 +369,9 @@ helm_status helm_conj_scale(int64_t n, const double* alpha, const void* d_x, voi
  * frequencies at once on
  *   A_j = K - w_j^2 M + i w_j B,
  * K, M, B real on one CSR pattern (stiffness, mass scaled by 1/c^2, impedance
- * face scaled by 1/c), A_j formed on the fly inside the SpMV.  Converged
+ * face scaled by 1/c), never assembled as complex matrices: the real parts
+ * fma(-w_j^2, M, K) are formed once per solve (or inside every product when
+ * they do not fit, the same values) and i w_j B inside the product.  Converged
  * frequencies are frozen; the whole sweep is one graph launch.
  */
 typedef struct helm_sweep_s* helm_sweep; /* opaque */
@@ -430,7 +432,7 @@ helm_status helm_sweep_solve(helm_sweep S, int32_t nfreq, const double* h_omega,
 
 /*
  * helm_sweep_spmv -- Y_j = A_j X_j for j < nfreq (1 <= nfreq <= 128), with
- * A_j = K - w_j^2 M + i w_j B formed on the fly exactly as inside
+ * A_j = K - w_j^2 M + i w_j B formed inside the product with the values of
  * helm_sweep_solve (the same row sums: each entry fma(-w_j^2, M, K) +
  * i w_j B, CSR order) -- the frequency sweep's product (Section 3's SpMV at
  * the wavenumbers of Section 1, k_j = w_j / c).
